@@ -1,0 +1,133 @@
+"""Seeded synthetic inputs shared by the oracle side and the CUDA side.
+
+This module draws random numbers and shapes fields; it holds none of the
+solver's arithmetic (no operator, sweep or reduction).  Right-hand sides that
+are defined through the operator (``b = A * ones``) are computed by each side
+with its own operator.
+
+Generator: a counter-based SplitMix64 stream (Steele, Lea & Flood, "Fast
+splittable pseudorandom number generators", OOPSLA 2014).  Element ``i`` of
+stream ``(seed, stream_id)`` is ``mix(key + (i + 1) * GAMMA)`` with
+``key = mix(seed * GAMMA ^ (stream_id << 32))`` and ``mix`` the SplitMix64
+finaliser.  Uniforms are ``(v >> 11) * 2**-53`` in [0, 1); normals use
+Box-Muller on the uniform pairs (2i, 2i+1).
+
+Workload recipes (shapes of the paper's benchmarks, Sec. 7.1):
+  * HPCG 27-point: b = A * ones, x0 = 0 (no random numbers).
+  * variable-kappa diffusion: log kappa = iid N(0,1) per cell, smoothed by a
+    separable Gaussian (sigma = 4 cells, taps -12..12, periodic wrap),
+    rescaled to unit marginal variance; kappa = exp(log kappa).
+  * NPB-LU-shaped block SSOR: D_p = U(-1,1)^{5x5} + 10 I, L/U couplings
+    U(-0.1, 0.1)^{5x5}, rhs U(-1,1), omega = 1.2.
+  * batched problems: cube sides drawn from {32, 48, 64, 96, 128}.
+"""
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+BASE_SEED = 13304
+
+STREAM_KAPPA = 1
+STREAM_D = 2
+STREAM_L = 3
+STREAM_U = 4
+STREAM_RHS = 5
+STREAM_TARGET = 6
+STREAM_VEC = 7
+STREAM_SIDES = 8
+
+BATCH_SIDES = (32, 48, 64, 96, 128)
+
+
+def _mix(z):
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def _key(seed, stream):
+    with np.errstate(over="ignore"):
+        s = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) * GAMMA
+    return _mix(s ^ (np.uint64(stream) << np.uint64(32)))
+
+
+def raw_u64(seed, stream, n, start=0):
+    """n raw 64-bit outputs of stream (seed, stream), elements start..start+n-1."""
+    key = _key(seed, stream)
+    i = np.arange(start + 1, start + n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix(key + i * GAMMA)
+
+
+def uniform(seed, stream, n, start=0, chunk=1 << 24):
+    """n uniforms in [0, 1) (53-bit), FP64."""
+    out = np.empty(n, dtype=np.float64)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        v = raw_u64(seed, stream, b - a, start + a)
+        out[a:b] = (v >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return out
+
+
+def normal(seed, stream, n):
+    """n standard normals by Box-Muller on the uniform pairs (2i, 2i+1)."""
+    u = uniform(seed, stream, 2 * n)
+    u1 = u[0::2]
+    u2 = u[1::2]
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def gaussian_taps(sigma=4.0, half_width=12):
+    k = np.arange(-half_width, half_width + 1, dtype=np.float64)
+    g = np.exp(-0.5 * (k / sigma) ** 2)
+    return g / g.sum()
+
+
+def kappa_field(n, seed=BASE_SEED, sigma=4.0, half_width=12, shape=None):
+    """kappa = exp(smoothed unit-variance Gaussian field); shape (nz, ny, nx)."""
+    from scipy.ndimage import convolve1d
+
+    shape = (n, n, n) if shape is None else tuple(shape)
+    f = normal(seed, STREAM_KAPPA, int(np.prod(shape))).reshape(shape)
+    g = gaussian_taps(sigma, half_width)
+    for ax in range(3):
+        f = convolve1d(f, g, axis=ax, mode="wrap")
+    f /= np.sum(g * g) ** 1.5
+    return np.exp(f)
+
+
+def block_ssor_inputs(n, seed=BASE_SEED, shape=None):
+    """(D, L, U, rhs) for the NPB-LU-shaped block problem on an n^3 grid.
+
+    D: (nz, ny, nx, 5, 5); L, U: (nz, ny, nx, 3, 5, 5) with index 0/1/2 the
+    x/y/z coupling; rhs: (nz, ny, nx, 5).
+    """
+    shape = (n, n, n) if shape is None else tuple(shape)
+    npts = int(np.prod(shape))
+    D = (2.0 * uniform(seed, STREAM_D, npts * 25) - 1.0).reshape(shape + (5, 5))
+    D += 10.0 * np.eye(5)
+    L = (0.2 * uniform(seed, STREAM_L, npts * 75) - 0.1).reshape(shape + (3, 5, 5))
+    U = (0.2 * uniform(seed, STREAM_U, npts * 75) - 0.1).reshape(shape + (3, 5, 5))
+    rhs = (2.0 * uniform(seed, STREAM_RHS, npts * 5) - 1.0).reshape(shape + (5,))
+    return D, L, U, rhs
+
+
+def target(shape, seed=BASE_SEED):
+    """u_target ~ U(0, 1)."""
+    return uniform(seed, STREAM_TARGET, int(np.prod(shape))).reshape(shape)
+
+
+def random_vector(shape, seed=BASE_SEED, stream_offset=0, lo=-1.0, hi=1.0):
+    """A U(lo, hi) test vector (stream STREAM_VEC + stream_offset)."""
+    u = uniform(seed, STREAM_VEC + 64 * stream_offset, int(np.prod(shape)))
+    return (lo + (hi - lo) * u).reshape(shape)
+
+
+def batch_sides(count=64, seed=BASE_SEED):
+    """Cube sides of the batched problems, drawn from BATCH_SIDES."""
+    u = uniform(seed, STREAM_SIDES, count)
+    return [BATCH_SIDES[int(v * len(BATCH_SIDES))] for v in u]

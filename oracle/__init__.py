@@ -1,0 +1,270 @@
+"""Serial CPU oracle for the Mat2Stencil solver hot path.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``; the library never imports it.
+It shares no code with the CUDA path.  Every routine is the plain definition
+of its step as serial loops in lexicographic order (z outermost, x fastest),
+in IEEE FP64 (the ``*_f32`` routines are the FP32-preconditioner form).
+
+Parity status: every function here is pinned by a ``-m "not gpu"`` test in
+``tests/test_oracle_pins.py`` (closed forms, invariants, brute force on tiny
+grids); none is "parity unpinned".
+
+Operator kinds (paper Sec. 4.2 row functions, Sec. 7.1 HPCG):
+  HPCG27 = 0  27-point, a_pp = 26, a_pq = -1, zero Dirichlet
+  KAPPA7 = 1  variable-coefficient 7-point diffusion, face kappa = mean
+"""
+import ctypes
+import numpy as np
+
+from . import build as _build
+
+HPCG27 = 0
+KAPPA7 = 1
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_i = ctypes.c_int
+_ll = ctypes.c_longlong
+_d = ctypes.c_double
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        sig = {
+            "or_apply": [_i, _i, _i, _i, _dp, _dp, _dp],
+            "or_gs_forward": [_i, _i, _i, _i, _dp, _dp, _dp],
+            "or_gs_backward": [_i, _i, _i, _i, _dp, _dp, _dp],
+            "or_symgs": [_i, _i, _i, _i, _dp, _dp, _dp, _i],
+            "or_gs_multicolor_forward": [_i, _i, _i, _i, _dp, _dp, _dp],
+            "or_restrict_residual": [_i, _i, _i, _i, _dp, _dp, _dp, _dp],
+            "or_prolong_add": [_i, _i, _i, _dp, _dp],
+            "or_coarsen_kappa": [_i, _i, _i, _dp, _dp],
+            "or_mg_vcycle": [_i, _i, _i, _i, _dp, _i, _dp, _dp],
+            "or_apply_f32": [_i, _i, _i, _i, _fp, _fp, _fp],
+            "or_symgs_f32": [_i, _i, _i, _i, _fp, _fp, _fp, _i],
+            "or_mg_vcycle_f32": [_i, _i, _i, _i, _dp, _i, _fp, _fp],
+            "or_dot": [_ll, _dp, _dp],
+            "or_pcg": [_i, _i, _i, _i, _dp, _i, _i, _dp, _dp, _i, _d, _i, _dp,
+                       ctypes.POINTER(_i)],
+            "or_kappa_grad": [_i, _i, _i, _dp, _dp, _dp],
+            "or_block_apply": [_i, _i, _i, _dp, _dp, _dp, _dp, _dp],
+            "or_block_residual": [_i, _i, _i, _dp, _dp, _dp, _dp, _dp, _dp],
+            "or_block_lower": [_i, _i, _i, _dp, _dp, _d, _dp, _dp],
+            "or_block_upper": [_i, _i, _i, _dp, _dp, _d, _dp, _dp],
+            "or_ssor": [_i, _i, _i, _dp, _dp, _dp, _d, _dp, _dp, _i],
+            "or_coarse_n": [_i],
+            "or_abi_version": [],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = None
+        L.or_dot.restype = _d
+        L.or_pcg.restype = _i
+        L.or_coarse_n.restype = _i
+        L.or_abi_version.restype = _i
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _p(a):
+    if a is None:
+        return None
+    if a.dtype == np.float64:
+        return a.ctypes.data_as(_dp)
+    if a.dtype == np.float32:
+        return a.ctypes.data_as(_fp)
+    raise TypeError(a.dtype)
+
+
+def _dims(shape):
+    nz, ny, nx = shape
+    return nx, ny, nz
+
+
+def coarse_n(n):
+    return lib().or_coarse_n(int(n))
+
+
+def apply(kind, x, kappa=None):
+    """y = A x (Sec. 4.3.1 SpMV); x has shape (nz, ny, nx)."""
+    x = _f64(x)
+    y = np.empty_like(x)
+    k = None if kappa is None else _f64(kappa)
+    lib().or_apply(kind, *_dims(x.shape), _p(k), _p(x), _p(y))
+    return y
+
+
+def gs_forward(kind, b, x, kappa=None):
+    """One lexicographic forward Gauss-Seidel sweep; returns the new x."""
+    b = _f64(b)
+    x = _f64(x).copy()
+    k = None if kappa is None else _f64(kappa)
+    lib().or_gs_forward(kind, *_dims(b.shape), _p(k), _p(b), _p(x))
+    return x
+
+
+def gs_backward(kind, b, x, kappa=None):
+    b = _f64(b)
+    x = _f64(x).copy()
+    k = None if kappa is None else _f64(kappa)
+    lib().or_gs_backward(kind, *_dims(b.shape), _p(k), _p(b), _p(x))
+    return x
+
+
+def symgs(kind, b, x, sweeps=1, kappa=None):
+    """`sweeps` symmetric GS (forward then backward each); returns new x."""
+    b = _f64(b)
+    x = _f64(x).copy()
+    k = None if kappa is None else _f64(kappa)
+    lib().or_symgs(kind, *_dims(b.shape), _p(k), _p(b), _p(x), int(sweeps))
+    return x
+
+
+def gs_multicolor_forward(kind, b, x, kappa=None):
+    """Negative control only: 8-colour reordered GS sweep (not the method)."""
+    b = _f64(b)
+    x = _f64(x).copy()
+    k = None if kappa is None else _f64(kappa)
+    lib().or_gs_multicolor_forward(kind, *_dims(b.shape), _p(k), _p(b), _p(x))
+    return x
+
+
+def restrict_residual(kind, r, z, kappa=None):
+    r = _f64(r)
+    z = _f64(z)
+    nz, ny, nx = r.shape
+    rc = np.empty((coarse_n(nz), coarse_n(ny), coarse_n(nx)))
+    k = None if kappa is None else _f64(kappa)
+    lib().or_restrict_residual(kind, nx, ny, nz, _p(k), _p(r), _p(z), _p(rc))
+    return rc
+
+
+def prolong_add(zc, z):
+    z = _f64(z).copy()
+    zc = _f64(zc)
+    nz, ny, nx = z.shape
+    lib().or_prolong_add(nx, ny, nz, _p(zc), _p(z))
+    return z
+
+
+def coarsen_kappa(kappa):
+    kappa = _f64(kappa)
+    nz, ny, nx = kappa.shape
+    kc = np.empty((coarse_n(nz), coarse_n(ny), coarse_n(nx)))
+    lib().or_coarsen_kappa(nx, ny, nz, _p(kappa), _p(kc))
+    return kc
+
+
+def mg_vcycle(kind, r, levels, kappa=None):
+    r = _f64(r)
+    z = np.empty_like(r)
+    k = None if kappa is None else _f64(kappa)
+    lib().or_mg_vcycle(kind, *_dims(r.shape), _p(k), int(levels), _p(r), _p(z))
+    return z
+
+
+def apply_f32(kind, x, kappa32=None):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    k = None if kappa32 is None else np.ascontiguousarray(kappa32, dtype=np.float32)
+    lib().or_apply_f32(kind, *_dims(x.shape), _p(k), _p(x), _p(y))
+    return y
+
+
+def symgs_f32(kind, b, x, sweeps=1, kappa32=None):
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32).copy()
+    k = None if kappa32 is None else np.ascontiguousarray(kappa32, dtype=np.float32)
+    lib().or_symgs_f32(kind, *_dims(b.shape), _p(k), _p(b), _p(x), int(sweeps))
+    return x
+
+
+def mg_vcycle_f32(kind, r32, levels, kappa=None):
+    """FP32 V-cycle; kappa is the FP64 fine kappa (FP32 copies derived inside)."""
+    r32 = np.ascontiguousarray(r32, dtype=np.float32)
+    z = np.empty_like(r32)
+    k = None if kappa is None else _f64(kappa)
+    lib().or_mg_vcycle_f32(kind, *_dims(r32.shape), _p(k), int(levels), _p(r32), _p(z))
+    return z
+
+
+def dot(a, b):
+    a = _f64(a).ravel()
+    b = _f64(b).ravel()
+    return lib().or_dot(a.size, _p(a), _p(b))
+
+
+def pcg(kind, b, levels, kappa=None, max_iters=50, rtol=0.0, fixed_iters=True,
+        precond_f32=False):
+    """PCG from x0 = 0.  Returns (x, iters, resid_hist, status)."""
+    b = _f64(b)
+    x = np.empty_like(b)
+    hist = np.zeros(max_iters + 1)
+    it = _i(0)
+    k = None if kappa is None else _f64(kappa)
+    st = lib().or_pcg(kind, *_dims(b.shape), _p(k), int(levels), int(bool(precond_f32)),
+                      _p(b), _p(x), int(max_iters), float(rtol), int(bool(fixed_iters)),
+                      _p(hist), ctypes.byref(it))
+    return x, it.value, hist[: it.value + 1].copy(), st
+
+
+def kappa_grad(u, lam):
+    u = _f64(u)
+    lam = _f64(lam)
+    g = np.empty_like(u)
+    lib().or_kappa_grad(*_dims(u.shape), _p(u), _p(lam), _p(g))
+    return g
+
+
+def block_apply(D, L, U, u):
+    u = _f64(u)
+    y = np.empty_like(u)
+    nz, ny, nx, _ = u.shape
+    lib().or_block_apply(nx, ny, nz, _p(_f64(D)), _p(_f64(L)), _p(_f64(U)), _p(u), _p(y))
+    return y
+
+
+def block_residual(D, L, U, b, u):
+    u = _f64(u)
+    b = _f64(b)
+    r = np.empty_like(u)
+    nz, ny, nx, _ = u.shape
+    lib().or_block_residual(nx, ny, nz, _p(_f64(D)), _p(_f64(L)), _p(_f64(U)), _p(b),
+                            _p(u), _p(r))
+    return r
+
+
+def block_lower(D, L, omega, r):
+    r = _f64(r)
+    v = np.empty_like(r)
+    nz, ny, nx, _ = r.shape
+    lib().or_block_lower(nx, ny, nz, _p(_f64(D)), _p(_f64(L)), float(omega), _p(r), _p(v))
+    return v
+
+
+def block_upper(D, U, omega, v):
+    v = _f64(v)
+    w = np.empty_like(v)
+    nz, ny, nx, _ = v.shape
+    lib().or_block_upper(nx, ny, nz, _p(_f64(D)), _p(_f64(U)), float(omega), _p(v), _p(w))
+    return w
+
+
+def ssor(D, L, U, omega, b, u, n_iters):
+    b = _f64(b)
+    u = _f64(u).copy()
+    nz, ny, nx, _ = u.shape
+    lib().or_ssor(nx, ny, nz, _p(_f64(D)), _p(_f64(L)), _p(_f64(U)), float(omega),
+                  _p(b), _p(u), int(n_iters))
+    return u

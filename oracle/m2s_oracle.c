@@ -1,0 +1,702 @@
+/*
+ * m2s_oracle.c -- serial CPU oracle for the matrix-free structured-grid
+ * solver hot path of Mat2Stencil (arXiv 2204.13304).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py load this library.  It shares no code, header,
+ * table or helper with the CUDA library, and neither side includes the other.
+ *
+ * Every routine is the plain definition of the step, written as serial loops
+ * over the grid in lexicographic order, in IEEE double precision (the FP32
+ * preconditioner routines, suffix _f32, are the same loops in float because
+ * that form fixes FP32 by definition).  Build with -ffp-contract=off so that
+ * no a*b+c is fused behind our back (results are then identical on x86-64 and
+ * aarch64).
+ *
+ * Conventions
+ *   grid      nx, ny, nz points; point (x, y, z) has flat index
+ *             p = (z*ny + y)*nx + x  (x fastest, z outermost).
+ *   order     "lexicographic" = increasing p, i.e. z outermost, then y, then
+ *             x -- the dictionary order of the domain loops (Sec. 4.3, the
+ *             SymGS routine's loops; Sec. 6.1.1 "lexicographical execution
+ *             order" within each thread).
+ *   boundary  neighbours outside [0,nx)x[0,ny)x[0,nz) are dropped (zero
+ *             Dirichlet), as in the HPCG operator.
+ *   kinds     M2SO_HPCG27 = 0 : a_pp = 26, a_pq = -1 for every in-domain
+ *                               neighbour of the 3x3x3 box (HPCG's operator).
+ *             M2SO_KAPPA7 = 1 : variable-coefficient 7-point diffusion,
+ *                               (A u)_p = sum_faces k_f (u_p - u_q), with the
+ *                               face coefficient the average of the two cell
+ *                               values (the averaging matrix A = [1/2 1/2] of
+ *                               Sec. 4.1); at a boundary face k_f = k_p and
+ *                               u_q = 0.
+ * Citations name the paper's section / equation / definition.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef long long i64;
+
+#define M2SO_HPCG27 0
+#define M2SO_KAPPA7 1
+
+static i64 pidx(int nx, int ny, int x, int y, int z) {
+    return ((i64)z * ny + y) * nx + x;
+}
+static int inside(int nx, int ny, int nz, int x, int y, int z) {
+    return x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Row functions (Sec. 4.2: a sparse matrix is a function from a row index  */
+/* to its list of (column, value) non-zeros).  Non-zeros come out in        */
+/* increasing column order; the diagonal is included.                      */
+/* ------------------------------------------------------------------------ */
+
+/* HPCG 27-point row: 26 on the diagonal, -1 for each in-domain neighbour. */
+static int row_hpcg27(int nx, int ny, int nz, int x, int y, int z,
+                      i64* col, double* val) {
+    int c = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int qx = x + dx, qy = y + dy, qz = z + dz;
+                if (!inside(nx, ny, nz, qx, qy, qz)) continue;
+                col[c] = pidx(nx, ny, qx, qy, qz);
+                val[c] = (dx == 0 && dy == 0 && dz == 0) ? 26.0 : -1.0;
+                ++c;
+            }
+    return c;
+}
+
+/* Face coefficient between cell p and its neighbour q (interior face):
+ * the arithmetic mean (averaging matrix A of Sec. 4.1). */
+static double face_kappa(double kp, double kq) { return 0.5 * (kp + kq); }
+
+/* Variable-kappa 7-point row.  For each of the 6 faces of cell p:
+ *   interior face to q:  diagonal += k_f, entry (p,q) = -k_f, k_f = (k_p+k_q)/2
+ *   boundary face:       diagonal += k_p (the ghost value u_q is 0).
+ * The diagonal accumulates its six face terms in the fixed face order
+ * -z, -y, -x, +x, +y, +z. */
+static int row_kappa7(int nx, int ny, int nz, const double* kappa,
+                      int x, int y, int z, i64* col, double* val) {
+    static const int off[6][3] = {{0, 0, -1}, {0, -1, 0}, {-1, 0, 0},
+                                  {1, 0, 0},  {0, 1, 0},  {0, 0, 1}};
+    i64 p = pidx(nx, ny, x, y, z);
+    double kp = kappa[p];
+    double diag = 0.0;
+    double offv[6];
+    i64 offc[6];
+    int has[6];
+    for (int f = 0; f < 6; ++f) {
+        int qx = x + off[f][0], qy = y + off[f][1], qz = z + off[f][2];
+        if (inside(nx, ny, nz, qx, qy, qz)) {
+            i64 q = pidx(nx, ny, qx, qy, qz);
+            double kf = face_kappa(kp, kappa[q]);
+            diag += kf;
+            offv[f] = -kf;
+            offc[f] = q;
+            has[f] = 1;
+        } else {
+            diag += kp;
+            has[f] = 0;
+        }
+    }
+    int c = 0;
+    for (int f = 0; f < 3; ++f)
+        if (has[f]) { col[c] = offc[f]; val[c] = offv[f]; ++c; }
+    col[c] = p; val[c] = diag; ++c;
+    for (int f = 3; f < 6; ++f)
+        if (has[f]) { col[c] = offc[f]; val[c] = offv[f]; ++c; }
+    return c;
+}
+
+static int row_of(int kind, int nx, int ny, int nz, const double* kappa,
+                  int x, int y, int z, i64* col, double* val) {
+    if (kind == M2SO_HPCG27) return row_hpcg27(nx, ny, nz, x, y, z, col, val);
+    return row_kappa7(nx, ny, nz, kappa, x, y, z, col, val);
+}
+
+/* ------------------------------------------------------------------------ */
+/* SpMV (Sec. 4.3.1): y_p = sum over the non-zeros of row p of a_pq * x_q,  */
+/* in the row's column order.                                              */
+/* ------------------------------------------------------------------------ */
+void or_apply(int kind, int nx, int ny, int nz, const double* kappa,
+              const double* x, double* y) {
+    i64 col[27];
+    double val[27];
+    for (int z = 0; z < nz; ++z)
+        for (int yy = 0; yy < ny; ++yy)
+            for (int xx = 0; xx < nx; ++xx) {
+                int c = row_of(kind, nx, ny, nz, kappa, xx, yy, z, col, val);
+                double s = 0.0;
+                for (int k = 0; k < c; ++k) s += val[k] * x[col[k]];
+                y[pidx(nx, ny, xx, yy, z)] = s;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Seidel sweeps (Sec. 4.3.3, the SymGS routine; the loop reads and   */
+/* writes the same vector, so a point sees the new values of the points     */
+/* visited before it and the old values of the others).                    */
+/*   x_p <- (b_p - sum_{q != p} a_pq x_q) / a_pp                           */
+/* forward  : p increasing (lexicographic)                                 */
+/* backward : p decreasing                                                 */
+/* ------------------------------------------------------------------------ */
+static void gs_point(int kind, int nx, int ny, int nz, const double* kappa,
+                     const double* b, double* x, int xx, int yy, int z) {
+    i64 col[27];
+    double val[27];
+    i64 p = pidx(nx, ny, xx, yy, z);
+    int c = row_of(kind, nx, ny, nz, kappa, xx, yy, z, col, val);
+    double s = b[p], diag = 0.0;
+    for (int k = 0; k < c; ++k) {
+        if (col[k] == p) { diag = val[k]; continue; }
+        s -= val[k] * x[col[k]];
+    }
+    x[p] = s / diag;
+}
+
+void or_gs_forward(int kind, int nx, int ny, int nz, const double* kappa,
+                   const double* b, double* x) {
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int xx = 0; xx < nx; ++xx)
+                gs_point(kind, nx, ny, nz, kappa, b, x, xx, y, z);
+}
+
+void or_gs_backward(int kind, int nx, int ny, int nz, const double* kappa,
+                    const double* b, double* x) {
+    for (int z = nz - 1; z >= 0; --z)
+        for (int y = ny - 1; y >= 0; --y)
+            for (int xx = nx - 1; xx >= 0; --xx)
+                gs_point(kind, nx, ny, nz, kappa, b, x, xx, y, z);
+}
+
+/* One symmetric Gauss-Seidel = one forward sweep then one backward sweep. */
+void or_symgs(int kind, int nx, int ny, int nz, const double* kappa,
+              const double* b, double* x, int n_sym_sweeps) {
+    for (int s = 0; s < n_sym_sweeps; ++s) {
+        or_gs_forward(kind, nx, ny, nz, kappa, b, x);
+        or_gs_backward(kind, nx, ny, nz, kappa, b, x);
+    }
+}
+
+/* Negative control for the ordering tests (NOT the method): the same update
+ * applied colour by colour, 8 colours given by the parities of (x, y, z),
+ * colours visited in the order 0..7 and each colour's points in increasing p.
+ * Its results differ from the lexicographic sweep, which is what the tests
+ * use to show that a reordered sweep would be caught. */
+void or_gs_multicolor_forward(int kind, int nx, int ny, int nz,
+                              const double* kappa, const double* b, double* x) {
+    for (int color = 0; color < 8; ++color)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int xx = 0; xx < nx; ++xx) {
+                    int cc = (xx & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+                    if (cc != color) continue;
+                    gs_point(kind, nx, ny, nz, kappa, b, x, xx, y, z);
+                }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometric multigrid pieces (Sec. 4.2 "HPCG Prolong" matrix with its      */
+/* periodic sparsity pattern: coarse point i <-> fine point 2i, coarsening  */
+/* by two per dimension; restriction is its transpose).                    */
+/* ------------------------------------------------------------------------ */
+
+/* coarse extent of a fine extent n: the fine points 0, 2, 4, ... */
+int or_coarse_n(int n) { return (n + 1) / 2; }
+
+/* rc_i = r_{2i} - (A z)_{2i}: residual of the fine level injected at the
+ * even fine points. */
+void or_restrict_residual(int kind, int nx, int ny, int nz, const double* kappa,
+                          const double* r, const double* z, double* rc) {
+    i64 n = (i64)nx * ny * nz;
+    double* az = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    or_apply(kind, nx, ny, nz, kappa, z, az);
+    int cx = or_coarse_n(nx), cy = or_coarse_n(ny), cz = or_coarse_n(nz);
+    for (int k = 0; k < cz; ++k)
+        for (int j = 0; j < cy; ++j)
+            for (int i = 0; i < cx; ++i) {
+                i64 f = pidx(nx, ny, 2 * i, 2 * j, 2 * k);
+                rc[pidx(cx, cy, i, j, k)] = r[f] - az[f];
+            }
+    free(az);
+}
+
+/* z_{2i} += zc_i; the other fine points are unchanged (prolongation = the
+ * transpose of injection). */
+void or_prolong_add(int nx, int ny, int nz, const double* zc, double* z) {
+    int cx = or_coarse_n(nx), cy = or_coarse_n(ny), cz = or_coarse_n(nz);
+    for (int k = 0; k < cz; ++k)
+        for (int j = 0; j < cy; ++j)
+            for (int i = 0; i < cx; ++i)
+                z[pidx(nx, ny, 2 * i, 2 * j, 2 * k)] += zc[pidx(cx, cy, i, j, k)];
+}
+
+/* Coarse kappa: mean of the fine cells {2i, 2i+1} x {2j, 2j+1} x {2k, 2k+1}
+ * that lie inside the fine grid. */
+void or_coarsen_kappa(int nx, int ny, int nz, const double* kf, double* kc) {
+    int cx = or_coarse_n(nx), cy = or_coarse_n(ny), cz = or_coarse_n(nz);
+    for (int k = 0; k < cz; ++k)
+        for (int j = 0; j < cy; ++j)
+            for (int i = 0; i < cx; ++i) {
+                double s = 0.0;
+                int cnt = 0;
+                for (int dz = 0; dz < 2; ++dz)
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) {
+                            int x = 2 * i + dx, y = 2 * j + dy, z = 2 * k + dz;
+                            if (!inside(nx, ny, nz, x, y, z)) continue;
+                            s += kf[pidx(nx, ny, x, y, z)];
+                            ++cnt;
+                        }
+                kc[pidx(cx, cy, i, j, k)] = s / (double)cnt;
+            }
+}
+
+/* V-cycle MG(l, r) -> z  (levels = total number of levels, >= 1):
+ *   z = 0
+ *   coarsest level: one symmetric Gauss-Seidel of A_l z = r
+ *   otherwise:      symmetric GS (pre-smoothing); rc = R (r - A_l z);
+ *                   zc = MG(l+1, rc); z += P zc; symmetric GS (post).
+ * The coarse operator is the same stencil rediscretised on the coarse grid
+ * (27-point: same coefficients; kappa: the coarsened kappa). */
+void or_mg_vcycle(int kind, int nx, int ny, int nz, const double* kappa,
+                  int levels, const double* r, double* z) {
+    i64 n = (i64)nx * ny * nz;
+    for (i64 i = 0; i < n; ++i) z[i] = 0.0;
+    if (levels <= 1) {
+        or_symgs(kind, nx, ny, nz, kappa, r, z, 1);
+        return;
+    }
+    or_symgs(kind, nx, ny, nz, kappa, r, z, 1);
+    int cx = or_coarse_n(nx), cy = or_coarse_n(ny), cz = or_coarse_n(nz);
+    i64 nc = (i64)cx * cy * cz;
+    double* rc = (double*)malloc(sizeof(double) * (size_t)nc);
+    double* zc = (double*)malloc(sizeof(double) * (size_t)nc);
+    double* kc = NULL;
+    if (kind == M2SO_KAPPA7) {
+        kc = (double*)malloc(sizeof(double) * (size_t)nc);
+        or_coarsen_kappa(nx, ny, nz, kappa, kc);
+    }
+    or_restrict_residual(kind, nx, ny, nz, kappa, r, z, rc);
+    or_mg_vcycle(kind, cx, cy, cz, kc, levels - 1, rc, zc);
+    or_prolong_add(nx, ny, nz, zc, z);
+    or_symgs(kind, nx, ny, nz, kappa, r, z, 1);
+    free(rc);
+    free(zc);
+    free(kc);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same V-cycle entirely in FP32 (the FP32-preconditioner form).  The   */
+/* FP32 kappa of every level is the FP32 rounding of the FP64 kappa of that */
+/* level; face averages and all sums are then taken in float.              */
+/* ------------------------------------------------------------------------ */
+static int row_of_f32(int kind, int nx, int ny, int nz, const float* kappa,
+                      int x, int y, int z, i64* col, float* val) {
+    if (kind == M2SO_HPCG27) {
+        int c = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int qx = x + dx, qy = y + dy, qz = z + dz;
+                    if (!inside(nx, ny, nz, qx, qy, qz)) continue;
+                    col[c] = pidx(nx, ny, qx, qy, qz);
+                    val[c] = (dx == 0 && dy == 0 && dz == 0) ? 26.0f : -1.0f;
+                    ++c;
+                }
+        return c;
+    }
+    static const int off[6][3] = {{0, 0, -1}, {0, -1, 0}, {-1, 0, 0},
+                                  {1, 0, 0},  {0, 1, 0},  {0, 0, 1}};
+    i64 p = pidx(nx, ny, x, y, z);
+    float kp = kappa[p], diag = 0.0f, offv[6];
+    i64 offc[6];
+    int has[6];
+    for (int f = 0; f < 6; ++f) {
+        int qx = x + off[f][0], qy = y + off[f][1], qz = z + off[f][2];
+        if (inside(nx, ny, nz, qx, qy, qz)) {
+            i64 q = pidx(nx, ny, qx, qy, qz);
+            float kf = 0.5f * (kp + kappa[q]);
+            diag += kf;
+            offv[f] = -kf;
+            offc[f] = q;
+            has[f] = 1;
+        } else {
+            diag += kp;
+            has[f] = 0;
+        }
+    }
+    int c = 0;
+    for (int f = 0; f < 3; ++f)
+        if (has[f]) { col[c] = offc[f]; val[c] = offv[f]; ++c; }
+    col[c] = p; val[c] = diag; ++c;
+    for (int f = 3; f < 6; ++f)
+        if (has[f]) { col[c] = offc[f]; val[c] = offv[f]; ++c; }
+    return c;
+}
+
+void or_apply_f32(int kind, int nx, int ny, int nz, const float* kappa,
+                  const float* x, float* y) {
+    i64 col[27];
+    float val[27];
+    for (int z = 0; z < nz; ++z)
+        for (int yy = 0; yy < ny; ++yy)
+            for (int xx = 0; xx < nx; ++xx) {
+                int c = row_of_f32(kind, nx, ny, nz, kappa, xx, yy, z, col, val);
+                float s = 0.0f;
+                for (int k = 0; k < c; ++k) s += val[k] * x[col[k]];
+                y[pidx(nx, ny, xx, yy, z)] = s;
+            }
+}
+
+static void gs_point_f32(int kind, int nx, int ny, int nz, const float* kappa,
+                         const float* b, float* x, int xx, int yy, int z) {
+    i64 col[27];
+    float val[27];
+    i64 p = pidx(nx, ny, xx, yy, z);
+    int c = row_of_f32(kind, nx, ny, nz, kappa, xx, yy, z, col, val);
+    float s = b[p], diag = 0.0f;
+    for (int k = 0; k < c; ++k) {
+        if (col[k] == p) { diag = val[k]; continue; }
+        s -= val[k] * x[col[k]];
+    }
+    x[p] = s / diag;
+}
+
+void or_symgs_f32(int kind, int nx, int ny, int nz, const float* kappa,
+                  const float* b, float* x, int n_sym_sweeps) {
+    for (int s = 0; s < n_sym_sweeps; ++s) {
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int xx = 0; xx < nx; ++xx)
+                    gs_point_f32(kind, nx, ny, nz, kappa, b, x, xx, y, z);
+        for (int z = nz - 1; z >= 0; --z)
+            for (int y = ny - 1; y >= 0; --y)
+                for (int xx = nx - 1; xx >= 0; --xx)
+                    gs_point_f32(kind, nx, ny, nz, kappa, b, x, xx, y, z);
+    }
+}
+
+/* kappa64 is the FP64 kappa of this level; the FP32 copy is derived here. */
+static void mg_vcycle_f32_rec(int kind, int nx, int ny, int nz,
+                              const double* kappa64, int levels,
+                              const float* r, float* z) {
+    i64 n = (i64)nx * ny * nz;
+    float* k32 = NULL;
+    if (kind == M2SO_KAPPA7) {
+        k32 = (float*)malloc(sizeof(float) * (size_t)n);
+        for (i64 i = 0; i < n; ++i) k32[i] = (float)kappa64[i];
+    }
+    for (i64 i = 0; i < n; ++i) z[i] = 0.0f;
+    or_symgs_f32(kind, nx, ny, nz, k32, r, z, 1);
+    if (levels > 1) {
+        int cx = or_coarse_n(nx), cy = or_coarse_n(ny), cz = or_coarse_n(nz);
+        i64 nc = (i64)cx * cy * cz;
+        float* az = (float*)malloc(sizeof(float) * (size_t)n);
+        float* rc = (float*)malloc(sizeof(float) * (size_t)nc);
+        float* zc = (float*)malloc(sizeof(float) * (size_t)nc);
+        double* kc = NULL;
+        if (kind == M2SO_KAPPA7) {
+            kc = (double*)malloc(sizeof(double) * (size_t)nc);
+            or_coarsen_kappa(nx, ny, nz, kappa64, kc);
+        }
+        or_apply_f32(kind, nx, ny, nz, k32, z, az);
+        for (int k = 0; k < cz; ++k)
+            for (int j = 0; j < cy; ++j)
+                for (int i = 0; i < cx; ++i) {
+                    i64 f = pidx(nx, ny, 2 * i, 2 * j, 2 * k);
+                    rc[pidx(cx, cy, i, j, k)] = r[f] - az[f];
+                }
+        mg_vcycle_f32_rec(kind, cx, cy, cz, kc, levels - 1, rc, zc);
+        for (int k = 0; k < cz; ++k)
+            for (int j = 0; j < cy; ++j)
+                for (int i = 0; i < cx; ++i)
+                    z[pidx(nx, ny, 2 * i, 2 * j, 2 * k)] += zc[pidx(cx, cy, i, j, k)];
+        or_symgs_f32(kind, nx, ny, nz, k32, r, z, 1);
+        free(az);
+        free(rc);
+        free(zc);
+        free(kc);
+    }
+    free(k32);
+}
+
+void or_mg_vcycle_f32(int kind, int nx, int ny, int nz, const double* kappa64,
+                      int levels, const float* r, float* z) {
+    mg_vcycle_f32_rec(kind, nx, ny, nz, kappa64, levels, r, z);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Compensated dot product Dot2 (Ogita, Rump & Oishi, "Accurate sum and dot */
+/* product", SIAM J. Sci. Comput. 26(6), 2005, Alg. 5.3): the result is as */
+/* accurate as if computed in twice the working precision and then rounded, */
+/* so it does not depend on the summation order to within ~1 ulp.  It is an */
+/* evaluation of the plain definition sum_i a_i b_i, not a different one.   */
+/* ------------------------------------------------------------------------ */
+static void two_sum(double a, double b, double* s, double* e) {
+    double x = a + b;
+    double z = x - a;
+    *s = x;
+    *e = (a - (x - z)) + (b - z);
+}
+static void two_prod(double a, double b, double* p, double* e) {
+    double x = a * b;
+    *p = x;
+    *e = fma(a, b, -x);
+}
+double or_dot(i64 n, const double* a, const double* b) {
+    if (n <= 0) return 0.0;
+    double p, s, h, r, q;
+    two_prod(a[0], b[0], &p, &s);
+    for (i64 i = 1; i < n; ++i) {
+        two_prod(a[i], b[i], &h, &r);
+        two_sum(p, h, &p, &q);
+        s = s + (q + r);
+    }
+    return p + s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Preconditioned conjugate gradients, x0 = 0, r0 = b:                      */
+/*   z = M^-1 r; rho = r.z; p = z (k = 1) or p = z + (rho/rho_old) p;       */
+/*   q = A p; alpha = rho / (p.q); x += alpha p; r -= alpha q; |r|.         */
+/* levels = 0: no preconditioner (M = I); levels >= 1: one V-cycle with    */
+/* that many levels (levels = 1 is one symmetric GS from z = 0).           */
+/* precond_f32 = 1: the FP32 V-cycle, z = double(V32(float(r))), inside     */
+/* the flexible (Polak-Ribiere) variant                                    */
+/*   beta = (r_k.z_k - r_k.z_{k-1}) / rho_{k-1}.                           */
+/* The residual, the dot products and the update of x stay in FP64.        */
+/* fixed_iters = 1 runs exactly max_iters iterations; otherwise it stops    */
+/* when |r|/|b| <= rtol.  resid_hist[k] = |r_k| (k = 0..iters).             */
+/* Returns 0 on success, 1 if not converged, 2 on breakdown (p.q <= 0 or a  */
+/* non-finite value).                                                      */
+/* ------------------------------------------------------------------------ */
+int or_pcg(int kind, int nx, int ny, int nz, const double* kappa, int levels,
+           int precond_f32, const double* b, double* x, int max_iters,
+           double rtol, int fixed_iters, double* resid_hist, int* iters_out) {
+    i64 n = (i64)nx * ny * nz;
+    size_t bytes = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    double* r = (double*)malloc(bytes);
+    double* z = (double*)malloc(bytes);
+    double* zold = (double*)malloc(bytes);
+    double* p = (double*)malloc(bytes);
+    double* q = (double*)malloc(bytes);
+    float* r32 = NULL;
+    float* z32 = NULL;
+    if (precond_f32) {
+        r32 = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+        z32 = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    }
+    for (i64 i = 0; i < n; ++i) { x[i] = 0.0; r[i] = b[i]; zold[i] = 0.0; }
+    double nb = sqrt(or_dot(n, b, b));
+    double nr = nb;
+    if (resid_hist) resid_hist[0] = nr;
+    double rho_old = 0.0;
+    int k = 0, status = 1;
+    if (nb == 0.0) { status = 0; goto done; }
+    for (k = 1; k <= max_iters; ++k) {
+        if (levels <= 0) {
+            for (i64 i = 0; i < n; ++i) z[i] = r[i];
+        } else if (precond_f32) {
+            for (i64 i = 0; i < n; ++i) r32[i] = (float)r[i];
+            or_mg_vcycle_f32(kind, nx, ny, nz, kappa, levels, r32, z32);
+            for (i64 i = 0; i < n; ++i) z[i] = (double)z32[i];
+        } else {
+            or_mg_vcycle(kind, nx, ny, nz, kappa, levels, r, z);
+        }
+        double rho = or_dot(n, r, z);
+        if (k == 1) {
+            for (i64 i = 0; i < n; ++i) p[i] = z[i];
+        } else {
+            double beta;
+            if (precond_f32) beta = (rho - or_dot(n, r, zold)) / rho_old;
+            else beta = rho / rho_old;
+            for (i64 i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        }
+        or_apply(kind, nx, ny, nz, kappa, p, q);
+        double pq = or_dot(n, p, q);
+        if (!(pq > 0.0) || !isfinite(rho)) { status = 2; break; }
+        double alpha = rho / pq;
+        for (i64 i = 0; i < n; ++i) x[i] += alpha * p[i];
+        for (i64 i = 0; i < n; ++i) r[i] -= alpha * q[i];
+        nr = sqrt(or_dot(n, r, r));
+        if (resid_hist) resid_hist[k] = nr;
+        if (precond_f32) for (i64 i = 0; i < n; ++i) zold[i] = z[i];
+        rho_old = rho;
+        if (!isfinite(nr)) { status = 2; break; }
+        if (!fixed_iters && nr <= rtol * nb) { status = 0; break; }
+    }
+    if (k > max_iters) {
+        k = max_iters;
+        status = (fixed_iters || nr <= rtol * nb) ? 0 : 1;
+    }
+done:
+    if (iters_out) *iters_out = k;
+    free(r); free(z); free(zold); free(p); free(q); free(r32); free(z32);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the variable-kappa solve.  With A(kappa) u = b and            */
+/* L = 0.5 |u - u*|^2, the adjoint state is lambda = A^-T (u - u*) and      */
+/*   dL/dkappa_c = - lambda^T (dA/dkappa_c) u.                              */
+/* An interior face f between p and q with k_f = (k_p + k_q)/2 adds          */
+/* k_f (u_p - u_q) to row p and k_f (u_q - u_p) to row q, so it contributes */
+/* (1/2)(lambda_p - lambda_q)(u_p - u_q) for each of its two cells; a       */
+/* boundary face of cell c adds k_c u_c to row c, contributing lambda_c u_c.*/
+/* g_c = -[ sum_{interior faces of c} (1/2)(lambda_c - lambda_q)(u_c - u_q) */
+/*          + (number of boundary faces of c) * lambda_c u_c ]             */
+/* ------------------------------------------------------------------------ */
+void or_kappa_grad(int nx, int ny, int nz, const double* u, const double* lam,
+                   double* g) {
+    static const int off[6][3] = {{0, 0, -1}, {0, -1, 0}, {-1, 0, 0},
+                                  {1, 0, 0},  {0, 1, 0},  {0, 0, 1}};
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                i64 c = pidx(nx, ny, x, y, z);
+                double s = 0.0;
+                for (int f = 0; f < 6; ++f) {
+                    int qx = x + off[f][0], qy = y + off[f][1], qz = z + off[f][2];
+                    if (inside(nx, ny, nz, qx, qy, qz)) {
+                        i64 q = pidx(nx, ny, qx, qy, qz);
+                        s += 0.5 * (lam[c] - lam[q]) * (u[c] - u[q]);
+                    } else {
+                        s += lam[c] * u[c];
+                    }
+                }
+                g[c] = -s;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Block (5x5) SSOR in the shape of NPB-LU (Sec. 4.2.3 inner values as      */
+/* tensors: 5 unknowns per point; Sec. 1 / Sec. 4.3.3 name SSOR among the   */
+/* routines).  Per point p, D[p] is a 5x5 block, L[p][d] and U[p][d]        */
+/* (d = 0,1,2 for x,y,z) couple p to p - e_d and p + e_d.  Blocks are        */
+/* row-major; couplings that leave the domain are dropped.                 */
+/*   A u:   (A u)_p = D_p u_p + sum_d L_{p,d} u_{p-e_d} + U_{p,d} u_{p+e_d}  */
+/*   SSOR step (Saad, Iterative Methods, Sec. 4.1.2; M = (D+wL) D^-1        */
+/*   (D+wU) / (w(2-w)) ):                                                  */
+/*     r = b - A u                                                         */
+/*     lower, p increasing:  v_p = D_p^-1 (r_p - w sum_d L_{p,d} v_{p-e_d})  */
+/*     upper, p decreasing:  w_p = v_p - w D_p^-1 sum_d U_{p,d} w_{p+e_d}    */
+/*     u += w(2-w) w                                                       */
+/* This is exactly one forward block-SOR sweep followed by one backward     */
+/* block-SOR sweep on u (the tests check that identity).                   */
+/* 5x5 solves: Gaussian elimination without pivoting, natural order.       */
+/* ------------------------------------------------------------------------ */
+static void solve5(const double* Dm, const double* rhs, double* out) {
+    double a[5][5], t[5];
+    for (int i = 0; i < 5; ++i) {
+        for (int j = 0; j < 5; ++j) a[i][j] = Dm[i * 5 + j];
+        t[i] = rhs[i];
+    }
+    for (int k = 0; k < 5; ++k)
+        for (int i = k + 1; i < 5; ++i) {
+            double m = a[i][k] / a[k][k];
+            for (int j = k; j < 5; ++j) a[i][j] -= m * a[k][j];
+            t[i] -= m * t[k];
+        }
+    for (int i = 4; i >= 0; --i) {
+        double s = t[i];
+        for (int j = i + 1; j < 5; ++j) s -= a[i][j] * out[j];
+        out[i] = s / a[i][i];
+    }
+}
+
+static void matvec5_acc(const double* M, const double* v, double* acc) {
+    for (int i = 0; i < 5; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < 5; ++j) s += M[i * 5 + j] * v[j];
+        acc[i] += s;
+    }
+}
+
+/* A u for the block operator, blocks taken in increasing column order
+ * (z-1, y-1, x-1, p, x+1, y+1, z+1). */
+void or_block_apply(int nx, int ny, int nz, const double* D, const double* L,
+                    const double* U, const double* u, double* y) {
+    for (int z = 0; z < nz; ++z)
+        for (int yy = 0; yy < ny; ++yy)
+            for (int x = 0; x < nx; ++x) {
+                i64 p = pidx(nx, ny, x, yy, z);
+                double acc[5] = {0, 0, 0, 0, 0};
+                if (z > 0) matvec5_acc(L + (p * 3 + 2) * 25, u + pidx(nx, ny, x, yy, z - 1) * 5, acc);
+                if (yy > 0) matvec5_acc(L + (p * 3 + 1) * 25, u + pidx(nx, ny, x, yy - 1, z) * 5, acc);
+                if (x > 0) matvec5_acc(L + (p * 3 + 0) * 25, u + pidx(nx, ny, x - 1, yy, z) * 5, acc);
+                matvec5_acc(D + p * 25, u + p * 5, acc);
+                if (x < nx - 1) matvec5_acc(U + (p * 3 + 0) * 25, u + pidx(nx, ny, x + 1, yy, z) * 5, acc);
+                if (yy < ny - 1) matvec5_acc(U + (p * 3 + 1) * 25, u + pidx(nx, ny, x, yy + 1, z) * 5, acc);
+                if (z < nz - 1) matvec5_acc(U + (p * 3 + 2) * 25, u + pidx(nx, ny, x, yy, z + 1) * 5, acc);
+                for (int i = 0; i < 5; ++i) y[p * 5 + i] = acc[i];
+            }
+}
+
+void or_block_residual(int nx, int ny, int nz, const double* D, const double* L,
+                       const double* U, const double* b, const double* u,
+                       double* r) {
+    i64 n5 = (i64)nx * ny * nz * 5;
+    double* au = (double*)malloc(sizeof(double) * (size_t)(n5 > 0 ? n5 : 1));
+    or_block_apply(nx, ny, nz, D, L, U, u, au);
+    for (i64 i = 0; i < n5; ++i) r[i] = b[i] - au[i];
+    free(au);
+}
+
+void or_block_lower(int nx, int ny, int nz, const double* D, const double* L,
+                    double omega, const double* r, double* v) {
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                i64 p = pidx(nx, ny, x, y, z);
+                double acc[5] = {0, 0, 0, 0, 0}, t[5];
+                if (x > 0) matvec5_acc(L + (p * 3 + 0) * 25, v + pidx(nx, ny, x - 1, y, z) * 5, acc);
+                if (y > 0) matvec5_acc(L + (p * 3 + 1) * 25, v + pidx(nx, ny, x, y - 1, z) * 5, acc);
+                if (z > 0) matvec5_acc(L + (p * 3 + 2) * 25, v + pidx(nx, ny, x, y, z - 1) * 5, acc);
+                for (int i = 0; i < 5; ++i) t[i] = r[p * 5 + i] - omega * acc[i];
+                solve5(D + p * 25, t, v + p * 5);
+            }
+}
+
+void or_block_upper(int nx, int ny, int nz, const double* D, const double* U,
+                    double omega, const double* v, double* w) {
+    for (int z = nz - 1; z >= 0; --z)
+        for (int y = ny - 1; y >= 0; --y)
+            for (int x = nx - 1; x >= 0; --x) {
+                i64 p = pidx(nx, ny, x, y, z);
+                double acc[5] = {0, 0, 0, 0, 0}, t[5];
+                if (x < nx - 1) matvec5_acc(U + (p * 3 + 0) * 25, w + pidx(nx, ny, x + 1, y, z) * 5, acc);
+                if (y < ny - 1) matvec5_acc(U + (p * 3 + 1) * 25, w + pidx(nx, ny, x, y + 1, z) * 5, acc);
+                if (z < nz - 1) matvec5_acc(U + (p * 3 + 2) * 25, w + pidx(nx, ny, x, y, z + 1) * 5, acc);
+                solve5(D + p * 25, acc, t);
+                for (int i = 0; i < 5; ++i) w[p * 5 + i] = v[p * 5 + i] - omega * t[i];
+            }
+}
+
+/* n_iters SSOR steps on u (in place). */
+void or_ssor(int nx, int ny, int nz, const double* D, const double* L,
+             const double* U, double omega, const double* b, double* u,
+             int n_iters) {
+    i64 n5 = (i64)nx * ny * nz * 5;
+    size_t bytes = sizeof(double) * (size_t)(n5 > 0 ? n5 : 1);
+    double* r = (double*)malloc(bytes);
+    double* v = (double*)malloc(bytes);
+    double* w = (double*)malloc(bytes);
+    double scale = omega * (2.0 - omega);
+    for (int it = 0; it < n_iters; ++it) {
+        or_block_residual(nx, ny, nz, D, L, U, b, u, r);
+        or_block_lower(nx, ny, nz, D, L, omega, r, v);
+        or_block_upper(nx, ny, nz, D, U, omega, v, w);
+        for (i64 i = 0; i < n5; ++i) u[i] += scale * w[i];
+    }
+    free(r); free(v); free(w);
+}
+
+/* Version tag so the tests can check which oracle build is loaded. */
+int or_abi_version(void) { return 1; }

@@ -1,0 +1,558 @@
+"""Pins for the CPU oracle: each oracle routine is checked against something
+other than itself -- closed forms, invariants, special cases that reduce to a
+textbook routine, and brute-force dense linear algebra on tiny grids.
+
+Paper references: Sec. 4.3.1 (SpMV), Sec. 4.3.3 (SymGS and other routines
+with spatial dependence), Sec. 4.2 (HPCG prolongation matrix), Sec. 4.1
+(averaging matrix), Sec. 7.1 (HPCG, NPB-LU workloads).
+"""
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import m2s_inputs as gen
+import oracle
+
+H27 = oracle.HPCG27
+K7 = oracle.KAPPA7
+
+SHAPES_TINY = [(3, 4, 5), (5, 3, 4), (4, 5, 3), (1, 3, 2), (2, 1, 1)]
+
+
+def dense_from_apply(kind, shape, kappa=None):
+    """Dense A assembled column by column from the oracle SpMV."""
+    n = int(np.prod(shape))
+    A = np.zeros((n, n))
+    e = np.zeros(shape)
+    for j in range(n):
+        e.flat[j] = 1.0
+        A[:, j] = oracle.apply(kind, e, kappa).ravel()
+        e.flat[j] = 0.0
+    return A
+
+
+def rnd(shape, k=0):
+    return gen.random_vector(shape, seed=gen.BASE_SEED + 17 * k)
+
+
+def kappa_small(shape, k=0):
+    return np.exp(rnd(shape, 100 + k))
+
+
+# --------------------------------------------------------------------------
+# c2: 27-point operator
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", SHAPES_TINY + [(6, 6, 6)])
+def test_hpcg27_row_sums_closed_form(shape):
+    """(A 1)_p = 26 - #in-domain neighbours = 27 - prod_d (#valid offsets)."""
+    nz, ny, nx = shape
+    y = oracle.apply(H27, np.ones(shape))
+    for z, yy, x in itertools.product(range(nz), range(ny), range(nx)):
+        cnt = 1
+        for c, n in ((x, nx), (yy, ny), (z, nz)):
+            cnt *= sum(1 for d in (-1, 0, 1) if 0 <= c + d < n)
+        assert y[z, yy, x] == 27 - cnt
+
+
+def test_hpcg27_interior_corner_edge_face_values():
+    y = oracle.apply(H27, np.ones((6, 6, 6)))
+    assert y[3, 3, 3] == 0.0          # interior
+    assert y[0, 0, 0] == 19.0         # corner: 7 neighbours
+    assert y[0, 0, 3] == 15.0         # edge: 11 neighbours
+    assert y[0, 3, 3] == 9.0          # face: 17 neighbours
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (5, 3, 4)])
+def test_hpcg27_dense_structure(shape):
+    """Dense A: 26 on the diagonal, -1 exactly at Chebyshev distance 1."""
+    A = dense_from_apply(H27, shape)
+    nz, ny, nx = shape
+    coords = [(z, y, x) for z in range(nz) for y in range(ny) for x in range(nx)]
+    for i, a in enumerate(coords):
+        for j, b in enumerate(coords):
+            d = max(abs(a[0] - b[0]), abs(a[1] - b[1]), abs(a[2] - b[2]))
+            want = 26.0 if d == 0 else (-1.0 if d == 1 else 0.0)
+            assert A[i, j] == want
+
+
+def test_hpcg27_symmetric():
+    shape = (7, 6, 5)
+    x, y = rnd(shape, 1), rnd(shape, 2)
+    a = oracle.dot(x, oracle.apply(H27, y))
+    b = oracle.dot(y, oracle.apply(H27, x))
+    assert abs(a - b) <= 1e-14 * max(abs(a), 1.0)
+
+
+# --------------------------------------------------------------------------
+# c8: variable-kappa 7-point operator
+# --------------------------------------------------------------------------
+def laplacian7_kron(shape):
+    """Standard 7-point Dirichlet Laplacian as a Kronecker sum of 1-D
+    tridiag(-1, 2, -1) matrices (independent construction)."""
+    nz, ny, nx = shape
+
+    def t(n):
+        return 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+
+    Iz, Iy, Ix = np.eye(nz), np.eye(ny), np.eye(nx)
+    return (np.kron(np.kron(t(nz), Iy), Ix) + np.kron(np.kron(Iz, t(ny)), Ix)
+            + np.kron(np.kron(Iz, Iy), t(nx)))
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (2, 3, 1)])
+def test_kappa7_unit_kappa_is_laplacian(shape):
+    A = dense_from_apply(K7, shape, np.ones(shape))
+    assert np.array_equal(A, laplacian7_kron(shape))
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (4, 4, 4)])
+def test_kappa7_row_sums_are_boundary_terms(shape):
+    """A 1 = sum over the boundary faces of cell p of kappa_p."""
+    kap = kappa_small(shape)
+    y = oracle.apply(K7, np.ones(shape), kap)
+    nz, ny, nx = shape
+    for z, yy, x in itertools.product(range(nz), range(ny), range(nx)):
+        nb = sum(1 for c, n in ((x, nx), (yy, ny), (z, nz)) for d in (-1, 1)
+                 if not 0 <= c + d < n)
+        assert abs(y[z, yy, x] - nb * kap[z, yy, x]) <= 1e-13 * (1 + abs(y[z, yy, x]))
+
+
+def test_kappa7_symmetric_positive_definite():
+    shape = (3, 4, 5)
+    kap = kappa_small(shape, 3)
+    A = dense_from_apply(K7, shape, kap)
+    assert np.array_equal(A, A.T)
+    assert np.linalg.eigvalsh(A).min() > 0
+    # off-diagonal (p, q) = -(k_p + k_q)/2 for face neighbours
+    nz, ny, nx = shape
+    p = (1 * ny + 2) * nx + 3
+    q = (1 * ny + 2) * nx + 4
+    assert A[p, q] == -0.5 * (kap.flat[p] + kap.flat[q])
+
+
+# --------------------------------------------------------------------------
+# c1 / c3: Gauss-Seidel sweeps: ordering, brute force, fixed point
+# --------------------------------------------------------------------------
+def dense_gs_forward(A, b, x0):
+    """x1 = (D + L)^-1 (b - U x0) with L/U split by flattened index."""
+    DL = np.tril(A)
+    U = np.triu(A, 1)
+    return np.linalg.solve(DL, b - U @ x0)
+
+
+def dense_gs_backward(A, b, x0):
+    DU = np.triu(A)
+    L = np.tril(A, -1)
+    return np.linalg.solve(DU, b - L @ x0)
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (5, 3, 4), (4, 5, 3)])
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_gs_sweeps_match_dense_triangular_solves(kind, shape):
+    kap = kappa_small(shape, 5) if kind == K7 else None
+    A = dense_from_apply(kind, shape, kap)
+    b, x0 = rnd(shape, 6), rnd(shape, 7)
+    f = oracle.gs_forward(kind, b, x0, kap)
+    fd = dense_gs_forward(A, b.ravel(), x0.ravel())
+    assert np.max(np.abs(f.ravel() - fd)) <= 1e-13 * np.max(np.abs(fd))
+    g = oracle.gs_backward(kind, b, f, kap)
+    gd = dense_gs_backward(A, b.ravel(), fd)
+    assert np.max(np.abs(g.ravel() - gd)) <= 1e-13 * np.max(np.abs(gd))
+    s = oracle.symgs(kind, b, x0, 1, kap)
+    assert np.array_equal(s, g)
+
+
+def test_gs_axis_order_matters():
+    """A transposed axis order would give a different sweep: the dense check
+    above therefore pins x fastest, z outermost."""
+    shape = (3, 4, 5)
+    A = dense_from_apply(H27, shape)
+    b, x0 = rnd(shape, 8), rnd(shape, 9)
+    # the same sweep, but with the points visited with y fastest
+    perm = np.arange(np.prod(shape)).reshape(shape).transpose(0, 2, 1).ravel()
+    Ap = A[np.ix_(perm, perm)]
+    wrong = np.empty(A.shape[0])
+    wrong[perm] = dense_gs_forward(Ap, b.ravel()[perm], x0.ravel()[perm])
+    f = oracle.gs_forward(H27, b, x0)
+    assert np.max(np.abs(f.ravel() - wrong)) > 1e-3
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (5, 7, 3)])
+def test_symgs_bitwise_fixed_point(shape):
+    """b = A 1, x = 1: every update is an exact integer sum / 26 = 1."""
+    b = oracle.apply(H27, np.ones(shape))
+    x = oracle.symgs(H27, b, np.ones(shape), 3)
+    assert np.array_equal(x, np.ones(shape))
+
+
+def test_symgs_error_a_norm_monotone():
+    shape = (6, 5, 7)
+    A = dense_from_apply(H27, shape)
+    xs = rnd(shape, 10).ravel()
+    b = (A @ xs).reshape(shape)
+    x = np.zeros(shape)
+    prev = np.inf
+    for _ in range(6):
+        x = oracle.symgs(H27, b, x, 1)
+        e = x.ravel() - xs
+        en = e @ A @ e
+        assert en <= prev * (1 + 1e-12)
+        prev = en
+
+
+def test_negative_control_multicolor_differs():
+    """A reordered (8-colour) sweep differs from the lexicographic one far
+    above the 1e-13 parity tolerance after 10 sweeps."""
+    shape = (16, 16, 16)
+    b = rnd(shape, 11)
+    x1 = np.zeros(shape)
+    x2 = np.zeros(shape)
+    for _ in range(10):
+        x1 = oracle.gs_forward(H27, b, x1)
+        x2 = oracle.gs_multicolor_forward(H27, b, x2)
+    rel = np.max(np.abs(x1 - x2)) / np.max(np.abs(x1))
+    assert rel > 1e-3
+
+
+# --------------------------------------------------------------------------
+# c4: restriction, prolongation, V-cycle
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(6, 6, 6), (5, 7, 4), (1, 2, 3)])
+def test_restriction_is_injection_and_prolongation_its_transpose(shape):
+    r = rnd(shape, 12)
+    rc = oracle.restrict_residual(H27, r, np.zeros(shape))
+    assert np.array_equal(rc, r[::2, ::2, ::2])
+    zc = rnd(rc.shape, 13)
+    z = rnd(shape, 14)
+    zp = oracle.prolong_add(zc, z)
+    want = z.copy()
+    want[::2, ::2, ::2] += zc
+    assert np.array_equal(zp, want)
+    # <R f, c> = <f, P c>
+    f = rnd(shape, 15)
+    Rf = oracle.restrict_residual(H27, f, np.zeros(shape))
+    Pc = oracle.prolong_add(zc, np.zeros(shape))
+    assert oracle.dot(Rf, zc) == oracle.dot(f, Pc)
+
+
+def test_restriction_of_residual():
+    shape = (6, 5, 7)
+    r, z = rnd(shape, 16), rnd(shape, 17)
+    rc = oracle.restrict_residual(H27, r, z)
+    res = r - (dense_from_apply(H27, shape) @ z.ravel()).reshape(shape)
+    assert np.max(np.abs(rc - res[::2, ::2, ::2])) <= 1e-13 * np.max(np.abs(res))
+
+
+def test_coarsen_kappa_is_block_mean():
+    k = kappa_small((6, 4, 8))
+    kc = oracle.coarsen_kappa(k)
+    want = k.reshape(3, 2, 2, 2, 4, 2).mean(axis=(1, 3, 5))
+    assert np.max(np.abs(kc - want)) <= 1e-15 * np.max(want)
+    # ragged: an odd extent keeps a single fine cell at the end
+    k = kappa_small((3, 2, 2))
+    kc = oracle.coarsen_kappa(k)
+    assert kc.shape == (2, 1, 1)
+    assert abs(kc[1, 0, 0] - k[2].mean()) <= 1e-15 * k.max()
+
+
+def test_vcycle_one_level_is_symgs_from_zero():
+    shape = (5, 6, 7)
+    r = rnd(shape, 18)
+    assert np.array_equal(oracle.mg_vcycle(H27, r, 1),
+                          oracle.symgs(H27, r, np.zeros(shape), 1))
+
+
+def _dense_symgs_operator(A):
+    """z = S r for one symmetric GS from z = 0: S = (D+U)^-1 D (D+L)^-1."""
+    DL, DU, D = np.tril(A), np.triu(A), np.diag(np.diag(A))
+    return np.linalg.solve(DU, D @ np.linalg.solve(DL, np.eye(A.shape[0])))
+
+
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_two_level_vcycle_dense(kind):
+    """Two-level V-cycle assembled from dense matrices."""
+    shape = (4, 6, 5)
+    kap = kappa_small(shape, 19) if kind == K7 else None
+    A = dense_from_apply(kind, shape, kap)
+    cshape = tuple((n + 1) // 2 for n in shape)
+    kc = oracle.coarsen_kappa(kap) if kind == K7 else None
+    Ac = dense_from_apply(kind, cshape, kc)
+    S, Sc = _dense_symgs_operator(A), _dense_symgs_operator(Ac)
+    n = A.shape[0]
+    idx = np.arange(n).reshape(shape)[::2, ::2, ::2].ravel()
+    R = np.zeros((len(idx), n))
+    R[np.arange(len(idx)), idx] = 1.0
+    P = R.T
+    I = np.eye(n)
+    V = S + (I - S @ A) @ (S + P @ Sc @ R @ (I - A @ S))
+    r = rnd(shape, 20)
+    z = oracle.mg_vcycle(kind, r, 2, kap)
+    zd = V @ r.ravel()
+    assert np.max(np.abs(z.ravel() - zd)) <= 1e-12 * np.max(np.abs(zd))
+
+
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_vcycle_symmetric(kind):
+    shape = (16, 16, 16)
+    kap = gen.kappa_field(16, seed=7) if kind == K7 else None
+    x, y = rnd(shape, 21), rnd(shape, 22)
+    a = oracle.dot(oracle.mg_vcycle(kind, x, 4, kap), y)
+    b = oracle.dot(x, oracle.mg_vcycle(kind, y, 4, kap))
+    assert abs(a - b) <= 1e-13 * abs(a)
+
+
+def test_forward_sweep_transpose_is_backward_sweep():
+    """<S_f b1, b2> = <b1, S_b b2> (from zero): the transposed forward sweep is
+    the backward sweep with transposed couplings (A symmetric)."""
+    shape = (9, 8, 7)
+    kap = kappa_small(shape, 23)
+    for kind, k in ((H27, None), (K7, kap)):
+        b1, b2 = rnd(shape, 24), rnd(shape, 25)
+        f = oracle.gs_forward(kind, b1, np.zeros(shape), k)
+        g = oracle.gs_backward(kind, b2, np.zeros(shape), k)
+        a, c = oracle.dot(f, b2), oracle.dot(b1, g)
+        assert abs(a - c) <= 1e-14 * abs(a)
+
+
+# --------------------------------------------------------------------------
+# c5: Dot2 and PCG
+# --------------------------------------------------------------------------
+def test_dot2_near_exact():
+    for k in range(3):
+        a = rnd((1000,), 30 + k) * 10.0 ** rnd((1000,), 40 + k) * 3
+        b = rnd((1000,), 50 + k)
+        exact = sum(Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b))
+        d = oracle.dot(a, b)
+        assert abs(Fraction(d) - exact) <= abs(exact) * Fraction(2.3e-16)
+
+
+def test_dot2_ill_conditioned():
+    """Cancellation that a plain sum gets wrong but Dot2 gets right."""
+    a = np.array([1e16, 1.0, -1e16, 1.0])
+    b = np.ones(4)
+    assert oracle.dot(a, b) == 2.0
+
+
+@pytest.mark.parametrize("kind,levels", [(H27, 0), (H27, 1), (H27, 2), (K7, 0), (K7, 2)])
+def test_pcg_converges_to_dense_solution(kind, levels):
+    shape = (4, 4, 6)
+    kap = kappa_small(shape, 26) if kind == K7 else None
+    A = dense_from_apply(kind, shape, kap)
+    b = rnd(shape, 27)
+    x, it, hist, st = oracle.pcg(kind, b, levels, kap, max_iters=200, rtol=1e-12,
+                                 fixed_iters=False)
+    assert st == 0
+    xd = np.linalg.solve(A, b.ravel())
+    assert np.max(np.abs(x.ravel() - xd)) <= 1e-10 * np.max(np.abs(xd))
+    # the recurrence residual equals the true residual
+    rt = np.linalg.norm(b.ravel() - A @ x.ravel())
+    assert abs(hist[-1] - rt) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_pcg_recovers_ones():
+    shape = (16, 16, 16)
+    b = oracle.apply(H27, np.ones(shape))
+    x, it, hist, st = oracle.pcg(H27, b, 4, max_iters=50, fixed_iters=True)
+    assert st == 0 and it == 50
+    assert np.max(np.abs(x - 1.0)) < 1e-9
+    # MG-PCG reduces the residual by many orders of magnitude
+    assert hist[-1] / hist[0] < 1e-10
+
+
+def test_pcg_mg_faster_than_sgs_faster_than_cg():
+    shape = (16, 16, 16)
+    b = oracle.apply(H27, np.ones(shape))
+    its = []
+    for levels in (0, 1, 4):
+        _, it, _, st = oracle.pcg(H27, b, levels, max_iters=500, rtol=1e-10,
+                                  fixed_iters=False)
+        assert st == 0
+        its.append(it)
+    assert its[0] > its[1] > its[2]
+
+
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_fp32_preconditioned_pcg_reaches_1e10(kind):
+    n = 16
+    kap = gen.kappa_field(n, seed=3) if kind == K7 else None
+    b = oracle.apply(kind, np.ones((n, n, n)), kap)
+    x64, it64, h64, st64 = oracle.pcg(kind, b, 3, kap, max_iters=200, rtol=1e-10,
+                                      fixed_iters=False)
+    x32, it32, h32, st32 = oracle.pcg(kind, b, 3, kap, max_iters=200, rtol=1e-10,
+                                      fixed_iters=False, precond_f32=True)
+    assert st64 == 0 and st32 == 0
+    assert h32[-1] <= 1e-10 * h32[0]
+    assert np.max(np.abs(x32 - x64)) <= 1e-7 * np.max(np.abs(x64))
+    assert it32 <= it64 + 3
+
+
+def test_fp32_vcycle_close_to_fp64_vcycle():
+    n = 16
+    kap = gen.kappa_field(n, seed=4)
+    r = rnd((n, n, n), 28)
+    for kind, k in ((H27, None), (K7, kap)):
+        z64 = oracle.mg_vcycle(kind, r, 3, k)
+        z32 = oracle.mg_vcycle_f32(kind, r.astype(np.float32), 3, k)
+        assert np.max(np.abs(z32 - z64)) <= 1e-5 * np.max(np.abs(z64))
+        y32 = oracle.apply_f32(kind, r.astype(np.float32),
+                               None if k is None else k.astype(np.float32))
+        y64 = oracle.apply(kind, r, k)
+        assert np.max(np.abs(y32 - y64)) <= 1e-5 * np.max(np.abs(y64))
+
+
+# --------------------------------------------------------------------------
+# c10: adjoint gradient
+# --------------------------------------------------------------------------
+def test_kappa_gradient_matches_finite_differences():
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    n = 8
+    shape = (n, n, n)
+    kap = gen.kappa_field(n, seed=5)
+    b = np.ones(shape)
+    ut = gen.target(shape, seed=6)
+
+    def solve(k):
+        A = sp.csc_matrix(dense_from_apply(K7, shape, k))
+        return spla.spsolve(A, b.ravel()).reshape(shape)
+
+    def loss(k):
+        u = solve(k)
+        return 0.5 * np.sum((u - ut) ** 2)
+
+    u = solve(kap)
+    A = sp.csc_matrix(dense_from_apply(K7, shape, kap))
+    lam = spla.spsolve(A.T, (u - ut).ravel()).reshape(shape)
+    g = oracle.kappa_grad(u, lam)
+    cells = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, 3, 4), (3, 0, 5), (4, 5, 0),
+             (3, 3, 3), (2, 5, 6), (7, 1, 2), (5, 7, 3), (1, 6, 7)]
+    for c in cells:
+        h = 1e-5 * kap[c]
+        kp, km = kap.copy(), kap.copy()
+        kp[c] += h
+        km[c] -= h
+        fd = (loss(kp) - loss(km)) / (2 * h)
+        assert abs(fd - g[c]) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(g)))
+
+
+# --------------------------------------------------------------------------
+# c7: block SSOR
+# --------------------------------------------------------------------------
+def block_dense(D, L, U):
+    """Dense 5N x 5N matrix of the block operator (built from the block
+    definition by scattering blocks)."""
+    nz, ny, nx = D.shape[:3]
+    n = nx * ny * nz
+    A = np.zeros((5 * n, 5 * n))
+
+    def P(x, y, z):
+        return (z * ny + y) * nx + x
+
+    for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+        p = P(x, y, z)
+        A[5 * p:5 * p + 5, 5 * p:5 * p + 5] = D[z, y, x]
+        for d, (dx, dy, dz) in enumerate(((1, 0, 0), (0, 1, 0), (0, 0, 1))):
+            if x - dx >= 0 and y - dy >= 0 and z - dz >= 0:
+                q = P(x - dx, y - dy, z - dz)
+                A[5 * p:5 * p + 5, 5 * q:5 * q + 5] = L[z, y, x, d]
+            if x + dx < nx and y + dy < ny and z + dz < nz:
+                q = P(x + dx, y + dy, z + dz)
+                A[5 * p:5 * p + 5, 5 * q:5 * q + 5] = U[z, y, x, d]
+    return A
+
+
+def test_block_sweeps_match_dense():
+    shape = (2, 4, 3)
+    D, L, U, b = gen.block_ssor_inputs(0, shape=shape, seed=31)
+    A = block_dense(D, L, U)
+    u = rnd(shape + (5,), 32)
+    y = oracle.block_apply(D, L, U, u)
+    assert np.max(np.abs(y.ravel() - A @ u.ravel())) <= 1e-13 * np.max(np.abs(y))
+    om = 1.2
+    Dd = np.zeros_like(A)
+    for p in range(A.shape[0] // 5):
+        Dd[5 * p:5 * p + 5, 5 * p:5 * p + 5] = A[5 * p:5 * p + 5, 5 * p:5 * p + 5]
+    Ld = np.tril(A - Dd)
+    Ud = np.triu(A - Dd)
+    r = rnd(shape + (5,), 33)
+    v = oracle.block_lower(D, L, om, r)
+    vd = np.linalg.solve(Dd + om * Ld, r.ravel())
+    assert np.max(np.abs(v.ravel() - vd)) <= 1e-13 * np.max(np.abs(vd))
+    w = oracle.block_upper(D, U, om, v)
+    wd = np.linalg.solve(Dd + om * Ud, Dd @ vd)
+    assert np.max(np.abs(w.ravel() - wd)) <= 1e-13 * np.max(np.abs(wd))
+
+
+def test_ssor_delta_form_equals_forward_backward_sor():
+    """u + w(2-w) (D+wU)^-1 D (D+wL)^-1 (b - A u) equals one classical
+    in-place forward block-SOR sweep followed by one backward sweep."""
+    shape = (3, 2, 4)
+    D, L, U, b = gen.block_ssor_inputs(0, shape=shape, seed=34)
+    A = block_dense(D, L, U)
+    om = 1.2
+    nb = A.shape[0] // 5
+    u = rnd(shape + (5,), 35).ravel()
+
+    def sor_sweep(u, order):
+        u = u.copy()
+        for p in order:
+            s = slice(5 * p, 5 * p + 5)
+            off = A[s] @ u - A[s, s] @ u[s]
+            u[s] = (1 - om) * u[s] + om * np.linalg.solve(A[s, s], b.ravel()[s] - off)
+        return u
+
+    classic = sor_sweep(sor_sweep(u, range(nb)), reversed(range(nb)))
+    delta = oracle.ssor(D, L, U, om, b, u.reshape(shape + (5,)), 1)
+    assert np.max(np.abs(delta.ravel() - classic)) <= 1e-13 * np.max(np.abs(classic))
+
+
+def test_ssor_scalar_special_case_is_symgs():
+    """D = 6 I, L = U = -I, omega = 1: each of the 5 components is the 7-point
+    Laplacian and one SSOR step from u is one symmetric GS from u."""
+    shape = (3, 4, 5)
+    D = np.broadcast_to(6.0 * np.eye(5), shape + (5, 5)).copy()
+    L = np.broadcast_to(-np.eye(5), shape + (3, 5, 5)).copy()
+    U = L.copy()
+    b = rnd(shape + (5,), 36)
+    u0 = rnd(shape + (5,), 37)
+    u1 = oracle.ssor(D, L, U, 1.0, b, u0, 1)
+    for c in range(5):
+        s = oracle.symgs(K7, b[..., c], u0[..., c], 1, np.ones(shape))
+        assert np.max(np.abs(u1[..., c] - s)) <= 1e-13 * np.max(np.abs(s))
+
+
+def test_ssor_converges_to_dense_solution():
+    shape = (3, 3, 2)
+    D, L, U, b = gen.block_ssor_inputs(0, shape=shape, seed=38)
+    A = block_dense(D, L, U)
+    u = oracle.ssor(D, L, U, 1.2, b, np.zeros(shape + (5,)), 60)
+    ud = np.linalg.solve(A, b.ravel())
+    assert np.max(np.abs(u.ravel() - ud)) <= 1e-12 * np.max(np.abs(ud))
+
+
+# --------------------------------------------------------------------------
+# c9 / c11: inputs
+# --------------------------------------------------------------------------
+def test_splitmix64_reference_value():
+    """SplitMix64 from state 0: first output 0xE220A8397B1DCDAF (published
+    reference sequence)."""
+    v = gen._mix(np.uint64(0) + gen.GAMMA)
+    assert int(v) == 0xE220A8397B1DCDAF
+
+
+def test_inputs_deterministic_and_distributed():
+    a = gen.uniform(5, 2, 1000)
+    assert np.array_equal(a, gen.uniform(5, 2, 1000))
+    assert not np.array_equal(a, gen.uniform(6, 2, 1000))
+    assert 0.0 <= a.min() and a.max() < 1.0
+    z = gen.normal(1, 1, 200000)
+    assert abs(z.mean()) < 0.01 and abs(z.var() - 1) < 0.02
+    k = gen.kappa_field(48, seed=9)
+    lk = np.log(k)
+    assert abs(lk.mean()) < 0.3 and 0.5 < lk.var() < 1.5
+    assert np.array_equal(k, gen.kappa_field(48, seed=9))
+    s = gen.batch_sides(64)
+    assert len(s) == 64 and set(s) <= set(gen.BATCH_SIDES) and len(set(s)) >= 4
