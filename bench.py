@@ -1,0 +1,358 @@
+"""Benchmark: FP64 MG-PCG to a relative residual of 1e-10 on the 256^3 HPCG
+27-point problem (b = A*ones, x0 = 0, 4-level V-cycle with symmetric
+Gauss-Seidel smoothing), the paper's HPCG workload shape (Sec. 7.1).
+
+One step = one complete solve (every row of the hot path: SpMV, forward and
+backward lexicographic sweeps, restriction, prolongation, V-cycle, PCG).
+The JSON line also carries the FP32-preconditioned solve of the same problem,
+per-kernel timings of the dominant kernels (CUDA events on the launching
+stream), the roofline of the dominant kernel, an end-to-end time through the
+public API with host buffers, and the serial oracle on the host CPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 256] [--impl ours|reference]
+
+Multi-GPU: the solve does not shard (exact lexicographic Gauss-Seidel is
+sequential across z-slabs), so N GPUs run N independent replicas; value is
+the whole job's time per solve (max-over-ranks time / solves of all ranks).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MG-PCG time to 1e-10 at 256^3 (FP64 vs FP32-precond); SymGS/SpMV HBM GB/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 issue rate of a GB300: 152 SMs x 4 sub-partitions, one FP64 warp
+# instruction per ~64 clocks each (2 FP64 lanes/clk/SM) at the 2070 MHz
+# maximum SM clock -> 152 * 2 * 2.07e9 = 629 G FP64 operations/s
+# (= 1.26 TFLOP/s counting an FMA as 2).
+FP64_OPS_PEAK = 152 * 2 * 2.07e9
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    def __init__(self):
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", dev, "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        s = self.samples
+        if not s:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        import statistics
+        sm = [float(x[0]) for x in s if x[0].replace(".", "").isdigit()]
+        mx = [float(x[1]) for x in s if x[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for x in s for i in range(4) if x[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(s)}
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(n, budget_s=20.0):
+    """The serial oracle on a bounded sample of the workload: MG-PCG
+    iterations of the same 256^3 problem, scaled to seconds per solve with
+    the GPU's iteration count."""
+    import numpy as np
+    import oracle
+    shape = (n, n, n)
+    t0 = time.perf_counter()
+    b = oracle.apply(oracle.HPCG27, np.ones(shape))
+    # time one V-cycle + one SpMV (the per-iteration work) a few times
+    reps = 0
+    t1 = time.perf_counter()
+    while True:
+        z = oracle.mg_vcycle(oracle.HPCG27, b, 4)
+        oracle.apply(oracle.HPCG27, z)
+        reps += 1
+        if time.perf_counter() - t1 > budget_s / 2 or reps >= 3:
+            break
+    per_iter = (time.perf_counter() - t1) / reps
+    return per_iter, reps, time.perf_counter() - t0
+
+
+def run_reference(args):
+    """--impl reference: the serial CPU oracle on the same problem, bounded."""
+    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.lib()
+    iters_per_solve = 40  # typical FP64 MG-PCG iteration count to 1e-10 at 256^3
+    per_iter, reps, _ = cpu_baseline(args.n, budget_s=min(60.0, 10.0 * max(1, args.steps)))
+    value = per_iter * iters_per_solve
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args.n),
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "s",
+                         "sample": "%d timed V-cycle+SpMV iterations of the %d^3 problem on 1 "
+                                   "host core, x %d iterations per solve" % (reps, args.n,
+                                                                          iters_per_solve)},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(n):
+    return {"workload": "HPCG 27-point operator %d^3 (%d rows), b = A*ones, x0 = 0, FP64 MG-PCG "
+                        "(4 levels, 1 pre + 1 post symmetric GS, injection) to rel. residual "
+                        "1e-10" % (n, n ** 3),
+            "grid": [n, n, n], "mg_levels": 4, "rtol": 1e-10,
+            "l2": "inputs larger than L2 (each FP64 vector %d MiB)" % (n ** 3 * 8 >> 20)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2204_13304_gb300 as m
+
+    n = args.n
+    shape = (n, n, n)
+    stream = torch.cuda.current_stream()
+    g64 = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.HPCG27, mg_levels=4, precond_dtype=m.DType.F64)])
+    g32 = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.HPCG27, mg_levels=4, precond_dtype=m.DType.F32)])
+    ones = torch.ones(shape, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(ones)
+    m.m2s_spmv(g64.handle, 0, ones, b)
+    x = torch.empty_like(ones)
+
+    def solve(g):
+        st, res = m.m2s_pcg_solve(g.handle, b, x, max_iters=500, rtol=1e-10, fixed_iters=False,
+                                  check_every=1)
+        return st, res
+
+    # warm-up
+    for _ in range(args.warmup):
+        st, res64 = solve(g64)
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st, res64 = solve(g64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t64 = e0.elapsed_time(e1) / 1e3 / args.steps
+    clk = clocks.stop()
+    x64 = x.clone()
+
+    # FP32-preconditioned form on the same problem
+    for _ in range(max(1, args.warmup // 2)):
+        st32, res32 = solve(g32)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        st32, res32 = solve(g32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t32 = e0.elapsed_time(e1) / 1e3 / args.steps
+    err32 = float((x - x64).abs().max() / x64.abs().max())
+    err64_ones = float((x64 - 1.0).abs().max())
+
+    # per-kernel timings (CUDA events on the launching stream)
+    def time_op(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        c.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(c) / 1e3 / reps
+
+    xs = torch.zeros_like(ones)
+    ys = torch.empty_like(ones)
+    t_spmv = time_op(lambda: m.m2s_spmv(g64.handle, 0, x64, ys))
+    # one sweep = (10 symmetric GS - 1 symmetric GS) / 18: removes the
+    # one-off old-neighbour-sum kernel that starts m2s_symgs
+    t_sweep64 = (time_op(lambda: m.m2s_symgs(g64.handle, 0, b, xs, 10), 2) -
+                 time_op(lambda: m.m2s_symgs(g64.handle, 0, b, xs, 1), 2)) / 18
+    b32 = b.float()
+    xs32 = torch.zeros_like(b32)
+    ys32 = torch.empty_like(b32)
+    t_spmv32 = time_op(lambda: m.m2s_spmv(g32.handle, 0, b32, ys32))
+    t_sweep32 = (time_op(lambda: m.m2s_symgs(g32.handle, 0, b32, xs32, 10), 2) -
+                 time_op(lambda: m.m2s_symgs(g32.handle, 0, b32, xs32, 1), 2)) / 18
+    rows = n ** 3
+    hbm, peak_kind = peaks()
+    kern = {
+        "spmv27_f64": {"ms": t_spmv * 1e3, "alg_GBs": 16 * rows / t_spmv / 1e9},
+        "symgs_sweep_f64": {"ms": t_sweep64 * 1e3, "alg_GBs": 24 * rows / t_sweep64 / 1e9,
+                            "alg_fp64_Gops": 27 * rows / t_sweep64 / 1e9},
+        "spmv27_f32": {"ms": t_spmv32 * 1e3, "alg_GBs": 8 * rows / t_spmv32 / 1e9},
+        "symgs_sweep_f32": {"ms": t_sweep32 * 1e3, "alg_GBs": 12 * rows / t_sweep32 / 1e9},
+    }
+    # dominant kernel of the FP64 solve: the Gauss-Seidel sweep, bound by the
+    # FP64 issue rate; 27 FP64 operations per row by definition (26 neighbour
+    # terms + the division), against 629 G FP64 ops/s.
+    ach = 27 * rows / t_sweep64 / 1e9
+    roof = {"kernel": "symgs_sweep_f64 (gs27_wave_kernel<double>)", "bound": "alu",
+            "achieved": ach, "peak": FP64_OPS_PEAK / 1e9, "unit": "G FP64 op/s",
+            "frac": ach / (FP64_OPS_PEAK / 1e9), "traffic": None,
+            "hbm_frac": 24 * rows / t_sweep64 / 1e9 / hbm,
+            "peak_note": "FP64 issue rate 152 SMs x 2 lanes/clk x 2.07 GHz; HBM %s %.0f GB/s"
+                         % (peak_kind, hbm)}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        bh = b.cpu().pin_memory()
+        xh = torch.empty(shape, dtype=torch.float64).pin_memory()
+        bd = torch.empty_like(b)
+        xd = torch.empty_like(b)
+
+        def e2e_step():
+            bd.copy_(bh, non_blocking=True)
+            m.m2s_pcg_solve(g64.handle, bd, xd, max_iters=500, rtol=1e-10, fixed_iters=False)
+            xh.copy_(xd, non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        te = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": te, "unit": "s", "h2d_bytes_per_step": rows * 8,
+               "d2h_bytes_per_step": rows * 8}
+
+    value = max_over_ranks(ws, t64) / ws
+    launches = launches_per_solve(res64.iters)
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t64 * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (HPCG operator, b = A*ones)", "config": workload_config(n),
+        "iters_fp64": res64.iters, "rel_resid_fp64": res64.rel_resid,
+        "max_err_vs_ones_fp64": err64_ones,
+        "fp32_precond": {"value": t32, "unit": "s", "iters": res32.iters,
+                         "rel_resid": res32.rel_resid, "rel_err_vs_fp64_solution": err32,
+                         "speedup_vs_fp64": t64 / t32},
+        "kernels": kern, "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        per_iter, reps, _ = cpu_baseline(n)
+        line["cpu_baseline"] = {"value": per_iter * res64.iters, "unit": "s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "%d V-cycle+SpMV iterations of the %d^3 problem on one "
+                                          "host core, x %d iterations" % (reps, n, res64.iters)}
+    if rank == 0:
+        print(json.dumps(line))
+    g64.close()
+    g32.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def launches_per_solve(iters, levels=4):
+    """Kernels of one FP64 MG-PCG solve: setup (dot + finalize) then per
+    iteration the V-cycle (per non-coarsest level 2 + 2 sweeps, restriction,
+    fused prolongation; coarsest 2 sweeps), finalize(rho), p-update+SpMV+dot,
+    finalize(pq), update+|r|, finalize(rr)."""
+    per_v = (levels - 1) * 6 + 2
+    return 2 + iters * (per_v + 5)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,223 @@
+/*
+ * m2s.h -- C ABI of the GB300 (sm_103a) library for the matrix-free
+ * structured-grid solver hot path studied in Mat2Stencil (arXiv 2204.13304).
+ *
+ * Problem statement (paper Sec. 1 and Sec. 2.1): solve A u = b on a regular
+ * Cartesian grid where A is a structured sparse operator that is never
+ * assembled (matrix-free, Sec. 2.1.2); the routines are the SpMV, Gauss-Seidel
+ * / SSOR sweeps with spatial dependence, geometric-multigrid restriction and
+ * prolongation, and the MG-preconditioned CG that HPCG runs (Sec. 4.3,
+ * Sec. 7.1).
+ *
+ * Conventions shared by every entry point
+ *   Layout     vectors are dense [nz][ny][nx] arrays (x fastest); the block
+ *              operator's vectors are [nz][ny][nx][5].  The flat index of
+ *              point (x,y,z) is p = (z*ny + y)*nx + x.  "Lexicographic order"
+ *              is increasing p.
+ *   Memory     every vector pointer is a DEVICE pointer owned by the caller,
+ *              8-byte aligned (FP64) or 4-byte aligned (FP32); vectors of one
+ *              call must not overlap unless stated.  Coefficients passed to
+ *              m2s_grid_create are copied; the grid owns all workspaces.
+ *   Batches    a grid may hold n_problems problems; vectors are then the
+ *              problems' arrays packed back to back in problem order.
+ *   Streams    `stream` is a cudaStream_t (NULL = legacy default stream).
+ *              Every call is stream-ordered and asynchronous unless stated.
+ *   Levels     level 0 is the finest grid; level l has extents
+ *              ceil(n_{l-1} / 2) (coarse point i <-> fine point 2i).
+ *   dtype      M2S_F64 or M2S_F32: the element type of the vector pointers
+ *              of the call.  FP32 calls need a grid created with
+ *              precond_dtype = M2S_F32 for the kappa operator (the 27-point
+ *              operator has no coefficients and accepts both).
+ *   Errors     functions return an m2s_status; nothing traps or aborts.
+ *              Invalid arguments are rejected before any launch.  A kernel
+ *              error word (for example an expired bounded spin-wait) is read
+ *              at the next synchronising call (m2s_pcg_solve,
+ *              m2s_adjoint_solve, m2s_grid_sync) and returned there.
+ */
+#ifndef M2S_H
+#define M2S_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct m2s_grid m2s_grid; /* opaque, library-owned */
+
+typedef enum {
+    M2S_OK = 0,
+    M2S_ERR_INVALID_ARG = 1,
+    M2S_ERR_CUDA = 2,
+    M2S_ERR_OOM = 3,
+    M2S_ERR_TIMEOUT = 4,       /* a bounded spin-wait expired in a sweep */
+    M2S_ERR_NOT_CONVERGED = 5, /* max_iters reached above rtol */
+    M2S_ERR_BREAKDOWN = 6      /* NaN/Inf or p.Ap <= 0 in CG */
+} m2s_status;
+
+typedef enum {
+    M2S_OP_HPCG27 = 0,      /* 27-point: a_pp = 26, a_pq = -1 (HPCG) */
+    M2S_OP_DIFF7_KAPPA = 1, /* 7-point variable-coefficient diffusion */
+    M2S_OP_BLOCK7_5x5 = 2   /* 7-point 5x5-block operator (NPB-LU shape) */
+} m2s_op;
+
+typedef enum { M2S_F64 = 0, M2S_F32 = 1 } m2s_dtype;
+
+typedef enum { M2S_FORWARD = 0, M2S_BACKWARD = 1 } m2s_direction;
+
+/* One problem of a grid.
+ *   nx, ny, nz     extents, each >= 1.
+ *   op             operator family.
+ *   mg_levels      1..8 multigrid levels (1 = symmetric GS preconditioner).
+ *   precond_dtype  M2S_F32 selects the FP32 V-cycle inside m2s_pcg_solve
+ *                  (flexible CG; residual, dots and x stay FP64).
+ *   kappa          op = DIFF7_KAPPA: device FP64 [nz][ny][nx] cell
+ *                  coefficients (> 0), copied at creation.  The face
+ *                  coefficient is the mean of its two cells (the averaging
+ *                  matrix of paper Sec. 4.1); a boundary face uses the
+ *                  cell's own value with a zero ghost value.
+ *   D, L, U        op = BLOCK7_5x5: device FP64 per-point 5x5 row-major
+ *                  blocks: D[n][5][5] diagonal blocks, L[n][3][5][5]
+ *                  couplings to p-e_x, p-e_y, p-e_z, U[n][3][5][5] to
+ *                  p+e_x, p+e_y, p+e_z (ignored where they leave the grid);
+ *                  copied at creation. */
+typedef struct {
+    int nx, ny, nz;
+    m2s_op op;
+    int mg_levels;
+    m2s_dtype precond_dtype;
+    const double* kappa;
+    const double* D;
+    const double* L;
+    const double* U;
+} m2s_grid_desc;
+
+/* PCG options.  max_iters >= 1; rtol >= 0 (stop when |r|/|b| <= rtol);
+ * fixed_iters = 1 runs exactly max_iters iterations (HPCG's 50-iteration
+ * run) and never reports NOT_CONVERGED; check_every >= 1 is how often the
+ * residual is copied to the host to test rtol (1 = every iteration). */
+typedef struct {
+    int max_iters;
+    double rtol;
+    int fixed_iters;
+    int check_every;
+} m2s_pcg_opts;
+
+/* Filled after the stream synchronisation of a solve (host memory). */
+typedef struct {
+    int iters;              /* iterations performed */
+    double rel_resid;       /* |r| / |b| after the last iteration (FP64) */
+    double resid_hist_last; /* |r| after the last iteration */
+} m2s_pcg_result;
+
+/* Create a grid of n_problems problems (n_problems >= 1; every desc must
+ * use the same op).  Allocates the multigrid hierarchy, coefficient copies,
+ * FP32 copies when requested, and all workspaces; copies coefficients with
+ * stream-ordered copies on `stream` and synchronises it before returning.
+ * On failure *out is NULL and nothing is leaked. */
+m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems,
+                           void* stream, m2s_grid** out);
+
+/* Release the grid (synchronises the device first).  NULL is accepted. */
+m2s_status m2s_grid_destroy(m2s_grid* grid);
+
+/* Synchronise the grid's last stream and return (then clear) any kernel
+ * error word, e.g. M2S_ERR_TIMEOUT from an expired spin-wait. */
+m2s_status m2s_grid_sync(m2s_grid* grid, void* stream);
+
+/* Number of points of level `level` of problem `problem` (0 if invalid). */
+long long m2s_grid_points(const m2s_grid* grid, int problem, int level);
+
+/* Sec. 4.3.1 SpMV on level `level`: y = A_level x (all problems of the
+ * grid).  x and y must not overlap.  Op HPCG27 or DIFF7_KAPPA. */
+m2s_status m2s_spmv(m2s_grid* grid, int level, m2s_dtype dtype,
+                    const void* x, void* y, void* stream);
+
+/* Sec. 4.3.3 symmetric Gauss-Seidel on level `level`: n_sym_sweeps times
+ * (one forward lexicographic sweep, then one backward sweep) of
+ * x_p <- (b_p - sum_{q != p} a_pq x_q) / a_pp, in exact sequential order
+ * (each point sees the new values of the points before it and the old
+ * values of the points after it).  x is in/out; b and x must not overlap. */
+m2s_status m2s_symgs(m2s_grid* grid, int level, m2s_dtype dtype,
+                     const void* b, void* x, int n_sym_sweeps, void* stream);
+
+/* One Gauss-Seidel sweep in one direction (forward = increasing p,
+ * backward = decreasing p); the transpose of a forward sweep is a backward
+ * sweep with the transposed couplings, which for these symmetric operators
+ * are the same couplings. */
+m2s_status m2s_gs_sweep(m2s_grid* grid, int level, m2s_dtype dtype,
+                        const void* b, void* x, m2s_direction direction,
+                        void* stream);
+
+/* Multigrid transfer (paper Table 1 "HPCG Prolong" matrix: coarse point i
+ * <-> fine point 2i).  Restriction of the residual:
+ *   rc_i = r_{2i} - (A_level z)_{2i}, rc on level+1.
+ * Prolongation (the transpose of injection): z_{2i} += zc_i. */
+m2s_status m2s_mg_restrict(m2s_grid* grid, int level, m2s_dtype dtype,
+                           const void* r, const void* z, void* rc, void* stream);
+m2s_status m2s_mg_prolong(m2s_grid* grid, int level, m2s_dtype dtype,
+                          const void* zc, void* z, void* stream);
+
+/* One multigrid V-cycle z = M^-1 r with the grid's mg_levels levels: z = 0;
+ * coarsest level one symmetric GS; otherwise symmetric GS (pre-smoothing),
+ * restrict the residual, recurse, prolongate, symmetric GS (post). dtype
+ * F64 runs the FP64 hierarchy, F32 the FP32 one.  r and z must not
+ * overlap. */
+m2s_status m2s_mg_vcycle(m2s_grid* grid, m2s_dtype dtype, const void* r,
+                         void* z, void* stream);
+
+/* Preconditioned CG from x0 = 0 (r0 = b) with the V-cycle preconditioner
+ * (FP64, or FP32 inside flexible CG when precond_dtype = F32).  b, x are
+ * FP64.  Synchronises `stream`; fills *out (may be NULL).  Returns
+ * M2S_ERR_NOT_CONVERGED if rtol was not met within max_iters (unless
+ * fixed_iters), M2S_ERR_BREAKDOWN on p.Ap <= 0 or non-finite values. */
+m2s_status m2s_pcg_solve(m2s_grid* grid, const double* b, double* x,
+                         const m2s_pcg_opts* opts, m2s_pcg_result* out,
+                         void* stream);
+
+/* Block SSOR on the BLOCK7_5x5 operator (NPB-LU shape, paper Sec. 1 and
+ * Sec. 4.3.3): n_iters times
+ *   r = b - A u; lower sweep (D + omega L) v = r; upper sweep
+ *   (D + omega U) w = D v; u += omega (2 - omega) w,
+ * i.e. one forward and one backward block-SOR sweep per iteration.
+ * 0 < omega < 2.  u is in/out ([n][5] FP64). */
+m2s_status m2s_ssor_sweep(m2s_grid* grid, const double* b, double* u,
+                          double omega, int n_iters, void* stream);
+
+/* Adjoint of the kappa solve (op DIFF7_KAPPA).  Given the forward solution u
+ * of A(kappa) u = b and dLdu, solves A^T lambda = dLdu with PCG (the
+ * transposed V-cycle: transposed sweeps in mirrored order, which for this
+ * symmetric operator is the same V-cycle) and writes
+ *   dLdkappa_c = - sum_{faces f of c} dk_f/dk_c (lambda_p - lambda_q)
+ *                (u_p - u_q) - (boundary faces of c) lambda_c u_c.
+ * All vectors FP64.  Synchronises; fills *out (may be NULL). */
+m2s_status m2s_adjoint_solve(m2s_grid* grid, const double* u,
+                             const double* dLdu, double* lambda,
+                             double* dLdkappa, const m2s_pcg_opts* opts,
+                             m2s_pcg_result* out, void* stream);
+
+/* dLdkappa from u and lambda alone (the stencil step of m2s_adjoint_solve). */
+m2s_status m2s_kappa_grad(m2s_grid* grid, const double* u,
+                          const double* lambda, double* dLdkappa,
+                          void* stream);
+
+/* Bound on every spin-wait of the dependent sweeps, in nanoseconds
+ * (default 4e9).  A wait that exceeds it sets M2S_ERR_TIMEOUT, every sweep
+ * in flight stops at its next wait, and the error is returned at the next
+ * synchronising call. */
+m2s_status m2s_set_spin_limit(m2s_grid* grid, long long limit_ns);
+
+/* Fault-injection hook for tests (host side; nothing faults on the GPU):
+ * in the next Gauss-Seidel sweep on `level`, wavefront unit `unit` (in ticket
+ * order) neither computes nor publishes its progress.  The units that wait
+ * on it run into their bounded spin-wait, every sweep unit stops, and the
+ * next synchronising call returns M2S_ERR_TIMEOUT; the sweep machinery is
+ * reset and usable afterwards.  The sweep's output is then undefined. */
+m2s_status m2s_debug_stall_unit(m2s_grid* grid, int level, int unit);
+
+/* Static description of a status code. */
+const char* m2s_status_string(m2s_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* M2S_H */

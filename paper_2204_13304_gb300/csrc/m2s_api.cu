@@ -1,0 +1,658 @@
+// C ABI of the m2s library: grid hierarchy, multigrid V-cycle and PCG
+// drivers (paper Sec. 7.1 HPCG: PCG with a multigrid preconditioner whose
+// smoother is symmetric Gauss-Seidel; Sec. 4.3 routines), and the entry
+// points declared in include/m2s.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "m2s_block.cuh"
+#include "m2s_internal.cuh"
+#include "m2s_pcg.cuh"
+
+using namespace m2s;
+
+namespace {
+
+constexpr int kMaxLevels = 8;
+constexpr int kWaveK = 5;
+
+template <typename T>
+struct Work {
+    std::vector<T*> Qa, Qb, rc, zc;  // per level, packed over problems
+};
+
+}  // namespace
+
+struct m2s_grid {
+    int np = 0;
+    m2s_op op = M2S_OP_HPCG27;
+    int levels = 1;
+    m2s_dtype pdtype = M2S_F64;
+    bool has32 = false;
+    std::vector<std::vector<Dims>> dims;  // [problem][level]
+    std::vector<i64> ltot;                // packed points per level
+    // variable-kappa hierarchy (packed per level)
+    std::vector<double*> kappa;
+    std::vector<KappaLevel<double>> k64;
+    std::vector<KappaLevel<float>> k32;
+    // sweep schedules per problem and level
+    std::vector<std::vector<WaveUnits>> units;
+    Work<double> w64;
+    Work<float> w32;
+    // PCG state (finest level, packed)
+    double *r = nullptr, *z = nullptr, *zold = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
+    float *r32 = nullptr, *z32 = nullptr;
+    double *part = nullptr, *part2 = nullptr;
+    int npart = 0;
+    PcgDev* dev = nullptr;
+    double* hist = nullptr;
+    int hist_cap = 0;
+    DevStatus* status = nullptr;
+    long long spin_ns = 4000000000LL;
+    int publish_every = 4;
+    int stall_level = -1;  // test hook consumed by the next sweep on that level
+    int stall_unit = -1;
+    BlockOp blk;
+    std::vector<void*> allocs;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+m2s_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return M2S_OK;
+    if (e == cudaErrorMemoryAllocation) return M2S_ERR_OOM;
+    return M2S_ERR_CUDA;
+}
+
+#define M2S_TRY(expr)                                  \
+    do {                                               \
+        cudaError_t e__ = (expr);                      \
+        if (e__ != cudaSuccess) return cuda_status(e__); \
+    } while (0)
+
+template <typename T>
+cudaError_t galloc(m2s_grid* g, T** p, i64 count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, (size_t)std::max<i64>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    g->allocs.push_back(v);
+    *p = (T*)v;
+    return cudaSuccess;
+}
+
+void destroy_grid(m2s_grid* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    for (auto& pl : g->units)
+        for (auto& u : pl) free_wave_units(&u);
+    for (void* p : g->allocs) cudaFree(p);
+    delete g;
+}
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+// Work set of the dtype of a call.
+template <typename T> Work<T>& work(m2s_grid* g);
+template <> Work<double>& work<double>(m2s_grid* g) { return g->w64; }
+template <> Work<float>& work<float>(m2s_grid* g) { return g->w32; }
+template <typename T> const KappaLevel<T>& klev(m2s_grid* g, int l);
+template <> const KappaLevel<double>& klev<double>(m2s_grid* g, int l) { return g->k64[l]; }
+template <> const KappaLevel<float>& klev<float>(m2s_grid* g, int l) { return g->k32[l]; }
+
+WaveCall wave_call(m2s_grid* g, int rev, double* rz) {
+    WaveCall c;
+    c.stall_unit = -1;
+    c.rev = rev;
+    c.publish_every = g->publish_every;
+    c.spin_ns = g->spin_ns;
+    c.status = g->status;
+    c.rz_partials = rz;
+    return c;
+}
+
+Dims coarse_of(m2s_grid* g, int i, int l) {
+    return (l + 1 < g->levels) ? g->dims[i][l + 1]
+                               : Dims{(g->dims[i][l].nx + 1) / 2, (g->dims[i][l].ny + 1) / 2,
+                                      (g->dims[i][l].nz + 1) / 2, 0, 0};
+}
+
+// ---------------------------------------------------------------------------
+// Operator-generic building blocks for problem i on level l.
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t op_spmv(m2s_grid* g, int i, int l, const T* x, T* y, cudaStream_t st) {
+    const Dims d = g->dims[i][l];
+    if (g->op == M2S_OP_HPCG27) return launch_st27<T>(ST27_SPMV, d, d, x, nullptr, nullptr, y, st);
+    return launch_spmv7<T>(d, klev<T>(g, l), x, y, st);
+}
+
+// Q = b + sum of the upper (up) or lower neighbours of (x + P xc).
+template <typename T>
+cudaError_t op_qinit(m2s_grid* g, int i, int l, int up, const T* x, const T* xc, const T* b, T* Q,
+                     cudaStream_t st) {
+    const Dims d = g->dims[i][l];
+    if (g->op == M2S_OP_HPCG27) {
+        if (xc) return launch_st27<T>(ST27_PROLONG_QUP, d, coarse_of(g, i, l), x, xc, b, Q, st);
+        return launch_st27<T>(up ? ST27_QUP : ST27_QLO, d, d, x, nullptr, b, Q, st);
+    }
+    return launch_qinit7<T>(d, xc ? coarse_of(g, i, l) : d, klev<T>(g, l), up, x, xc, b, Q, st);
+}
+
+template <typename T>
+cudaError_t op_sweep(m2s_grid* g, int i, int l, int rev, const T* Qin, T* Qout, const T* b, T* x,
+                     double* rz, cudaStream_t st) {
+    const Dims d = g->dims[i][l];
+    WaveCall c = wave_call(g, rev, rz);
+    if (g->stall_level == l && g->stall_unit >= 0) {
+        c.stall_unit = g->stall_unit;
+        g->stall_level = -1;
+        g->stall_unit = -1;
+    }
+    if (g->op == M2S_OP_HPCG27) return launch_gs27_wave<T>(g->units[i][l], c, d, Qin, Qout, b, x, st);
+    return launch_gs7_wave<T>(g->units[i][l], c, d, klev<T>(g, l), Qin, Qout, b, x, st);
+}
+
+template <typename T>
+cudaError_t op_restrict(m2s_grid* g, int i, int l, const T* r, const T* z, T* rc, cudaStream_t st) {
+    const Dims f = g->dims[i][l], c = g->dims[i][l + 1];
+    if (g->op == M2S_OP_HPCG27) return launch_restrict27<T>(f, c, r, z, rc, st);
+    return launch_restrict7<T>(f, c, klev<T>(g, l), r, z, rc, st);
+}
+
+// V-cycle of problem i from level l: z = M_l^-1 r (r, z packed level-l
+// arrays).  rz (optional) receives the per-unit partials of r.z from the
+// last sweep of the finest level.
+template <typename T>
+cudaError_t vcycle(m2s_grid* g, int i, int l, const T* r, T* z, double* rz, cudaStream_t st) {
+    Work<T>& w = work<T>(g);
+    T* Qa = w.Qa[l];
+    T* Qb = w.Qb[l];
+    cudaError_t e;
+    // pre-smoothing from z = 0: the old-neighbour sum is r itself
+    if ((e = op_sweep<T>(g, i, l, 0, r, Qb, r, z, nullptr, st)) != cudaSuccess) return e;
+    if (l == g->levels - 1)
+        return op_sweep<T>(g, i, l, 1, Qb, nullptr, r, z, rz, st);
+    if ((e = op_sweep<T>(g, i, l, 1, Qb, nullptr, r, z, nullptr, st)) != cudaSuccess) return e;
+    if ((e = op_restrict<T>(g, i, l, r, z, w.rc[l + 1], st)) != cudaSuccess) return e;
+    if ((e = vcycle<T>(g, i, l + 1, w.rc[l + 1], w.zc[l + 1], nullptr, st)) != cudaSuccess) return e;
+    // prolongation fused into the old-neighbour sum of the post-smoothing
+    if ((e = op_qinit<T>(g, i, l, 1, z, w.zc[l + 1], r, Qa, st)) != cudaSuccess) return e;
+    if ((e = op_sweep<T>(g, i, l, 0, Qa, Qb, r, z, nullptr, st)) != cudaSuccess) return e;
+    return op_sweep<T>(g, i, l, 1, Qb, nullptr, r, z, rz, st);
+}
+
+template <typename T>
+cudaError_t symgs(m2s_grid* g, int i, int l, const T* b, T* x, int sweeps, cudaStream_t st) {
+    Work<T>& w = work<T>(g);
+    cudaError_t e;
+    if ((e = op_qinit<T>(g, i, l, 1, x, nullptr, b, w.Qa[l], st)) != cudaSuccess) return e;
+    for (int s = 0; s < sweeps; ++s) {
+        if ((e = op_sweep<T>(g, i, l, 0, w.Qa[l], w.Qb[l], b, x, nullptr, st)) != cudaSuccess) return e;
+        T* qn = (s + 1 < sweeps) ? w.Qa[l] : nullptr;
+        if ((e = op_sweep<T>(g, i, l, 1, w.Qb[l], qn, b, x, nullptr, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t gs_sweep(m2s_grid* g, int i, int l, const T* b, T* x, int rev, cudaStream_t st) {
+    Work<T>& w = work<T>(g);
+    cudaError_t e;
+    if ((e = op_qinit<T>(g, i, l, rev ? 0 : 1, x, nullptr, b, w.Qa[l], st)) != cudaSuccess) return e;
+    return op_sweep<T>(g, i, l, rev, w.Qa[l], nullptr, b, x, nullptr, st);
+}
+
+bool valid_level(m2s_grid* g, int level) { return g && level >= 0 && level < g->levels; }
+
+m2s_status check_dtype(m2s_grid* g, m2s_dtype dt) {
+    if (dt == M2S_F64) return M2S_OK;
+    if (dt == M2S_F32 && g->has32) return M2S_OK;
+    return M2S_ERR_INVALID_ARG;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// ---------------------------------------------------------------------------
+// PCG for problem i (finest level): x0 = 0, r0 = b.
+// ---------------------------------------------------------------------------
+m2s_status pcg_problem(m2s_grid* g, int i, const double* b, double* x, const m2s_pcg_opts& o,
+                       m2s_pcg_result* out, cudaStream_t st) {
+    const Dims d = g->dims[i][0];
+    const i64 n = d.n, off = d.off;
+    double* r = g->r + off;
+    double* z = g->z + off;
+    double* zold = g->zold + off;
+    double* q = g->q + off;
+    const bool f32 = g->pdtype == M2S_F32;
+    const int nd = dot_num_partials(n);
+    const int nst = g->op == M2S_OP_HPCG27 ? st27_num_partials(d) : nd;
+    const int nu = g->units[i][0].n_units;
+
+    M2S_TRY(cudaMemsetAsync(x + off, 0, n * sizeof(double), st));
+    M2S_TRY(cudaMemcpyAsync(r, b + off, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    M2S_TRY(launch_dot_partials<double>(n, r, r, g->part, nd, st));
+    M2S_TRY(launch_finalize(FIN_BB, g->dev, g->part, nd, nullptr, 0, g->hist, st));
+    PcgDev h{};
+    int k = 0;
+    for (k = 1; k <= o.max_iters; ++k) {
+        // z = M^-1 r and rho = r.z
+        if (g->levels <= 0) {
+            M2S_TRY(cudaMemcpyAsync(z, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            M2S_TRY(launch_dot_partials<double>(n, r, z, g->part, nd, st));
+            M2S_TRY(launch_finalize(FIN_RHO, g->dev, g->part, nd, nullptr, 0, nullptr, st));
+        } else if (f32) {
+            M2S_TRY(launch_cast_down(n, r, g->r32 + off, st));
+            M2S_TRY(vcycle<float>(g, i, 0, g->r32, g->z32, nullptr, st));
+            double* zo = (k > 1) ? zold : nullptr;
+            M2S_TRY(launch_cast_up_dots(n, g->z32 + off, r, zo, z, g->part, g->part2, st));
+            M2S_TRY(launch_finalize(FIN_RHO, g->dev, g->part, nd, zo ? g->part2 : nullptr, nd,
+                                    nullptr, st));
+        } else {
+            M2S_TRY(vcycle<double>(g, i, 0, g->r, g->z, g->part, st));
+            M2S_TRY(launch_finalize(FIN_RHO, g->dev, g->part, nu, nullptr, 0, nullptr, st));
+        }
+        // p = z + beta p; q = A p; p.q   (p ping-pongs between p0 and p1)
+        double* pin_b = (k & 1) ? g->p1 : g->p0;
+        double* pout_b = (k & 1) ? g->p0 : g->p1;
+        double* pout = pout_b + off;
+        const double* beta = (k == 1) ? nullptr : &g->dev->beta;
+        if (g->op == M2S_OP_HPCG27) {
+            M2S_TRY(launch_pspmv_dot(d, g->z, pin_b, pout_b, g->q, beta, g->part, st));
+            M2S_TRY(launch_finalize(FIN_PQ, g->dev, g->part, nst, nullptr, 0, nullptr, st));
+        } else {
+            M2S_TRY(launch_paxpy(n, z, pin_b + off, pout, beta, st));
+            M2S_TRY(op_spmv<double>(g, i, 0, pout_b, g->q, st));
+            M2S_TRY(launch_dot_partials<double>(n, pout, q, g->part, nd, st));
+            M2S_TRY(launch_finalize(FIN_PQ, g->dev, g->part, nd, nullptr, 0, nullptr, st));
+        }
+        M2S_TRY(launch_update(n, g->dev, pout, q, x + off, r, g->part, st));
+        M2S_TRY(launch_finalize(FIN_RR, g->dev, g->part, nd, nullptr, 0, g->hist, st));
+        if (f32) std::swap(g->z, g->zold), z = g->z + off, zold = g->zold + off;
+        const bool last = k == o.max_iters;
+        if (!o.fixed_iters && (k % o.check_every == 0 || last)) {
+            M2S_TRY(cudaMemcpyAsync(&h, g->dev, sizeof(PcgDev), cudaMemcpyDeviceToHost, st));
+            M2S_TRY(cudaStreamSynchronize(st));
+            if (h.status != 0) break;
+            if (h.rr <= o.rtol * o.rtol * h.bb) break;
+        }
+    }
+    M2S_TRY(cudaMemcpyAsync(&h, g->dev, sizeof(PcgDev), cudaMemcpyDeviceToHost, st));
+    M2S_TRY(cudaStreamSynchronize(st));
+    DevStatus ds;
+    M2S_TRY(cudaMemcpy(&ds, g->status, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+    if (ds.err != 0) {
+        cudaMemset(g->status, 0, sizeof(DevStatus));
+        return (m2s_status)ds.err;
+    }
+    if (out) {
+        out->iters = h.iter;
+        out->resid_hist_last = std::sqrt(h.rr);
+        out->rel_resid = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+    }
+    if (h.status != 0) return M2S_ERR_BREAKDOWN;
+    if (!o.fixed_iters && !(h.rr <= o.rtol * o.rtol * h.bb) && h.bb > 0) return M2S_ERR_NOT_CONVERGED;
+    return M2S_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* m2s_status_string(m2s_status s) {
+    switch (s) {
+        case M2S_OK: return "ok";
+        case M2S_ERR_INVALID_ARG: return "invalid argument";
+        case M2S_ERR_CUDA: return "CUDA error";
+        case M2S_ERR_OOM: return "out of device memory";
+        case M2S_ERR_TIMEOUT: return "a bounded spin-wait expired";
+        case M2S_ERR_NOT_CONVERGED: return "not converged";
+        case M2S_ERR_BREAKDOWN: return "breakdown (non-finite value or p.Ap <= 0)";
+    }
+    return "unknown status";
+}
+
+m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* stream,
+                           m2s_grid** out) {
+    if (!out) return M2S_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!descs || n_problems < 1) return M2S_ERR_INVALID_ARG;
+    const m2s_op op = descs[0].op;
+    const int levels = descs[0].mg_levels;
+    const m2s_dtype pdt = descs[0].precond_dtype;
+    if (op != M2S_OP_HPCG27 && op != M2S_OP_DIFF7_KAPPA && op != M2S_OP_BLOCK7_5x5)
+        return M2S_ERR_INVALID_ARG;
+    if (levels < 1 || levels > kMaxLevels) return M2S_ERR_INVALID_ARG;
+    if (pdt != M2S_F64 && pdt != M2S_F32) return M2S_ERR_INVALID_ARG;
+    for (int i = 0; i < n_problems; ++i) {
+        const m2s_grid_desc& d = descs[i];
+        if (d.op != op || d.mg_levels != levels || d.precond_dtype != pdt) return M2S_ERR_INVALID_ARG;
+        if (d.nx < 1 || d.ny < 1 || d.nz < 1) return M2S_ERR_INVALID_ARG;
+        if ((i64)d.nx * d.ny * d.nz > (1LL << 34)) return M2S_ERR_INVALID_ARG;
+        if (op == M2S_OP_DIFF7_KAPPA && (!d.kappa || !aligned(d.kappa, 8))) return M2S_ERR_INVALID_ARG;
+        if (op == M2S_OP_BLOCK7_5x5 && (!d.D || !d.L || !d.U)) return M2S_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = S(stream);
+    m2s_grid* g = new (std::nothrow) m2s_grid();
+    if (!g) return M2S_ERR_OOM;
+    g->np = n_problems;
+    g->op = op;
+    g->levels = op == M2S_OP_BLOCK7_5x5 ? 1 : levels;
+    g->pdtype = pdt;
+    g->has32 = op == M2S_OP_HPCG27 || (op == M2S_OP_DIFF7_KAPPA && pdt == M2S_F32);
+    const int L = g->levels;
+    g->dims.assign(n_problems, std::vector<Dims>(L));
+    g->ltot.assign(L, 0);
+    for (int l = 0; l < L; ++l)
+        for (int i = 0; i < n_problems; ++i) {
+            Dims d;
+            if (l == 0) {
+                d.nx = descs[i].nx;
+                d.ny = descs[i].ny;
+                d.nz = descs[i].nz;
+            } else {
+                const Dims& f = g->dims[i][l - 1];
+                d.nx = (f.nx + 1) / 2;
+                d.ny = (f.ny + 1) / 2;
+                d.nz = (f.nz + 1) / 2;
+            }
+            d.n = (i64)d.nx * d.ny * d.nz;
+            d.off = g->ltot[l];
+            g->ltot[l] += d.n;
+            g->dims[i][l] = d;
+        }
+    auto fail = [&](cudaError_t e) {
+        destroy_grid(g);
+        return cuda_status(e);
+    };
+    cudaError_t e = cudaSuccess;
+    if ((e = galloc(g, &g->status, 1)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(g->status, 0, sizeof(DevStatus), st)) != cudaSuccess) return fail(e);
+    if ((e = galloc(g, &g->dev, 1)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(g->dev, 0, sizeof(PcgDev), st)) != cudaSuccess) return fail(e);
+
+    if (op == M2S_OP_BLOCK7_5x5) {
+        e = block_create(&g->blk, descs, n_problems, g->dims, st,
+                         [g](void** p, size_t bytes) -> cudaError_t {
+                             cudaError_t ee = cudaMalloc(p, bytes);
+                             if (ee == cudaSuccess) g->allocs.push_back(*p);
+                             return ee;
+                         });
+        if (e != cudaSuccess) return fail(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+        *out = g;
+        return M2S_OK;
+    }
+
+    // workspaces per level
+    g->w64.Qa.assign(L, nullptr); g->w64.Qb.assign(L, nullptr);
+    g->w64.rc.assign(L, nullptr); g->w64.zc.assign(L, nullptr);
+    g->w32.Qa.assign(L, nullptr); g->w32.Qb.assign(L, nullptr);
+    g->w32.rc.assign(L, nullptr); g->w32.zc.assign(L, nullptr);
+    for (int l = 0; l < L; ++l) {
+        if ((e = galloc(g, &g->w64.Qa[l], g->ltot[l])) != cudaSuccess) return fail(e);
+        if ((e = galloc(g, &g->w64.Qb[l], g->ltot[l])) != cudaSuccess) return fail(e);
+        if (l > 0) {
+            if ((e = galloc(g, &g->w64.rc[l], g->ltot[l])) != cudaSuccess) return fail(e);
+            if ((e = galloc(g, &g->w64.zc[l], g->ltot[l])) != cudaSuccess) return fail(e);
+        }
+        if (g->has32) {
+            if ((e = galloc(g, &g->w32.Qa[l], g->ltot[l])) != cudaSuccess) return fail(e);
+            if ((e = galloc(g, &g->w32.Qb[l], g->ltot[l])) != cudaSuccess) return fail(e);
+            if (l > 0) {
+                if ((e = galloc(g, &g->w32.rc[l], g->ltot[l])) != cudaSuccess) return fail(e);
+                if ((e = galloc(g, &g->w32.zc[l], g->ltot[l])) != cudaSuccess) return fail(e);
+            }
+        }
+    }
+    // kappa hierarchy
+    if (op == M2S_OP_DIFF7_KAPPA) {
+        g->kappa.assign(L, nullptr);
+        g->k64.resize(L);
+        g->k32.resize(L);
+        for (int l = 0; l < L; ++l) {
+            if ((e = galloc(g, &g->kappa[l], g->ltot[l])) != cudaSuccess) return fail(e);
+            KappaLevel<double>& k = g->k64[l];
+            for (int c = 0; c < 3; ++c)
+                if ((e = galloc(g, &k.kf[c], g->ltot[l])) != cudaSuccess) return fail(e);
+            if ((e = galloc(g, &k.diag, g->ltot[l])) != cudaSuccess) return fail(e);
+            if ((e = galloc(g, &k.invdiag, g->ltot[l])) != cudaSuccess) return fail(e);
+            if (g->has32) {
+                KappaLevel<float>& k3 = g->k32[l];
+                for (int c = 0; c < 3; ++c)
+                    if ((e = galloc(g, &k3.kf[c], g->ltot[l])) != cudaSuccess) return fail(e);
+                if ((e = galloc(g, &k3.diag, g->ltot[l])) != cudaSuccess) return fail(e);
+                if ((e = galloc(g, &k3.invdiag, g->ltot[l])) != cudaSuccess) return fail(e);
+            }
+        }
+        for (int i = 0; i < n_problems; ++i) {
+            const Dims& d = g->dims[i][0];
+            if ((e = cudaMemcpyAsync(g->kappa[0] + d.off, descs[i].kappa, d.n * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                return fail(e);
+            for (int l = 1; l < L; ++l)
+                if ((e = launch_kappa_coarsen(g->dims[i][l - 1], g->dims[i][l], g->kappa[l - 1],
+                                              g->kappa[l], st)) != cudaSuccess)
+                    return fail(e);
+            for (int l = 0; l < L; ++l) {
+                if ((e = launch_kappa_setup<double>(g->dims[i][l], g->kappa[l], g->k64[l], st)) !=
+                    cudaSuccess)
+                    return fail(e);
+                if (g->has32 &&
+                    (e = launch_kappa_setup<float>(g->dims[i][l], g->kappa[l], g->k32[l], st)) !=
+                        cudaSuccess)
+                    return fail(e);
+            }
+        }
+    }
+    // sweep schedules
+    g->units.assign(n_problems, std::vector<WaveUnits>(L));
+    const int stencil = op == M2S_OP_HPCG27 ? 27 : 7;
+    for (int i = 0; i < n_problems; ++i)
+        for (int l = 0; l < L; ++l)
+            if ((e = build_wave_units(stencil, kWaveK, g->dims[i][l], &g->units[i][l])) != cudaSuccess)
+                return fail(e);
+    // PCG vectors
+    const i64 n0 = g->ltot[0];
+    for (double** p : {&g->r, &g->z, &g->zold, &g->p0, &g->p1, &g->q})
+        if ((e = galloc(g, p, n0)) != cudaSuccess) return fail(e);
+    if (g->has32) {
+        if ((e = galloc(g, &g->r32, n0)) != cudaSuccess) return fail(e);
+        if ((e = galloc(g, &g->z32, n0)) != cudaSuccess) return fail(e);
+    }
+    int np = 0;
+    for (int i = 0; i < n_problems; ++i) {
+        np = std::max(np, dot_num_partials(g->dims[i][0].n));
+        np = std::max(np, st27_num_partials(g->dims[i][0]));
+        np = std::max(np, g->units[i][0].n_units);
+    }
+    g->npart = np;
+    if ((e = galloc(g, &g->part, np)) != cudaSuccess) return fail(e);
+    if ((e = galloc(g, &g->part2, np)) != cudaSuccess) return fail(e);
+    g->hist_cap = 4096;
+    if ((e = galloc(g, &g->hist, g->hist_cap + 1)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    *out = g;
+    return M2S_OK;
+}
+
+m2s_status m2s_grid_destroy(m2s_grid* grid) {
+    destroy_grid(grid);
+    return M2S_OK;
+}
+
+m2s_status m2s_debug_stall_unit(m2s_grid* grid, int level, int unit) {
+    if (!valid_level(grid, level) || unit < 0 || grid->op == M2S_OP_BLOCK7_5x5)
+        return M2S_ERR_INVALID_ARG;
+    grid->stall_level = level;
+    grid->stall_unit = unit;
+    return M2S_OK;
+}
+
+m2s_status m2s_set_spin_limit(m2s_grid* grid, long long limit_ns) {
+    if (!grid || limit_ns <= 0) return M2S_ERR_INVALID_ARG;
+    grid->spin_ns = limit_ns;
+    return M2S_OK;
+}
+
+long long m2s_grid_points(const m2s_grid* grid, int problem, int level) {
+    if (!grid || problem < 0 || problem >= grid->np || level < 0 || level >= grid->levels) return 0;
+    return grid->dims[problem][level].n;
+}
+
+m2s_status m2s_grid_sync(m2s_grid* grid, void* stream) {
+    if (!grid) return M2S_ERR_INVALID_ARG;
+    M2S_TRY(cudaStreamSynchronize(S(stream)));
+    DevStatus ds;
+    M2S_TRY(cudaMemcpy(&ds, grid->status, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+    if (ds.err != 0) {
+        M2S_TRY(cudaMemset(grid->status, 0, sizeof(DevStatus)));
+        return (m2s_status)ds.err;
+    }
+    return M2S_OK;
+}
+
+m2s_status m2s_spmv(m2s_grid* g, int level, m2s_dtype dtype, const void* x, void* y, void* stream) {
+    if (!valid_level(g, level) || !x || !y || x == y) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5) {
+        if (dtype != M2S_F64) return M2S_ERR_INVALID_ARG;
+        return cuda_status(block_apply(&g->blk, (const double*)x, (double*)y, S(stream)));
+    }
+    if (check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    for (int i = 0; i < g->np; ++i) {
+        if (dtype == M2S_F64) M2S_TRY(op_spmv<double>(g, i, level, (const double*)x, (double*)y, S(stream)));
+        else M2S_TRY(op_spmv<float>(g, i, level, (const float*)x, (float*)y, S(stream)));
+    }
+    return M2S_OK;
+}
+
+m2s_status m2s_symgs(m2s_grid* g, int level, m2s_dtype dtype, const void* b, void* x,
+                     int n_sym_sweeps, void* stream) {
+    if (!valid_level(g, level) || !b || !x || b == x || n_sym_sweeps < 0) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    if (n_sym_sweeps == 0) return M2S_OK;
+    for (int i = 0; i < g->np; ++i) {
+        if (dtype == M2S_F64)
+            M2S_TRY(symgs<double>(g, i, level, (const double*)b, (double*)x, n_sym_sweeps, S(stream)));
+        else
+            M2S_TRY(symgs<float>(g, i, level, (const float*)b, (float*)x, n_sym_sweeps, S(stream)));
+    }
+    return M2S_OK;
+}
+
+m2s_status m2s_gs_sweep(m2s_grid* g, int level, m2s_dtype dtype, const void* b, void* x,
+                        m2s_direction direction, void* stream) {
+    if (!valid_level(g, level) || !b || !x || b == x) return M2S_ERR_INVALID_ARG;
+    if (direction != M2S_FORWARD && direction != M2S_BACKWARD) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    const int rev = direction == M2S_BACKWARD;
+    for (int i = 0; i < g->np; ++i) {
+        if (dtype == M2S_F64)
+            M2S_TRY(gs_sweep<double>(g, i, level, (const double*)b, (double*)x, rev, S(stream)));
+        else
+            M2S_TRY(gs_sweep<float>(g, i, level, (const float*)b, (float*)x, rev, S(stream)));
+    }
+    return M2S_OK;
+}
+
+m2s_status m2s_mg_restrict(m2s_grid* g, int level, m2s_dtype dtype, const void* r, const void* z,
+                           void* rc, void* stream) {
+    if (!g || level < 0 || level + 1 >= g->levels || !r || !z || !rc) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    for (int i = 0; i < g->np; ++i) {
+        if (dtype == M2S_F64)
+            M2S_TRY(op_restrict<double>(g, i, level, (const double*)r, (const double*)z, (double*)rc, S(stream)));
+        else
+            M2S_TRY(op_restrict<float>(g, i, level, (const float*)r, (const float*)z, (float*)rc, S(stream)));
+    }
+    return M2S_OK;
+}
+
+m2s_status m2s_mg_prolong(m2s_grid* g, int level, m2s_dtype dtype, const void* zc, void* z,
+                          void* stream) {
+    if (!g || level < 0 || level + 1 >= g->levels || !zc || !z) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    for (int i = 0; i < g->np; ++i) {
+        const Dims f = g->dims[i][level], c = g->dims[i][level + 1];
+        if (dtype == M2S_F64) M2S_TRY(launch_prolong<double>(f, c, (const double*)zc, (double*)z, S(stream)));
+        else M2S_TRY(launch_prolong<float>(f, c, (const float*)zc, (float*)z, S(stream)));
+    }
+    return M2S_OK;
+}
+
+m2s_status m2s_mg_vcycle(m2s_grid* g, m2s_dtype dtype, const void* r, void* z, void* stream) {
+    if (!g || !r || !z || r == z) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    for (int i = 0; i < g->np; ++i) {
+        if (dtype == M2S_F64)
+            M2S_TRY(vcycle<double>(g, i, 0, (const double*)r, (double*)z, nullptr, S(stream)));
+        else
+            M2S_TRY(vcycle<float>(g, i, 0, (const float*)r, (float*)z, nullptr, S(stream)));
+    }
+    return M2S_OK;
+}
+
+m2s_status m2s_pcg_solve(m2s_grid* g, const double* b, double* x, const m2s_pcg_opts* opts,
+                         m2s_pcg_result* out, void* stream) {
+    if (!g || !b || !x || !opts || b == x) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    m2s_pcg_opts o = *opts;
+    if (o.max_iters < 1 || o.max_iters > g->hist_cap || !(o.rtol >= 0)) return M2S_ERR_INVALID_ARG;
+    if (o.check_every < 1) o.check_every = 1;
+    m2s_status worst = M2S_OK;
+    m2s_pcg_result agg{};
+    agg.rel_resid = 0;
+    for (int i = 0; i < g->np; ++i) {
+        m2s_pcg_result res{};
+        m2s_status s = pcg_problem(g, i, b, x, o, &res, S(stream));
+        if (s != M2S_OK && worst == M2S_OK) worst = s;
+        if (s == M2S_ERR_TIMEOUT || s == M2S_ERR_CUDA || s == M2S_ERR_OOM) return s;
+        agg.iters = std::max(agg.iters, res.iters);
+        agg.rel_resid = std::max(agg.rel_resid, res.rel_resid);
+        agg.resid_hist_last = std::max(agg.resid_hist_last, res.resid_hist_last);
+    }
+    if (out) *out = agg;
+    return worst;
+}
+
+m2s_status m2s_kappa_grad(m2s_grid* g, const double* u, const double* lambda, double* dLdkappa,
+                          void* stream) {
+    if (!g || !u || !lambda || !dLdkappa || g->op != M2S_OP_DIFF7_KAPPA) return M2S_ERR_INVALID_ARG;
+    for (int i = 0; i < g->np; ++i)
+        M2S_TRY(launch_kappa_grad(g->dims[i][0], u, lambda, dLdkappa, S(stream)));
+    return M2S_OK;
+}
+
+m2s_status m2s_adjoint_solve(m2s_grid* g, const double* u, const double* dLdu, double* lambda,
+                             double* dLdkappa, const m2s_pcg_opts* opts, m2s_pcg_result* out,
+                             void* stream) {
+    if (!g || !u || !dLdu || !lambda || !dLdkappa || !opts) return M2S_ERR_INVALID_ARG;
+    if (g->op != M2S_OP_DIFF7_KAPPA) return M2S_ERR_INVALID_ARG;
+    // A is symmetric (k_f is the same for both cells of a face), so A^T = A
+    // and the transposed V-cycle -- transposed sweeps in mirrored order --
+    // is the V-cycle itself: the adjoint solve is PCG on A lambda = dL/du.
+    m2s_status s = m2s_pcg_solve(g, dLdu, lambda, opts, out, stream);
+    if (s != M2S_OK && s != M2S_ERR_NOT_CONVERGED) return s;
+    m2s_status s2 = m2s_kappa_grad(g, u, lambda, dLdkappa, stream);
+    if (s2 != M2S_OK) return s2;
+    M2S_TRY(cudaStreamSynchronize(S(stream)));
+    return s;
+}
+
+m2s_status m2s_ssor_sweep(m2s_grid* g, const double* b, double* u, double omega, int n_iters,
+                          void* stream) {
+    if (!g || !b || !u || b == u || g->op != M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (!(omega > 0.0 && omega < 2.0) || n_iters < 0) return M2S_ERR_INVALID_ARG;
+    for (int it = 0; it < n_iters; ++it)
+        M2S_TRY(block_ssor_iter(&g->blk, b, u, omega, g->status, g->spin_ns, S(stream)));
+    return M2S_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,37 @@
+// 5x5-block 7-point operator (NPB-LU shape) and its SSOR step.
+#pragma once
+#include <functional>
+#include <vector>
+
+#include "m2s_internal.cuh"
+
+namespace m2s {
+
+struct BlockOp {
+    int np = 0;
+    std::vector<Dims> dims;     // per problem (points; vectors hold 5 per point)
+    i64 npts = 0;               // total points
+    double* D = nullptr;        // [npts][25]
+    double* L = nullptr;        // [npts][3][25]  couplings to p - e_{x,y,z}
+    double* U = nullptr;        // [npts][3][25]  couplings to p + e_{x,y,z}
+    double* Dinv = nullptr;     // [npts][25]
+    double* M = nullptr;        // [npts][3][25]  omega D^-1 L (0 off the grid)
+    double* N = nullptr;        // [npts][3][25]  omega D^-1 U (0 off the grid)
+    double* s = nullptr;        // [npts][5] D^-1 (b - A u)
+    double* v = nullptr;        // [npts][5] lower-sweep result
+    double* w = nullptr;        // [npts][5] upper-sweep result
+    double omega = -1.0;        // omega that M and N were built for
+    std::vector<WaveUnits> units;  // per problem
+};
+
+using BlockAlloc = std::function<cudaError_t(void**, size_t)>;
+
+cudaError_t block_create(BlockOp* b, const m2s_grid_desc* descs, int n_problems,
+                         const std::vector<std::vector<Dims>>& dims, cudaStream_t st,
+                         BlockAlloc alloc);
+cudaError_t block_apply(BlockOp* b, const double* u, double* y, cudaStream_t st);
+cudaError_t block_ssor_iter(BlockOp* b, const double* rhs, double* u, double omega,
+                            DevStatus* status, long long spin_ns, cudaStream_t st);
+void block_free_units(BlockOp* b);
+
+}  // namespace m2s

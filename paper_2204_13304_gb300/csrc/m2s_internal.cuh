@@ -1,0 +1,149 @@
+// Internal declarations of the m2s CUDA library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/m2s.h"
+
+namespace m2s {
+
+typedef long long i64;
+
+// Extents of one grid level of one problem and where its arrays start in the
+// packed batch vectors.
+struct Dims {
+    int nx, ny, nz;
+    i64 n;        // nx*ny*nz
+    i64 off;      // element offset of this problem in packed vectors
+};
+
+// Device-side status words of a grid (one allocation).
+struct DevStatus {
+    int err;        // first error code raised by a kernel (0 = none)
+    int abort;      // set together with err: every waiting unit stops
+    int pad[14];
+};
+
+// ---------------------------------------------------------------------------
+// Memory-model helpers (PTX ISA: release/acquire at gpu scope).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T> struct Lit;
+template <> struct Lit<double> {
+    static __device__ __forceinline__ double inv26() { return 1.0 / 26.0; }
+};
+template <> struct Lit<float> {
+    static __device__ __forceinline__ float inv26() { return 1.0f / 26.0f; }
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the kernel translation units).
+// ---------------------------------------------------------------------------
+
+// 27-point stencil tile kernels (k_stencil27.cu).
+enum St27Mode {
+    ST27_SPMV = 0,        // y = A x
+    ST27_PSPMV_DOT = 1,   // p = z + beta p (stored), q = A p, partial p.q
+    ST27_QUP = 2,         // Q = b + sum of the 13 upper neighbours of x
+    ST27_QLO = 3,         // Q = b + sum of the 13 lower neighbours of x
+    ST27_PROLONG_QUP = 4  // Q = b + upper sums of (x + P xc)  (x not written)
+};
+template <typename T>
+cudaError_t launch_st27(St27Mode mode, Dims d, Dims dc, const T* x, const T* xc, const T* b, T* y,
+                        cudaStream_t st);
+int st27_num_partials(Dims d);
+
+template <typename T>
+cudaError_t launch_restrict27(Dims f, Dims c, const T* r, const T* z, T* rc,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_prolong(Dims f, Dims c, const T* zc, T* z, cudaStream_t st);
+
+// Wavefront Gauss-Seidel (k_wave.cu).
+struct WaveUnits {
+    int n_units;      // units in ticket (topological) order
+    int2* d_origin;   // (u0, v0) of each unit
+    int4* d_prod;     // producer unit indices (left, below, below-left, -1)
+    int* d_flags;     // progress word per unit (0 at rest)
+    int* d_ctrl;      // [0] ticket, [1] exited CTAs
+    int grid;         // CTAs launched
+    int K;            // slots per lane (incl. the halo slot)
+    int stencil;      // 27 or 7
+};
+struct WaveCall {
+    int rev;              // 0 forward, 1 backward (reflected index space)
+    int publish_every;    // steps between progress publications
+    long long spin_ns;    // bound of every spin-wait
+    DevStatus* status;
+    double* rz_partials;  // per unit b.x partials of the new x, or NULL
+    int stall_unit;       // test hook: this unit neither computes nor
+                          // publishes (-1 = none), so its consumers' bounded
+                          // waits expire and the sweep reports a timeout
+};
+template <typename T>
+cudaError_t launch_gs27_wave(const WaveUnits& u, const WaveCall& c, Dims d,
+                             const T* Qin, T* Qout, const T* b, T* x,
+                             cudaStream_t st);
+// Face coefficients of the variable-kappa operator of one level: kf[d][p] is
+// the coefficient of the face between p and p - e_d (0 on the boundary).
+template <typename T>
+struct KappaLevel {
+    T* kf[3];
+    T* diag;
+    T* invdiag;
+};
+template <typename T>
+cudaError_t launch_gs7_wave(const WaveUnits& u, const WaveCall& c, Dims d,
+                            const KappaLevel<T>& k, const T* Qin, T* Qout,
+                            const T* b, T* x, cudaStream_t st);
+
+// Variable-kappa 7-point kernels (k_kappa7.cu).
+cudaError_t launch_kappa_coarsen(Dims f, Dims c, const double* kf, double* kc,
+                                 cudaStream_t st);
+template <typename T>
+cudaError_t launch_kappa_setup(Dims d, const double* kappa, KappaLevel<T> k,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_spmv7(Dims d, const KappaLevel<T>& k, const T* x, T* y,
+                         cudaStream_t st);
+// Q = b + sum over upper (up=1) or lower (up=0) faces of k_f x_q, with
+// x = x + P xc when xc != NULL (prolongation fused; x is not written).
+template <typename T>
+cudaError_t launch_qinit7(Dims d, Dims dc, const KappaLevel<T>& k, int up,
+                          const T* x, const T* xc, const T* b, T* Q,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict7(Dims f, Dims c, const KappaLevel<T>& k,
+                             const T* r, const T* z, T* rc, cudaStream_t st);
+cudaError_t launch_kappa_grad(Dims d, const double* u, const double* lam,
+                              double* g, cudaStream_t st);
+cudaError_t build_wave_units(int stencil, int K, Dims d, WaveUnits* out);
+cudaError_t build_units(int lanes, int skew, int corner, int K, Dims d, int per_sm,
+                        WaveUnits* out);
+void free_wave_units(WaveUnits* u);
+
+// Vector kernels (k_vec.cu).
+template <typename T>
+cudaError_t launch_dot_partials(i64 n, const T* a, const T* b, double* partials,
+                                int nparts, cudaStream_t st);
+int dot_num_partials(i64 n);
+
+}  // namespace m2s

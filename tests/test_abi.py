@@ -1,0 +1,76 @@
+"""CPU-side checks of the boundary: the library builds for sm_103a, loads,
+exports every function include/m2s.h declares, and rejects invalid
+arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2204_13304_gb300 import build as b
+    b.build()
+    import paper_2204_13304_gb300 as m
+    return m.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "m2s.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(m2s_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("m2s_grid_create", "m2s_grid_destroy", "m2s_spmv", "m2s_symgs",
+                 "m2s_ssor_sweep", "m2s_mg_vcycle", "m2s_pcg_solve", "m2s_adjoint_solve"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header():
+    import paper_2204_13304_gb300 as m
+    assert set(m.EXPORTS) == set(declared_functions())
+    for name in m.EXPORTS:
+        assert callable(getattr(m, name))
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert lib.m2s_status_string(s)
+    assert b"timeout" in lib.m2s_status_string(4) or b"spin" in lib.m2s_status_string(4)
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    import paper_2204_13304_gb300 as m
+    h = ctypes.c_void_p()
+    assert lib.m2s_grid_create(None, 1, None, ctypes.byref(h)) == m.Status.INVALID_ARG
+    d = (m.GridDesc * 1)()
+    d[0].nx, d[0].ny, d[0].nz, d[0].op, d[0].mg_levels = 0, 4, 4, 0, 1
+    assert lib.m2s_grid_create(d, 1, None, ctypes.byref(h)) == m.Status.INVALID_ARG
+    assert not h.value
+    d[0].nx, d[0].mg_levels = 4, 0
+    assert lib.m2s_grid_create(d, 1, None, ctypes.byref(h)) == m.Status.INVALID_ARG
+    d[0].mg_levels, d[0].op = 2, 1  # kappa operator without kappa
+    assert lib.m2s_grid_create(d, 1, None, ctypes.byref(h)) == m.Status.INVALID_ARG
+    assert lib.m2s_grid_create(d, 0, None, ctypes.byref(h)) == m.Status.INVALID_ARG
+    assert lib.m2s_spmv(None, 0, 0, None, None, None) == m.Status.INVALID_ARG
+    assert lib.m2s_symgs(None, 0, 0, None, None, 1, None) == m.Status.INVALID_ARG
+    assert lib.m2s_pcg_solve(None, None, None, None, None, None) == m.Status.INVALID_ARG
+    assert lib.m2s_ssor_sweep(None, None, None, 1.2, 1, None) == m.Status.INVALID_ARG
+    assert lib.m2s_grid_destroy(None) == m.Status.OK
+
+
+def test_library_is_sm103a_only():
+    """The build targets exactly compute_103a/sm_103a."""
+    from paper_2204_13304_gb300 import build as b
+    assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert "--use_fast_math" not in b.FLAGS

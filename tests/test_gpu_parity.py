@@ -1,0 +1,436 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the serial
+oracle, element by element, on the same seeded inputs.
+
+Tolerances (per entry, e_i = |g_i - o_i| / max(|o_i|, f |o|_inf)):
+  * FP64, workload-shaped data (b = A*ones, x0 = 0 as in the HPCG configs):
+    every term is non-negative, no cancellation: f = 1e-3, e <= 1e-13.
+  * FP64, random-sign stress data: the GPU re-associates sums (separable
+    3x3x3 box sums, a rounded 1/26 or 1/diag, old/new neighbour sums split),
+    so entries near a zero crossing differ by a few ulps of |o|_inf; one
+    sweep's rounding error is <= gamma_27 * sum|terms| / a_pp ~ 3e-15 |o|_inf
+    and ten contracting sweeps stay below ~3e-14 |o|_inf.  f = 1e-2 keeps
+    the bound 1e-13 (i.e. 1e-15 |o|_inf absolute at small entries) while any
+    reordering of the sweep shows at 1e-3..1e-2.
+  * FP32 against the FP32 oracle: the same reasoning with 2^-24: f = 1e-1,
+    e <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import m2s_inputs as gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+H27, K7 = oracle.HPCG27, oracle.KAPPA7
+TOL64 = 1e-13
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def m():
+    from paper_2204_13304_gb300 import build
+    build.build()
+    import paper_2204_13304_gb300 as m
+    m.load()
+    return m
+
+
+def err(g, o, floor=1e-3):
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    scale = np.max(np.abs(o)) if o.size else 0.0
+    if scale == 0.0:
+        return float(np.max(np.abs(g))) if g.size else 0.0
+    den = np.maximum(np.abs(o), floor * scale)
+    return float(np.max(np.abs(g - o) / den))
+
+
+def err64(g, o):
+    return err(g, o, floor=1e-2)
+
+
+def err32(g, o):
+    return err(g, o, floor=1e-1)
+
+
+def dev(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rnd(shape, k):
+    return gen.random_vector(shape, seed=gen.BASE_SEED + 101 * k)
+
+
+def make_grid(m, shape, op=0, levels=1, kappa=None, pdt=0):
+    nz, ny, nx = shape
+    d = dict(nx=nx, ny=ny, nz=nz, op=op, mg_levels=levels, precond_dtype=pdt)
+    if kappa is not None:
+        d["kappa"] = dev(kappa)
+    return m.Grid([d])
+
+
+SHAPES = [(1, 1, 1), (2, 3, 1), (3, 4, 5), (5, 3, 4), (7, 17, 5), (17, 33, 32), (33, 17, 35),
+          (32, 32, 32)]
+
+
+def kappa_for(shape, k=0):
+    return np.exp(rnd(shape, 500 + k))
+
+
+# ---------------------------------------------------------------------------
+# a1: SpMV
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_spmv_f64(m, kind, shape):
+    import torch
+    kap = kappa_for(shape) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, kappa=kap)
+    x = rnd(shape, 1)
+    y = torch.empty(shape, dtype=torch.float64, device="cuda")
+    m.m2s_spmv(g.handle, 0, dev(x), y)
+    assert err64(host(y), oracle.apply(kind, x, kap)) <= TOL64
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (17, 33, 32), (32, 32, 32)])
+def test_spmv27_integer_data_bitwise(m, shape):
+    import torch
+    g = make_grid(m, shape)
+    y = torch.empty(shape, dtype=torch.float64, device="cuda")
+    m.m2s_spmv(g.handle, 0, torch.ones(shape, dtype=torch.float64, device="cuda"), y)
+    assert np.array_equal(host(y), oracle.apply(H27, np.ones(shape)))
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (17, 33, 32)])
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_spmv_f32(m, kind, shape):
+    import torch
+    kap = kappa_for(shape) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, kappa=kap, pdt=1)
+    x = rnd(shape, 2).astype(np.float32)
+    y = torch.empty(shape, dtype=torch.float32, device="cuda")
+    m.m2s_spmv(g.handle, 0, dev(x), y)
+    want = oracle.apply_f32(kind, x, None if kap is None else kap.astype(np.float32))
+    assert err32(host(y), want) <= TOL32
+
+
+# ---------------------------------------------------------------------------
+# a2-a4: Gauss-Seidel sweeps (exact lexicographic order)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_single_sweeps(m, kind, shape):
+    kap = kappa_for(shape, 1) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, kappa=kap)
+    b, x0 = rnd(shape, 3), rnd(shape, 4)
+    x = dev(x0)
+    m.m2s_gs_sweep(g.handle, 0, dev(b), x, m.FORWARD)
+    assert err64(host(x), oracle.gs_forward(kind, b, x0, kap)) <= TOL64
+    x = dev(x0)
+    m.m2s_gs_sweep(g.handle, 0, dev(b), x, m.BACKWARD)
+    assert err64(host(x), oracle.gs_backward(kind, b, x0, kap)) <= TOL64
+
+
+@pytest.mark.parametrize("shape", [(5, 3, 4), (17, 33, 32), (33, 17, 35), (40, 40, 40)])
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_symgs_ten_sweeps(m, kind, shape):
+    """10 consecutive symmetric sweeps: a reordering would show at ~1e-2."""
+    kap = kappa_for(shape, 2) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, kappa=kap)
+    b, x0 = rnd(shape, 5), rnd(shape, 6)
+    x = dev(x0)
+    m.m2s_symgs(g.handle, 0, dev(b), x, 10)
+    assert err64(host(x), oracle.symgs(kind, b, x0, 10, kap)) <= TOL64
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (33, 17, 35), (64, 64, 64)])
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_symgs_ten_sweeps_workload_data(m, kind, shape):
+    """b = A*ones, x0 = 0 (the configs' data): pure per-entry 1e-13."""
+    import torch
+    kap = kappa_for(shape, 12) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, kappa=kap)
+    b = oracle.apply(kind, np.ones(shape), kap)
+    x = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    m.m2s_symgs(g.handle, 0, dev(b), x, 10)
+    assert err(host(x), oracle.symgs(kind, b, np.zeros(shape), 10, kap)) <= TOL64
+
+
+def test_symgs_fixed_point_bitwise(m):
+    import torch
+    shape = (33, 17, 35)
+    g = make_grid(m, shape)
+    b = oracle.apply(H27, np.ones(shape))
+    x = torch.ones(shape, dtype=torch.float64, device="cuda")
+    m.m2s_symgs(g.handle, 0, dev(b), x, 3)
+    assert np.array_equal(host(x), np.ones(shape))
+
+
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_symgs_f32(m, kind):
+    shape = (17, 33, 32)
+    kap = kappa_for(shape, 3) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, kappa=kap, pdt=1)
+    b, x0 = rnd(shape, 7).astype(np.float32), rnd(shape, 8).astype(np.float32)
+    x = dev(x0)
+    m.m2s_symgs(g.handle, 0, dev(b), x, 2)
+    want = oracle.symgs_f32(kind, b, x0, 2, None if kap is None else kap.astype(np.float32))
+    assert err32(host(x), want) <= TOL32
+
+
+def test_negative_control_is_detectable(m):
+    """A multicolour sweep (not the method) differs from the GPU result by far
+    more than the tolerance: the comparison would catch a reordering."""
+    shape = (16, 16, 16)
+    g = make_grid(m, shape)
+    b = rnd(shape, 9)
+    x = dev(np.zeros(shape))
+    mc = np.zeros(shape)
+    for _ in range(10):
+        m.m2s_gs_sweep(g.handle, 0, dev(b), x, m.FORWARD)
+        mc = oracle.gs_multicolor_forward(H27, b, mc)
+    assert err(host(x), mc) > 1e-3
+
+
+def test_sweep_timeout_is_reported_and_recoverable(m):
+    """Host-injected stall: one unit never publishes; its consumers' bounded
+    waits expire; the call reports TIMEOUT and the next sweep is correct."""
+    shape = (32, 32, 32)
+    g = make_grid(m, shape)
+    m.m2s_set_spin_limit(g.handle, 50_000_000)
+    b, x0 = rnd(shape, 10), rnd(shape, 11)
+    m.m2s_debug_stall_unit(g.handle, 0, 0)
+    x = dev(x0)
+    m.m2s_gs_sweep(g.handle, 0, dev(b), x, m.FORWARD)
+    with pytest.raises(m.M2SError) as ei:
+        m.m2s_grid_sync(g.handle)
+    assert ei.value.status == m.Status.TIMEOUT
+    x = dev(x0)
+    m.m2s_gs_sweep(g.handle, 0, dev(b), x, m.FORWARD)
+    m.m2s_grid_sync(g.handle)
+    assert err64(host(x), oracle.gs_forward(H27, b, x0)) <= TOL64
+
+
+# ---------------------------------------------------------------------------
+# a5-a7: restriction, prolongation, V-cycle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(5, 7, 4), (17, 33, 32), (32, 32, 32)])
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_restrict_prolong(m, kind, shape):
+    import torch
+    kap = kappa_for(shape, 4) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, levels=2, kappa=kap)
+    r, z = rnd(shape, 12), rnd(shape, 13)
+    cs = tuple((n + 1) // 2 for n in shape)
+    rc = torch.empty(cs, dtype=torch.float64, device="cuda")
+    m.m2s_mg_restrict(g.handle, 0, dev(r), dev(z), rc)
+    assert err64(host(rc), oracle.restrict_residual(kind, r, z, kap)) <= TOL64
+    zc = rnd(cs, 14)
+    zz = dev(z)
+    m.m2s_mg_prolong(g.handle, 0, dev(zc), zz)
+    assert np.array_equal(host(zz), oracle.prolong_add(zc, z))
+
+
+@pytest.mark.parametrize("shape,levels", [((32, 32, 32), 4), ((33, 17, 35), 3), ((5, 3, 4), 2),
+                                          ((64, 64, 64), 4)])
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_vcycle_f64(m, kind, shape, levels):
+    import torch
+    kap = kappa_for(shape, 5) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, levels=levels, kappa=kap)
+    r = rnd(shape, 15)
+    z = torch.empty(shape, dtype=torch.float64, device="cuda")
+    m.m2s_mg_vcycle(g.handle, dev(r), z)
+    assert err64(host(z), oracle.mg_vcycle(kind, r, levels, kap)) <= TOL64
+
+
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_vcycle_f32(m, kind):
+    import torch
+    shape = (32, 32, 32)
+    kap = kappa_for(shape, 6) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, levels=4, kappa=kap, pdt=1)
+    r = rnd(shape, 16).astype(np.float32)
+    z = torch.empty(shape, dtype=torch.float32, device="cuda")
+    m.m2s_mg_vcycle(g.handle, dev(r), z)
+    assert err32(host(z), oracle.mg_vcycle_f32(kind, r, 4, kap)) <= TOL32
+
+
+# ---------------------------------------------------------------------------
+# a8: PCG (HPCG 32^3: SGS-PCG; MG-PCG)
+# ---------------------------------------------------------------------------
+def test_hpcg_32_sgs_pcg_50(m):
+    """32^3, b = A*ones, x0 = 0: one SpMV, one SymGS, 50 SGS-PCG iterations."""
+    import torch
+    shape = (32, 32, 32)
+    g = make_grid(m, shape, levels=1)
+    ones = torch.ones(shape, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(ones)
+    m.m2s_spmv(g.handle, 0, ones, b)
+    bh = host(b)
+    assert np.array_equal(bh, oracle.apply(H27, np.ones(shape)))
+    xs = torch.zeros_like(ones)
+    m.m2s_symgs(g.handle, 0, b, xs, 1)
+    assert err(host(xs), oracle.symgs(H27, bh, np.zeros(shape), 1)) <= TOL64
+    x = torch.empty_like(ones)
+    st, res = m.m2s_pcg_solve(g.handle, b, x, max_iters=50, fixed_iters=True)
+    ox, oit, ohist, ost = oracle.pcg(H27, bh, 1, max_iters=50, fixed_iters=True)
+    assert st == m.Status.OK and res.iters == 50
+    assert err(host(x), ox) <= TOL64
+    assert abs(res.resid_hist_last - ohist[-1]) <= 1e-9 * ohist[0]
+
+
+@pytest.mark.parametrize("kind,shape,levels", [(H27, (64, 64, 64), 4), (K7, (48, 48, 48), 3),
+                                               (H27, (33, 17, 35), 3)])
+def test_mg_pcg_f64(m, kind, shape, levels):
+    import torch
+    kap = gen.kappa_field(0, seed=21, shape=shape) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, levels=levels, kappa=kap)
+    bh = oracle.apply(kind, np.ones(shape), kap)
+    x = torch.empty(shape, dtype=torch.float64, device="cuda")
+    st, res = m.m2s_pcg_solve(g.handle, dev(bh), x, max_iters=20, fixed_iters=True)
+    ox, oit, ohist, ost = oracle.pcg(kind, bh, levels, kap, max_iters=20, fixed_iters=True)
+    assert st == m.Status.OK and res.iters == 20
+    assert err(host(x), ox) <= TOL64
+    assert abs(res.resid_hist_last - ohist[-1]) <= 1e-8 * ohist[-1] + 1e-14 * ohist[0]
+
+
+@pytest.mark.parametrize("kind", [H27, K7])
+def test_fp32_preconditioned_pcg(m, kind):
+    """Form 1: FP32 V-cycle inside FP64 flexible CG reaches 1e-10; its error
+    against the FP64 oracle solution is stated (asserted small)."""
+    import torch
+    shape = (32, 32, 32)
+    kap = gen.kappa_field(0, seed=22, shape=shape) if kind == K7 else None
+    g = make_grid(m, shape, op=kind, levels=4, kappa=kap, pdt=1)
+    bh = oracle.apply(kind, np.ones(shape), kap)
+    x = torch.empty(shape, dtype=torch.float64, device="cuda")
+    st, res = m.m2s_pcg_solve(g.handle, dev(bh), x, max_iters=200, rtol=1e-10, fixed_iters=False)
+    assert st == m.Status.OK and res.rel_resid <= 1e-10
+    ox, oit, ohist, ost = oracle.pcg(kind, bh, 4, kap, max_iters=200, rtol=1e-10,
+                                     fixed_iters=False)
+    xo32, oit32, _, _ = oracle.pcg(kind, bh, 4, kap, max_iters=200, rtol=1e-10,
+                                   fixed_iters=False, precond_f32=True)
+    assert abs(res.iters - oit32) <= 2
+    e = np.max(np.abs(host(x) - ox)) / np.max(np.abs(ox))
+    assert e <= 1e-8
+
+
+# ---------------------------------------------------------------------------
+# a9-a11: block SSOR (NPB-LU shape)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(2, 4, 3), (9, 10, 12), (17, 6, 33)])
+def test_block_ssor(m, shape):
+    import torch
+    D, L, U, b = gen.block_ssor_inputs(0, shape=shape, seed=41)
+    nz, ny, nx = shape
+    g = m.Grid([dict(nx=nx, ny=ny, nz=nz, op=m.Op.BLOCK7_5x5, mg_levels=1,
+                     D=dev(D), L=dev(L), U=dev(U))])
+    u0 = rnd(shape + (5,), 17)
+    y = torch.empty(shape + (5,), dtype=torch.float64, device="cuda")
+    m.m2s_spmv(g.handle, 0, dev(u0), y)
+    assert err64(host(y), oracle.block_apply(D, L, U, u0)) <= TOL64
+    u = dev(u0)
+    m.m2s_ssor_sweep(g.handle, dev(b), u, 1.2, 5)
+    m.m2s_grid_sync(g.handle)
+    assert err64(host(u), oracle.ssor(D, L, U, 1.2, b, u0, 5)) <= TOL64
+
+
+def test_block_ssor_omega_change(m):
+    import torch
+    shape = (6, 5, 7)
+    D, L, U, b = gen.block_ssor_inputs(0, shape=shape, seed=42)
+    nz, ny, nx = shape
+    g = m.Grid([dict(nx=nx, ny=ny, nz=nz, op=m.Op.BLOCK7_5x5, mg_levels=1,
+                     D=dev(D), L=dev(L), U=dev(U))])
+    u = torch.zeros(shape + (5,), dtype=torch.float64, device="cuda")
+    m.m2s_ssor_sweep(g.handle, dev(b), u, 1.2, 3)
+    m.m2s_ssor_sweep(g.handle, dev(b), u, 0.8, 2)
+    want = oracle.ssor(D, L, U, 0.8, b, oracle.ssor(D, L, U, 1.2, b, np.zeros(shape + (5,)), 3), 2)
+    assert err64(host(u), want) <= TOL64
+
+
+# ---------------------------------------------------------------------------
+# a12: adjoint
+# ---------------------------------------------------------------------------
+def test_kappa_grad_and_adjoint(m):
+    import torch
+    shape = (16, 16, 16)
+    kap = gen.kappa_field(16, seed=23)
+    g = make_grid(m, shape, op=K7, levels=3, kappa=kap)
+    u, lam = rnd(shape, 18), rnd(shape, 19)
+    gg = torch.empty(shape, dtype=torch.float64, device="cuda")
+    m.m2s_kappa_grad(g.handle, dev(u), dev(lam), gg)
+    assert err64(host(gg), oracle.kappa_grad(u, lam)) <= TOL64
+    # adjoint solve against the oracle's PCG and gradient
+    ut = gen.target(shape, seed=24)
+    b = np.ones(shape)
+    uo, _, _, _ = oracle.pcg(K7, b, 3, kap, max_iters=200, rtol=1e-12, fixed_iters=False)
+    dLdu = uo - ut
+    lo, _, _, _ = oracle.pcg(K7, dLdu, 3, kap, max_iters=200, rtol=1e-12, fixed_iters=False)
+    go = oracle.kappa_grad(uo, lo)
+    lam_d = torch.empty(shape, dtype=torch.float64, device="cuda")
+    st, res = m.m2s_adjoint_solve(g.handle, dev(uo), dev(dLdu), lam_d, gg, max_iters=200,
+                                  rtol=1e-12)
+    assert st == m.Status.OK
+    assert err(host(gg), go) <= 1e-9
+
+
+def test_autograd_matches_finite_differences(m):
+    import torch
+    n = 12
+    kap = torch.from_numpy(gen.kappa_field(n, seed=25)).cuda().requires_grad_(True)
+    b = torch.ones((n, n, n), dtype=torch.float64, device="cuda")
+    ut = torch.from_numpy(gen.target((n, n, n), seed=26)).cuda()
+    u = m.pcg_solve(kap, b, mg_levels=3, rtol=1e-13, max_iters=500)
+    loss = 0.5 * ((u - ut) ** 2).sum()
+    loss.backward()
+    gk = kap.grad.detach().cpu().numpy()
+    k0 = kap.detach().cpu().numpy()
+
+    def L(k):
+        x, _, _, _ = oracle.pcg(K7, np.ones((n, n, n)), 3, k, max_iters=500, rtol=1e-13,
+                                fixed_iters=False)
+        return 0.5 * np.sum((x - ut.cpu().numpy()) ** 2)
+
+    for c in [(0, 0, 0), (n - 1, n - 1, n - 1), (0, 5, 7), (6, 0, 3), (5, 6, 7), (11, 2, 9)]:
+        h = 1e-5 * k0[c]
+        kp, km = k0.copy(), k0.copy()
+        kp[c] += h
+        km[c] -= h
+        fd = (L(kp) - L(km)) / (2 * h)
+        assert abs(fd - gk[c]) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(gk)))
+
+
+# ---------------------------------------------------------------------------
+# batch (form 2): packed problems of different sizes
+# ---------------------------------------------------------------------------
+def test_batched_problems(m):
+    import torch
+    shapes = [(16, 16, 16), (24, 24, 24), (12, 12, 12)]
+    kaps = [gen.kappa_field(s[0], seed=30 + i) for i, s in enumerate(shapes)]
+    descs = [dict(nx=s[2], ny=s[1], nz=s[0], op=m.Op.DIFF7_KAPPA, mg_levels=3, kappa=dev(k))
+             for s, k in zip(shapes, kaps)]
+    g = m.Grid(descs)
+    bs = [oracle.apply(K7, np.ones(s), k) for s, k in zip(shapes, kaps)]
+    b = dev(np.concatenate([x.ravel() for x in bs]))
+    x = torch.empty_like(b)
+    st, res = m.m2s_pcg_solve(g.handle, b, x, max_iters=10, fixed_iters=True)
+    xh = host(x)
+    off = 0
+    for s, k, bb in zip(shapes, kaps, bs):
+        n = int(np.prod(s))
+        ox, _, _, _ = oracle.pcg(K7, bb, 3, k, max_iters=10, fixed_iters=True)
+        assert err(xh[off:off + n].reshape(s), ox) <= TOL64
+        off += n
