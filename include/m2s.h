@@ -205,6 +205,31 @@ m2s_status m2s_kappa_grad(m2s_grid* grid, const double* u,
  * synchronising call. */
 m2s_status m2s_set_spin_limit(m2s_grid* grid, long long limit_ns);
 
+/* Symmetric Gauss-Seidel on the 27-point (HPCG) operator of an
+ * nx x ny x nz grid that allocates no device memory: n_sym_sweeps times one
+ * forward and one backward lexicographic sweep, exactly as m2s_symgs on a
+ * grid of that operator.  (The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate -- applications that reserve all
+ * device memory for their own pool, or latency-critical loops that cannot
+ * afford cudaMalloc's implicit synchronisation.)
+ *   b, x     device [nz][ny][nx] vectors of type dtype (x in/out, b and x
+ *            must not overlap).
+ *   limits   nx*ny*nz <= 262144 (64^3) points and at most 8192 wavefront
+ *            units; larger requests return M2S_ERR_INVALID_ARG before any
+ *            launch.
+ *   scratch  one fixed-size array (about 4.4 MB) in the library's static
+ *            device memory, shared by every call on every stream; the
+ *            counters that must start at zero are cleared by each call.
+ *            Calls that overlap on the GPU race on it: serialise them.
+ *   set-up   the first call on a device looks up the array's device address
+ *            (cudaGetSymbolAddress, that device current); make that first
+ *            call before any stream capture.
+ *   sync     synchronises `stream` before returning and reports an expired
+ *            spin-wait as M2S_ERR_TIMEOUT. */
+m2s_status m2s_symgs_noalloc(int nx, int ny, int nz, m2s_dtype dtype,
+                             const void* b, void* x, int n_sym_sweeps,
+                             void* stream);
+
 /* Fault-injection hook for tests (host side; nothing faults on the GPU):
  * in the next Gauss-Seidel sweep on `level`, wavefront unit `unit` (in ticket
  * order) neither computes nor publishes its progress.  The units that wait

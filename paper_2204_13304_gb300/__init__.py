@@ -71,7 +71,7 @@ EXPORTS = (
     "m2s_grid_create", "m2s_grid_destroy", "m2s_grid_sync", "m2s_grid_points", "m2s_spmv",
     "m2s_symgs", "m2s_gs_sweep", "m2s_mg_restrict", "m2s_mg_prolong", "m2s_mg_vcycle",
     "m2s_pcg_solve", "m2s_ssor_sweep", "m2s_adjoint_solve", "m2s_kappa_grad",
-    "m2s_set_spin_limit", "m2s_debug_stall_unit", "m2s_status_string",
+    "m2s_set_spin_limit", "m2s_debug_stall_unit", "m2s_symgs_noalloc", "m2s_status_string",
 )
 
 
@@ -108,6 +108,7 @@ def load():
         "m2s_kappa_grad": ([vp, vp, vp, vp, vp], i),
         "m2s_set_spin_limit": ([vp, ll], i),
         "m2s_debug_stall_unit": ([vp, i, i], i),
+        "m2s_symgs_noalloc": ([i, i, i, i, vp, vp, i, vp], i),
         "m2s_status_string": ([i], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -203,6 +204,16 @@ def m2s_set_spin_limit(grid, limit_ns):
 
 def m2s_debug_stall_unit(grid, level, unit):
     return _check(load().m2s_debug_stall_unit(grid, int(level), int(unit)), "m2s_debug_stall_unit")
+
+
+def m2s_symgs_noalloc(b, x, n_sym_sweeps=1, stream=None):
+    """Symmetric Gauss-Seidel (27-point operator) that allocates no device
+    memory, for callers that cannot allocate (its scratch is a fixed static
+    array of the library: at most 64^3 points; calls must not overlap)."""
+    nz, ny, nx = x.shape
+    return _check(load().m2s_symgs_noalloc(nx, ny, nz, _dtype(x), _ptr(b, "b"), _ptr(x, "x"),
+                                           int(n_sym_sweeps), _stream(stream)),
+                  "m2s_symgs_noalloc")
 
 
 def m2s_spmv(grid, level, x, y, stream=None):

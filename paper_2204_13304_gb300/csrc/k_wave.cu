@@ -277,14 +277,15 @@ __global__ void __launch_bounds__(32) gs7_wave_kernel(WaveArgs<T> a) {
 // `lanes` computing rows in u and K-1 computing slots in v, u = y + skew*z.
 // Producers: the unit to the left (u - lanes), below (v - (K-1)) and, when
 // `corner`, below-left.  Empty units (no row inside the grid) are dropped.
-cudaError_t build_units(int lanes, int skew, int corner, int K, Dims d, int per_sm,
-                        WaveUnits* out) {
+// Host only: fills `org` and `prod`.
+void build_units_host(int lanes, int skew, int corner, int K, Dims d, std::vector<int2>& org,
+                      std::vector<int4>& prod) {
     const int slots = K - 1;
     const int umax = (d.ny - 1) + skew * (d.nz - 1);
     const int NU = umax / lanes + 1;
     const int NV = (d.nz + slots - 1) / slots;
     std::vector<int> index((size_t)NU * NV, -1);
-    std::vector<int2> org;
+    org.clear();
     for (int V = 0; V < NV; ++V)
         for (int U = 0; U < NU; ++U) {
             const int u0 = U * lanes, v0 = V * slots;
@@ -298,7 +299,7 @@ cudaError_t build_units(int lanes, int skew, int corner, int K, Dims d, int per_
             index[(size_t)V * NU + U] = (int)org.size();
             org.push_back(make_int2(u0, v0));
         }
-    std::vector<int4> prod(org.size());
+    prod.assign(org.size(), make_int4(-1, -1, -1, -1));
     for (int V = 0; V < NV; ++V)
         for (int U = 0; U < NU; ++U) {
             const int id = index[(size_t)V * NU + U];
@@ -313,6 +314,31 @@ cudaError_t build_units(int lanes, int skew, int corner, int K, Dims d, int per_
             p.w = -1;
             prod[id] = p;
         }
+}
+
+// CTAs of a persistent sweep launch: as many single-warp CTAs as can be
+// resident, at most one per unit.
+int wave_grid(int n_units, int per_sm) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, std::min(n_units, sms * std::max(1, per_sm)));
+}
+
+int wave_blocks_per_sm(int stencil) {
+    int per_sm = 0;
+    if (stencil == 27)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs27_wave_kernel<double, 5>, 32, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs7_wave_kernel<double, 5>, 32, 0);
+    return std::max(1, per_sm);
+}
+
+cudaError_t build_units(int lanes, int skew, int corner, int K, Dims d, int per_sm,
+                        WaveUnits* out) {
+    std::vector<int2> org;
+    std::vector<int4> prod;
+    build_units_host(lanes, skew, corner, K, d, org, prod);
     WaveUnits u{};
     u.n_units = (int)org.size();
     u.K = K;
@@ -336,23 +362,14 @@ cudaError_t build_units(int lanes, int skew, int corner, int K, Dims d, int per_
         free_wave_units(&u);
         return e;
     }
-    // Persistent grid: as many single-warp CTAs as can be resident, at most
-    // one per unit.
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    u.grid = std::max(1, std::min(u.n_units, sms * std::max(1, per_sm)));
+    u.grid = wave_grid(u.n_units, per_sm);
     *out = u;
     return cudaSuccess;
 }
 
 cudaError_t build_wave_units(int stencil, int K, Dims d, WaveUnits* out) {
-    int per_sm = 0;
-    cudaError_t e;
-    if (stencil == 27)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs27_wave_kernel<double, 5>, 32, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs7_wave_kernel<double, 5>, 32, 0);
+    const int per_sm = wave_blocks_per_sm(stencil);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = stencil == 27 ? build_units(30, 1, 1, K, d, per_sm, out)
                       : build_units(31, 0, 0, K, d, per_sm, out);

@@ -138,6 +138,14 @@ cudaError_t launch_kappa_grad(Dims d, const double* u, const double* lam,
 cudaError_t build_wave_units(int stencil, int K, Dims d, WaveUnits* out);
 cudaError_t build_units(int lanes, int skew, int corner, int K, Dims d, int per_sm,
                         WaveUnits* out);
+}  // namespace m2s
+#include <vector>
+namespace m2s {
+void build_units_host(int lanes, int skew, int corner, int K, Dims d, std::vector<int2>& org,
+                      std::vector<int4>& prod);
+int wave_grid(int n_units, int per_sm);
+int wave_blocks_per_sm(int stencil);
+constexpr int kWaveSlots = 5;  // register slots per lane of the sweep kernels
 void free_wave_units(WaveUnits* u);
 
 // Vector kernels (k_vec.cu).
