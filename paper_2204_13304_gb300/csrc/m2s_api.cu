@@ -39,8 +39,9 @@ struct m2s_grid {
     std::vector<double*> kappa;
     std::vector<KappaLevel<double>> k64;
     std::vector<KappaLevel<float>> k32;
-    // sweep schedules per problem and level
+    // sweep schedules per problem and level (27-point: one set per dtype)
     std::vector<std::vector<WaveUnits>> units;
+    std::vector<std::vector<WaveUnits>> units32;
     Work<double> w64;
     Work<float> w32;
     // PCG state (finest level, packed)
@@ -89,6 +90,8 @@ void destroy_grid(m2s_grid* g) {
     if (!g) return;
     cudaDeviceSynchronize();
     for (auto& pl : g->units)
+        for (auto& u : pl) free_wave_units(&u);
+    for (auto& pl : g->units32)
         for (auto& u : pl) free_wave_units(&u);
     for (void* p : g->allocs) cudaFree(p);
     delete g;
@@ -153,7 +156,10 @@ cudaError_t op_sweep(m2s_grid* g, int i, int l, int rev, const T* Qin, T* Qout, 
         g->stall_level = -1;
         g->stall_unit = -1;
     }
-    if (g->op == M2S_OP_HPCG27) return launch_gs27_wave<T>(g->units[i][l], c, d, Qin, Qout, b, x, st);
+    if (g->op == M2S_OP_HPCG27) {
+        const WaveUnits& u = sizeof(T) == 8 ? g->units[i][l] : g->units32[i][l];
+        return launch_gs27_cta<T>(u, c, d, Qin, Qout, b, x, st);
+    }
     return launch_gs7_wave<T>(g->units[i][l], c, d, klev<T>(g, l), Qin, Qout, b, x, st);
 }
 
@@ -207,6 +213,9 @@ cudaError_t gs_sweep(m2s_grid* g, int i, int l, const T* b, T* x, int rev, cudaS
     return op_sweep<T>(g, i, l, rev, w.Qa[l], nullptr, b, x, nullptr, st);
 }
 
+// b.x partials written per sweep unit by the last sweep of a V-cycle
+int rz_per_unit(m2s_grid* g) { return g->op == M2S_OP_HPCG27 ? cta_units_per_rz(1) : 1; }
+
 bool valid_level(m2s_grid* g, int level) { return g && level >= 0 && level < g->levels; }
 
 m2s_status check_dtype(m2s_grid* g, m2s_dtype dt) {
@@ -231,7 +240,7 @@ m2s_status pcg_problem(m2s_grid* g, int i, const double* b, double* x, const m2s
     const bool f32 = g->pdtype == M2S_F32;
     const int nd = dot_num_partials(n);
     const int nst = g->op == M2S_OP_HPCG27 ? st27_num_partials(d) : nd;
-    const int nu = g->units[i][0].n_units;
+    const int nu = g->units[i][0].n_units * rz_per_unit(g);
 
     M2S_TRY(cudaMemsetAsync(x + off, 0, n * sizeof(double), st));
     M2S_TRY(cudaMemcpyAsync(r, b + off, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -454,11 +463,19 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     }
     // sweep schedules
     g->units.assign(n_problems, std::vector<WaveUnits>(L));
-    const int stencil = op == M2S_OP_HPCG27 ? 27 : 7;
+    g->units32.assign(n_problems, std::vector<WaveUnits>(L));
     for (int i = 0; i < n_problems; ++i)
-        for (int l = 0; l < L; ++l)
-            if ((e = build_wave_units(stencil, kWaveK, g->dims[i][l], &g->units[i][l])) != cudaSuccess)
+        for (int l = 0; l < L; ++l) {
+            if (op == M2S_OP_HPCG27) {
+                if ((e = build_cta_units<double>(g->dims[i][l], &g->units[i][l])) != cudaSuccess)
+                    return fail(e);
+                if ((e = build_cta_units<float>(g->dims[i][l], &g->units32[i][l])) != cudaSuccess)
+                    return fail(e);
+            } else if ((e = build_wave_units(7, kWaveK, g->dims[i][l], &g->units[i][l])) !=
+                       cudaSuccess) {
                 return fail(e);
+            }
+        }
     // PCG vectors
     const i64 n0 = g->ltot[0];
     for (double** p : {&g->r, &g->z, &g->zold, &g->p0, &g->p1, &g->q})
@@ -471,7 +488,7 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     for (int i = 0; i < n_problems; ++i) {
         np = std::max(np, dot_num_partials(g->dims[i][0].n));
         np = std::max(np, st27_num_partials(g->dims[i][0]));
-        np = std::max(np, g->units[i][0].n_units);
+        np = std::max(np, g->units[i][0].n_units * rz_per_unit(g));
     }
     g->npart = np;
     if ((e = galloc(g, &g->part, np)) != cudaSuccess) return fail(e);

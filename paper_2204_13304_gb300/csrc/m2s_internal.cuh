@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/m2s.h"
+#include "m2s.h"
 
 namespace m2s {
 
@@ -146,6 +146,13 @@ void build_units_host(int lanes, int skew, int corner, int K, Dims d, std::vecto
 int wave_grid(int n_units, int per_sm);
 int wave_blocks_per_sm(int stencil);
 constexpr int kWaveSlots = 5;  // register slots per lane of the sweep kernels
+// CTA-pipelined 27-point sweep (k_wave2.cu)
+template <typename T>
+cudaError_t build_cta_units(Dims d, WaveUnits* out);
+template <typename T>
+cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, Dims d, const T* Qin, T* Qout,
+                            const T* b, T* x, cudaStream_t st);
+int cta_units_per_rz(int dtype_is_f64);
 void free_wave_units(WaveUnits* u);
 
 // Vector kernels (k_vec.cu).
