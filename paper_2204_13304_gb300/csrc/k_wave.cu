@@ -382,6 +382,7 @@ void free_wave_units(WaveUnits* u) {
     if (u->d_prod) cudaFree(u->d_prod);
     if (u->d_flags) cudaFree(u->d_flags);
     if (u->d_ctrl) cudaFree(u->d_ctrl);
+    if (u->d_mbox) cudaFree(u->d_mbox);
     *u = WaveUnits{};
 }
 

@@ -58,365 +58,332 @@ struct CtaArgs {
     DevStatus* status;
     double* rz;          // per-unit partials of b.x (W per unit) or NULL
     int stall_unit;
+    unsigned long long* mbox;  // tagged copies of the rows other units read
 };
 
-__device__ __forceinline__ int ld_acquire_cta_smem(const int* p) {
-    int v;
-    asm volatile("ld.acquire.cta.shared::cta.s32 %0, [%1];" : "=r"(v)
-                 : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+// ---------------------------------------------------------------------------
+// Tagged words.  A value and a 32-bit tag travel in 64-bit words, each
+// written with one relaxed 64-bit store (single-copy atomic): a reader that
+// sees the expected tag sees the value, with no fence on either side.
+// FP32: one word (tag | bits); FP64: two words (tag | low half, tag | high).
+// ---------------------------------------------------------------------------
+typedef unsigned long long u64;
+
+template <typename T> struct Tagged;
+template <> struct Tagged<float> {
+    struct W { u64 w; };
+    static __device__ __forceinline__ W pack(float v, unsigned tag) {
+        return W{((u64)tag << 32) | (u64)__float_as_uint(v)};
+    }
+    static __device__ __forceinline__ bool unpack(W w, unsigned tag, float* v) {
+        *v = __uint_as_float((unsigned)w.w);
+        return (unsigned)(w.w >> 32) == tag;
+    }
+    static __device__ __forceinline__ W zero() { return W{0ull}; }
+};
+template <> struct Tagged<double> {
+    struct W { u64 lo, hi; };
+    static __device__ __forceinline__ W pack(double v, unsigned tag) {
+        const u64 b = (u64)__double_as_longlong(v);
+        return W{((u64)tag << 32) | (b & 0xffffffffull), ((u64)tag << 32) | (b >> 32)};
+    }
+    static __device__ __forceinline__ bool unpack(W w, unsigned tag, double* v) {
+        const u64 b = (w.lo & 0xffffffffull) | ((w.hi & 0xffffffffull) << 32);
+        *v = __longlong_as_double((long long)b);
+        return (unsigned)(w.lo >> 32) == tag && (unsigned)(w.hi >> 32) == tag;
+    }
+    static __device__ __forceinline__ W zero() { return W{0ull, 0ull}; }
+};
+
+__device__ __forceinline__ void st_relaxed_u64(u64* p, u64 v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ u64 ld_relaxed_u64(const u64* p) {
+    u64 v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_cta_smem(int* p, int v) {
-    asm volatile("st.release.cta.shared::cta.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)),
-                 "r"(v) : "memory");
-}
-__device__ __forceinline__ void st_relaxed_gpu(int* p, int v) {
-    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Producers of one compute warp: up to three global words and one word of
-// a sibling warp in shared memory.
-struct Prods {
-    const int* g[3];
-    int ng;
-    const int* s;  // shared-memory word or NULL
-};
-
-// Bounded wait until every producer word is >= need.  Returns the minimum
-// seen (>= need) in *cached, or false if the sweep was aborted.
-__device__ __forceinline__ bool wait_all(const Prods& pr, int need, int* cached,
-                                         DevStatus* status, long long spin_ns) {
-    const int lane = threadIdx.x & 31;
-    int ok = 1, cache = 0;
-    if (lane == 0) {
-        unsigned long long t0 = 0;
-        for (;;) {
-            int m = INT_MAX;
-            for (int i = 0; i < pr.ng; ++i) m = min(m, ld_acquire_gpu(pr.g[i]));
-            if (pr.s) m = min(m, ld_acquire_cta_smem(pr.s));
-            if (m >= need) { cache = m; break; }
-            if (ld_relaxed_gpu(&status->abort)) { ok = 0; break; }
-            const unsigned long long now = global_ns();
-            if (t0 == 0) t0 = now;
-            else if ((long long)(now - t0) > spin_ns) {
-                atomicCAS(&status->err, 0, (int)M2S_ERR_TIMEOUT);
-                atomicExch(&status->abort, 1);
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
+template <typename T>
+__device__ __forceinline__ void mb_store(u64* mb, i64 p, T v, unsigned tag) {
+    const typename Tagged<T>::W w = Tagged<T>::pack(v, tag);
+    if constexpr (sizeof(T) == 4) {
+        st_relaxed_u64(mb + p, w.w);
+    } else {
+        st_relaxed_u64(mb + 2 * p, w.lo);
+        st_relaxed_u64(mb + 2 * p + 1, w.hi);
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    *cached = __shfl_sync(0xffffffffu, cache, 0);
-    __syncwarp();
-    return ok != 0;
+}
+template <typename T>
+__device__ __forceinline__ typename Tagged<T>::W mb_load(const u64* mb, i64 p) {
+    typename Tagged<T>::W w;
+    if constexpr (sizeof(T) == 4) {
+        w.w = ld_relaxed_u64(mb + p);
+    } else {
+        w.lo = ld_relaxed_u64(mb + 2 * p);
+        w.hi = ld_relaxed_u64(mb + 2 * p + 1);
+    }
+    return w;
 }
 
-// Shared-memory staging of one compute warp (pitch 33 keeps the lane index
-// conflict-free).  A = Q (computing rows) or x (halo rows), B = b.
-template <typename T, int K, int CH>
-struct WarpStage {
-    T inA[2][K][CH][33];
-    T inB[2][K - 1][CH][33];
-    T outX[K - 1][CH][33];
-    T outQ[K - 1][CH][33];
+// A replayed row keeps its mailbox word in the ring registers of Q and b
+// (a row is either computed or replayed, never both).
+__device__ __forceinline__ void tw_to_regs(Tagged<float>::W w, float* q, float* b) {
+    *q = __uint_as_float((unsigned)w.w);
+    *b = __uint_as_float((unsigned)(w.w >> 32));
+}
+__device__ __forceinline__ Tagged<float>::W regs_to_tw(float q, float b) {
+    return Tagged<float>::W{((u64)__float_as_uint(b) << 32) | (u64)__float_as_uint(q)};
+}
+__device__ __forceinline__ void tw_to_regs(Tagged<double>::W w, double* q, double* b) {
+    *q = __longlong_as_double((long long)w.lo);
+    *b = __longlong_as_double((long long)w.hi);
+}
+__device__ __forceinline__ Tagged<double>::W regs_to_tw(double q, double b) {
+    return Tagged<double>::W{(u64)__double_as_longlong(q), (u64)__double_as_longlong(b)};
+}
+
+constexpr int RING = 32;  // steps held by a plane-sum ring
+
+// Shared memory of one CTA: per warp, a ring of tagged plane sums G read by
+// the warp above, and the warp's progress (read by the warp below for
+// back-pressure only).
+template <typename T, int W>
+struct CtaShared {
+    typename Tagged<T>::W ring[W][RING][32];
+    volatile int prog[W];
 };
 
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, int bytes) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if (bytes == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
-}
-
-template <typename T, int K, int W, int CH>
-__device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w, int* sflag,
-                                             WarpStage<T, K, CH>& sm) {
-    constexpr int S_COMP = K - 1;
+// One compute warp of a CTA unit: lane = row u (lanes 0-1 replay the rows
+// of the unit to the left), plane v1 = org.y + w is computed, plane
+// v0 = v1 - 1 below it is replayed (warp 0 reads it from the producers'
+// mailbox and forms its sums; warps above take the finished plane sums G of
+// the warp below from its shared-memory ring).  Rows that other units read
+// (lanes 30-31, and the top warp's plane) are also written to the mailbox
+// with the launch tag.  The step is written for the fewest instructions:
+// incremental indices, one warp vote per step for all tag checks.
+template <typename T, int W, int D>
+__device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
+                                             CtaShared<T, W>& sh, unsigned tag) {
+    typedef typename Tagged<T>::W TW;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int2 org = a.origin[t];
-    const int4 pu = a.prod[t];
-    const int vbase = org.y + w * S_COMP - 1;  // plane of slot 0
-    const int u0m2 = org.x - 2;                // u of lane 0
-    const int tbase = 2 * u0m2 + 2 * vbase;
+    const int v1 = org.y + w, v0 = v1 - 1;
+    const int u = org.x - 2 + lane;
+    const int tbase = 2 * (org.x - 2) + 2 * v0;
     const T inv26 = Lit<T>::inv26();
-    const i64 dir = a.rev ? -1 : 1;
+    const bool halo = lane < 2;
+    const bool ring_in = w > 0;
+    const bool ring_out = w < W - 1;
+    const bool mb_out = !halo && (lane >= 30 || w == W - 1);
+    const int nx = a.nx;
+    const int y1 = u - v1, y0 = u - v0;
+    const bool rv1 = v1 < a.nz && y1 >= 0 && y1 < a.ny;
+    const bool rv0 = !ring_in && v0 >= 0 && v0 < a.nz && y0 >= 0 && y0 < a.ny;
+    const i64 step_dir = a.rev ? -1 : 1;
+    // problem-local index of x = 0 of both rows (meaningful only if valid)
+    const i64 r1 = ((i64)v1 * a.ny + y1) * nx, r0 = ((i64)v0 * a.ny + y0) * nx;
+    const i64 L1 = a.rev ? a.n - 1 - r1 : r1;
+    const i64 L0 = a.rev ? a.n - 1 - r0 : r0;
+    const T* Qin = a.Qin + a.off;
+    const T* B = a.b + a.off;
+    T* Xo = a.x + a.off;
+    T* Qo = a.Qout ? a.Qout + a.off : nullptr;
+    const bool want_rz = a.rz != nullptr;
 
-    Prods pr;
-    pr.ng = 0;
-    pr.s = nullptr;
-    if (pu.x >= 0) pr.g[pr.ng++] = a.flags + pu.x * W + w;  // halo lanes
-    if (w > 0) {
-        pr.s = sflag + (w - 1);                                 // halo plane
-        if (pu.x >= 0) pr.g[pr.ng++] = a.flags + pu.x * W + (w - 1);
-    } else {
-        if (pu.y >= 0) pr.g[pr.ng++] = a.flags + pu.y * W + (W - 1);
-        if (pu.z >= 0) pr.g[pr.ng++] = a.flags + pu.z * W + (W - 1);
-    }
-    const bool has_prod = pr.ng > 0 || pr.s != nullptr;
+    // row state: slot 1 (computed or replayed) and slot 0 (warp 0 only)
+    T xm1 = 0, xm2 = 0, h1 = 0, h2 = 0, s21 = 0, s22 = 0;
+    T zm1 = 0, zm2 = 0, k1 = 0, k2 = 0, t21 = 0, t22 = 0, g0 = 0;
+    // prefetch ring: slot 1 (Q, b or mailbox bits), slot 0 (mailbox bits)
+    T rq[D], rb[D], ra0[D], rb0[D];
 
-    // row (r, j) of this warp: u = u0m2 + r, v = vbase + j; returns the
-    // address of x = 0 (forward or reflected) or -1 if the row is outside.
-    auto row_base = [&](int r, int j) -> i64 {
-        const int v = vbase + j, y = u0m2 + r - v;
-        if (v < 0 || v >= a.nz || y < 0 || y >= a.ny) return -1;
-        const i64 rb = ((i64)v * a.ny + y) * a.nx;
-        return a.rev ? a.off + a.n - 1 - rb : a.off + rb;
-    };
-    // own rows
-    i64 base[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) base[j] = row_base(lane, j);
-    const bool halo_lane = lane < 2;
-
-    T xm1[K], xm2[K], h1[K], h2[K], s21[K], s22[K], g1[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) xm1[j] = xm2[j] = h1[j] = h2[j] = s21[j] = s22[j] = g1[j] = T(0);
-
-    const int S = a.nx + 2 * 31 + 2 * (K - 1) + 1;  // steps until every row is done
-    const int nchunks = (S + CH - 1) / CH;
-    int cached = 0;
-    // halo values of the next chunk travel through registers (.cg loads):
-    // slot 0: 32 rows x CH (lane r = q % 32 ... one row per lane, CH values);
-    // slots >= 1: rows 0-1 x CH values -> lanes 0..2*CH-1, one value each.
-    T hv0[CH];
-    T hv1[K];
-
-    // Issue the loads of chunk c into buffer c & 1.  Returns false on abort.
-    auto issue = [&](int c) -> bool {
-        const int c0 = c * CH;
-        if (c0 >= S) {
-#pragma unroll
-            for (int e = 0; e < CH; ++e) hv0[e] = T(0);
-#pragma unroll
-            for (int j = 0; j < K; ++j) hv1[j] = T(0);
-            return true;
-        }
-        const int tneed = c0 + CH - 1 + tbase + BIAS;
-        if (has_prod && tneed > cached) {
-            if (!wait_all(pr, tneed, &cached, a.status, a.spin_ns)) return false;
-        }
-        const int bsel = c & 1;
-        // computing rows: Q and b by cp.async (read-only in this launch)
-#pragma unroll
-        for (int j = 1; j < K; ++j) {
-#pragma unroll
-            for (int m = 0; m < CH; ++m) {
-                const int q = lane + 32 * m;
-                const int r = q / CH, e = q - (q / CH) * CH;
-                const int xx = c0 + e - 2 * r - 2 * j;
-                const i64 rbse = row_base(r, j);
-                T* dA = &sm.inA[bsel][j][e][r];
-                T* dB = &sm.inB[bsel][j - 1][e][r];
-                if (r >= 2) {
-                    if (rbse >= 0 && xx >= 0 && xx < a.nx) {
-                        const i64 p = rbse + dir * xx;
-                        cp_async4(dA, a.Qin + p, sizeof(T));
-                        cp_async4(dB, a.b + p, sizeof(T));
-                    } else {
-                        *dA = T(0);
-                        *dB = T(0);
-                    }
-                }
+    const int S = nx + 2 * 31 + 3;
+    // fetch the inputs of step s (x1 = s - 2 lane - 2, x0 = x1 + 2) into slot k
+    auto fetch = [&](int k, int x1) {
+        T q = 0, bv = 0, m0 = 0, m1 = 0;
+        if (rv1 && (unsigned)x1 < (unsigned)nx) {
+            const i64 p = L1 + step_dir * x1;
+            if (!halo) {
+                q = __ldg(Qin + p);
+                bv = __ldg(B + p);
+            } else {
+                tw_to_regs(mb_load<T>(a.mbox, p), &q, &bv);
             }
         }
-        // halo rows of slot 0: lane r loads its row's CH values
-        {
-            const i64 rbse = row_base(lane, 0);
-#pragma unroll
-            for (int e = 0; e < CH; ++e) {
-                const int xx = c0 + e - 2 * lane;
-                hv0[e] = (rbse >= 0 && xx >= 0 && xx < a.nx) ? __ldcg(a.x + rbse + dir * xx) : T(0);
-            }
-        }
-        // halo rows 0-1 of slots >= 1: lane q < 2*CH loads (row q/CH, e = q%CH)
-#pragma unroll
-        for (int j = 1; j < K; ++j) {
-            T v = T(0);
-            if (lane < 2 * CH) {
-                const int r = lane / CH, e = lane - (lane / CH) * CH;
-                const int xx = c0 + e - 2 * r - 2 * j;
-                const i64 rbse = row_base(r, j);
-                if (rbse >= 0 && xx >= 0 && xx < a.nx) v = __ldcg(a.x + rbse + dir * xx);
-            }
-            hv1[j] = v;
-        }
-        return true;
+        const int x0 = x1 + 2;
+        if (rv0 && (unsigned)x0 < (unsigned)nx)
+            tw_to_regs(mb_load<T>(a.mbox, L0 + step_dir * x0), &m0, &m1);
+        rq[k] = q;
+        rb[k] = bv;
+        ra0[k] = m0;
+        rb0[k] = m1;
     };
-    // complete the loads of chunk c: land the halo registers, wait for the
-    // asynchronous copies, make everything visible to the whole warp
-    auto land = [&](int c) {
-        const int bsel = c & 1;
 #pragma unroll
-        for (int e = 0; e < CH; ++e) sm.inA[bsel][0][e][lane] = hv0[e];
-#pragma unroll
-        for (int j = 1; j < K; ++j)
-            if (lane < 2 * CH) sm.inA[bsel][j][lane - (lane / CH) * CH][lane / CH] = hv1[j];
-        cp_async_commit_wait_all();
-        __syncwarp();
-    };
-    // write chunk c's outputs (coalesced along each row) and publish it
-    auto flush = [&](int c) {
-        const int c0 = c * CH;
-        __syncwarp();
-#pragma unroll
-        for (int j = 1; j < K; ++j) {
-#pragma unroll
-            for (int m = 0; m < CH; ++m) {
-                const int q = lane + 32 * m;
-                const int r = q / CH, e = q - (q / CH) * CH;
-                if (r < 2) continue;
-                const int xx = c0 + e - 2 * r - 2 * j;
-                const i64 rbse = row_base(r, j);
-                if (rbse >= 0 && xx >= 0 && xx < a.nx) {
-                    const i64 p = rbse + dir * xx;
-                    a.x[p] = sm.outX[j - 1][e][r];
-                    if (a.Qout) a.Qout[p] = sm.outQ[j - 1][e][r];
-                }
-            }
-        }
-        __syncwarp();
-        if (lane == 0) st_release_cta_smem(sflag + w, c0 + CH - 1 + tbase + BIAS);
-    };
+    for (int k = 0; k < D; ++k) fetch(k, k - 2 * lane - 2);
 
-    bool ok = issue(0);
-    if (ok) land(0);
     double rz = 0.0;
-    for (int c = 0; ok && c < nchunks; ++c) {
-        ok = issue(c + 1);
-        if (!ok) break;
-        const int bsel = c & 1;
-#pragma unroll
-        for (int e = 0; e < CH; ++e) {
-            const int s = c * CH + e;
-            T hu1[K], hu2[K], su2[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                hu1[j] = __shfl_up_sync(FULL, h1[j], 1);
-                hu2[j] = __shfl_up_sync(FULL, h2[j], 1);
-                su2[j] = (j < K - 1) ? __shfl_up_sync(FULL, s22[j], 1) : T(0);
-            }
-            T X[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const int xx = s - 2 * lane - 2 * j;
-                const bool in = base[j] >= 0 && xx >= 0 && xx < a.nx;
-                const T va = sm.inA[bsel][j][e][lane];
-                T v = T(0);
-                if (j > 0 && !halo_lane) {
-                    if (in) {
-                        const T vb = sm.inB[bsel][j - 1][e][lane];
-                        const T N = (xm1[j] + hu1[j]) + g1[j - 1];
-                        v = (va + N) * inv26;
-                        sm.outX[j - 1][e][lane] = v;
-                        sm.outQ[j - 1][e][lane] = vb + N;
-                        if (a.rz) rz = fma((double)vb, (double)v, rz);
-                    }
-                } else {
-                    v = va;  // halo row (0 outside the grid)
-                }
-                X[j] = v;
-            }
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const T H = (xm2[j] + xm1[j]) + X[j];
-                xm2[j] = xm1[j];
-                xm1[j] = X[j];
-                h2[j] = h1[j];
-                h1[j] = H;
-                if (j < K - 1) {
-                    const T S2 = hu2[j] + H;
-                    const T G = su2[j] + H;
-                    s22[j] = s21[j];
-                    s21[j] = S2;
-                    g1[j] = G;
-                }
+    bool ok = true;
+    int cachedC = -(1 << 30);
+    auto fail = [&]() -> bool {  // abort check / timeout for the slow paths
+        int ab = 0;
+        if (lane == 0) ab = ld_relaxed_gpu(&a.status->abort);
+        return __shfl_sync(FULL, ab, 0) != 0;
+    };
+    auto timeout = [&]() {
+        if (lane == 0) {
+            atomicCAS(&a.status->err, 0, (int)M2S_ERR_TIMEOUT);
+            atomicExch(&a.status->abort, 1);
+        }
+    };
+    auto step = [&](int s, int k) {
+        const int x1 = s - 2 * lane - 2;
+        const int x0 = x1 + 2;
+        const int tnow = s + tbase;
+        const T q = rq[k], bv = rb[k], m0 = ra0[k], m1 = rb0[k];
+        fetch(k, x1 + D);
+        const bool in1 = rv1 && (unsigned)x1 < (unsigned)nx;
+        const bool in0 = rv0 && (unsigned)x0 < (unsigned)nx;
+        const bool comp = in1 && !halo;
+        // replayed values: mailbox (slot 1 halo lanes, slot 0 of warp 0) and
+        // ring (plane sums of the plane below, warps above 0)
+        T X1 = 0, X0 = 0, gin = 0;
+        bool good = true;
+        if (in1 && halo) good = Tagged<T>::unpack(regs_to_tw(q, bv), tag, &X1);
+        if (in0) good = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &X0) && good;
+        const TW* re = ring_in ? &sh.ring[w - 1][(tnow - 1) & (RING - 1)][lane] : nullptr;
+        const bool need_g = ring_in && __any_sync(FULL, comp);
+        if (need_g) good = Tagged<T>::unpack(*re, (unsigned)(tnow - 1 + BIAS), &gin) && good;
+        if (!__all_sync(FULL, good)) {
+            const unsigned long long t0 = global_ns();
+            for (;;) {
+                good = true;
+                if (in1 && halo)
+                    good = Tagged<T>::unpack(mb_load<T>(a.mbox, L1 + step_dir * x1), tag, &X1);
+                if (in0)
+                    good = Tagged<T>::unpack(mb_load<T>(a.mbox, L0 + step_dir * x0), tag, &X0) && good;
+                if (need_g)
+                    good = Tagged<T>::unpack(*(volatile const TW*)re, (unsigned)(tnow - 1 + BIAS), &gin) &&
+                           good;
+                if (__all_sync(FULL, good)) break;
+                if (fail()) { ok = false; return; }
+                if ((long long)(global_ns() - t0) > a.spin_ns) { timeout(); ok = false; return; }
             }
         }
-        flush(c);
-        land(c + 1);
+        // computed plane
+        const T hu1 = __shfl_up_sync(FULL, h1, 1);
+        const T hu2 = __shfl_up_sync(FULL, h2, 1);
+        const T su2 = ring_out ? __shfl_up_sync(FULL, s22, 1) : T(0);
+        if (comp) {
+            const T N = (xm1 + hu1) + (ring_in ? gin : g0);
+            X1 = (q + N) * inv26;
+            const i64 p = L1 + step_dir * x1;
+            Xo[p] = X1;
+            if (Qo) Qo[p] = bv + N;
+            if (want_rz) rz = fma((double)bv, (double)X1, rz);
+            if (mb_out) mb_store<T>(a.mbox, p, X1, tag);
+        }
+        const T H = (xm2 + xm1) + X1;
+        xm2 = xm1;
+        xm1 = X1;
+        h2 = h1;
+        h1 = H;
+        if (ring_out) {
+            const T S2 = hu2 + H;
+            const T G = su2 + H;
+            s22 = s21;
+            s21 = S2;
+            // back-pressure: the ring entry of step tnow - RING must have been
+            // read by the warp above (first read: entry tbase + 1)
+            const int old_entry = tnow - RING;
+            if (old_entry >= tbase + 1 && old_entry + 1 > cachedC) {
+                int c = 0, okk = 1;
+                if (lane == 0) {
+                    const unsigned long long t0 = global_ns();
+                    for (;;) {
+                        c = sh.prog[w + 1];
+                        if (c >= old_entry + 1) break;
+                        if (ld_relaxed_gpu(&a.status->abort) ||
+                            (long long)(global_ns() - t0) > a.spin_ns) {
+                            atomicCAS(&a.status->err, 0, (int)M2S_ERR_TIMEOUT);
+                            atomicExch(&a.status->abort, 1);
+                            okk = 0;
+                            break;
+                        }
+                    }
+                }
+                okk = __shfl_sync(FULL, okk, 0);
+                cachedC = __shfl_sync(FULL, c, 0);
+                if (!okk) { ok = false; return; }
+            }
+            sh.ring[w][tnow & (RING - 1)][lane] = Tagged<T>::pack(G, (unsigned)(tnow + BIAS));
+        }
+        // replayed plane below (warp 0): its sums feed the computed plane
+        if (!ring_in) {
+            const T ku2 = __shfl_up_sync(FULL, k2, 1);
+            const T tu2 = __shfl_up_sync(FULL, t22, 1);
+            const T H0 = (zm2 + zm1) + X0;
+            zm2 = zm1;
+            zm1 = X0;
+            k2 = k1;
+            k1 = H0;
+            t22 = t21;
+            t21 = ku2 + H0;
+            g0 = tu2 + H0;
+        }
+        __syncwarp();
+        if (lane == 0) sh.prog[w] = tnow;
+    };
+    for (int s0 = 0; ok && s0 < S; s0 += D) {
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+            if (ok) step(s0 + k, k);
     }
     __syncwarp();
-    if (lane == 0) st_release_cta_smem(sflag + w, ok ? DONE : DONE - 1);
-    if (a.rz) {
+    if (lane == 0) sh.prog[w] = INT_MAX;
+    if (want_rz) {
         for (int o = 16; o > 0; o >>= 1) rz += __shfl_down_sync(FULL, rz, o);
         if (lane == 0) a.rz[(i64)t * W + w] = ok ? rz : 0.0;
     }
 }
 
-// Forwards the compute warps' CTA-scope progress to their global words.
-template <int W>
-__device__ __forceinline__ void service_warp(int* flags, int t, const int* sflag, DevStatus* status) {
-    const int lane = threadIdx.x & 31;
-    int last = 0;
-    for (;;) {
-        int v = DONE;
-        if (lane < W) v = ld_acquire_cta_smem(sflag + lane);
-        const int fresh = (lane < W && v != last) ? 1 : 0;
-        if (__any_sync(0xffffffffu, fresh)) {
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");
-            // DONE - 1 marks an aborted warp: nothing to forward
-            if (fresh && v != DONE - 1) st_relaxed_gpu(flags + t * W + lane, v);
-            last = v;
-        }
-        const int done = (lane < W) ? (v >= DONE - 1) : 1;
-        if (__all_sync(0xffffffffu, done)) break;
-        int ab = 0;
-        if (lane == 0) ab = ld_relaxed_gpu(&status->abort);
-        ab = __shfl_sync(0xffffffffu, ab, 0);
-        if (ab) break;
-        __nanosleep(64);
-    }
-}
-
 template <typename T, int K, int W, int D>
-__global__ void __launch_bounds__((W + 1) * 32, 1) gs27_cta_kernel(CtaArgs<T> a) {
-    __shared__ int sflag[W];
+__global__ void __launch_bounds__(W * 32, 1) gs27_cta_kernel(CtaArgs<T> a) {
+    static_assert(K == 2, "one halo plane and one computed plane per warp");
     __shared__ int s_ticket;
+    __shared__ unsigned s_tag;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    WarpStage<T, K, D>* stages = reinterpret_cast<WarpStage<T, K, D>*>(dyn_smem);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    CtaShared<T, W>& sh = *reinterpret_cast<CtaShared<T, W>*>(dyn_smem);
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tag = (unsigned)ld_relaxed_gpu(&a.ctrl[2]) + 1u;
     for (;;) {
         if (threadIdx.x == 0) s_ticket = atomicAdd(&a.ctrl[0], 1);
-        if (threadIdx.x < W) sflag[threadIdx.x] = 0;
+        // ring tags from an earlier unit of this CTA could match a step of
+        // this unit: clear the rings
+        for (int i = threadIdx.x; i < W * RING * 32; i += blockDim.x)
+            (&sh.ring[0][0][0])[i] = Tagged<T>::zero();
+        if (threadIdx.x < W) sh.prog[threadIdx.x] = -(1 << 30);
         __syncthreads();
         const int t = s_ticket;
         if (t >= a.n_units) break;
         int ab = 0;
         if (threadIdx.x == 0) ab = ld_relaxed_gpu(&a.status->abort) || t == a.stall_unit;
         ab = __syncthreads_or(ab);
-        if (!ab) {
-            if (warp < W) compute_warp<T, K, W, D>(a, t, warp, sflag, stages[warp]);
-            else service_warp<W>(a.flags, t, sflag, a.status);
-        }
+        if (!ab) compute_warp<T, W, D>(a, t, warp, sh, s_tag);
         __syncthreads();
     }
-    // exit protocol: the last CTA out resets the counters for the next launch
+    // exit protocol: the last CTA out resets the ticket and advances the tag
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const int last = atomicAdd(&a.ctrl[1], 1) == (int)gridDim.x - 1;
-        s_ticket = last;
-    }
-    __syncthreads();
-    if (s_ticket) {
-        __threadfence();
-        for (int i = threadIdx.x; i < a.n_units * W; i += blockDim.x) a.flags[i] = 0;
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (last) {
             a.ctrl[0] = 0;
             a.ctrl[1] = 0;
+            a.ctrl[2] = a.ctrl[2] + 1;
             a.status->abort = 0;
             __threadfence();
         }
     }
-    (void)lane;
 }
 
 }  // namespace
@@ -426,12 +393,12 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) gs27_cta_kernel(CtaArgs<T> a)
 // chunk length in steps (inputs are staged one chunk ahead, outputs flushed
 // and published once per chunk).
 template <typename T> struct CtaShape;
-template <> struct CtaShape<double> { static constexpr int K = 2, W = 4, D = 4; };
-template <> struct CtaShape<float> { static constexpr int K = 5, W = 4, D = 8; };
+template <> struct CtaShape<double> { static constexpr int K = 2, W = 8, D = 4; };
+template <> struct CtaShape<float> { static constexpr int K = 2, W = 8, D = 8; };
 
 template <typename T>
 size_t cta_smem_bytes() {
-    return sizeof(WarpStage<T, CtaShape<T>::K, CtaShape<T>::D>) * CtaShape<T>::W;
+    return sizeof(CtaShared<T, CtaShape<T>::W>);
 }
 
 template <typename T>
@@ -450,7 +417,16 @@ cudaError_t build_cta_units(Dims d, WaveUnits* out) {
     if ((e = cudaMalloc(&u.d_origin, nu * sizeof(int2))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&u.d_prod, nu * sizeof(int4))) != cudaSuccess) { free_wave_units(&u); return e; }
     if ((e = cudaMalloc(&u.d_flags, nu * W * sizeof(int))) != cudaSuccess) { free_wave_units(&u); return e; }
-    if ((e = cudaMalloc(&u.d_ctrl, 2 * sizeof(int))) != cudaSuccess) { free_wave_units(&u); return e; }
+    if ((e = cudaMalloc(&u.d_ctrl, 4 * sizeof(int))) != cudaSuccess) { free_wave_units(&u); return e; }
+    // mailbox: one tagged word (FP32) or two (FP64) per point of the level
+    if ((e = cudaMalloc(&u.d_mbox, (size_t)std::max<i64>(d.n, 1) * sizeof(T) * 2)) != cudaSuccess) {
+        free_wave_units(&u);
+        return e;
+    }
+    if ((e = cudaMemset(u.d_mbox, 0, (size_t)std::max<i64>(d.n, 1) * sizeof(T) * 2)) != cudaSuccess) {
+        free_wave_units(&u);
+        return e;
+    }
     if (!org.empty() &&
         ((e = cudaMemcpy(u.d_origin, org.data(), org.size() * sizeof(int2), cudaMemcpyHostToDevice)) !=
              cudaSuccess ||
@@ -460,7 +436,7 @@ cudaError_t build_cta_units(Dims d, WaveUnits* out) {
         return e;
     }
     if ((e = cudaMemset(u.d_flags, 0, nu * W * sizeof(int))) != cudaSuccess ||
-        (e = cudaMemset(u.d_ctrl, 0, 2 * sizeof(int))) != cudaSuccess) {
+        (e = cudaMemset(u.d_ctrl, 0, 4 * sizeof(int))) != cudaSuccess) {
         free_wave_units(&u);
         return e;
     }
@@ -468,8 +444,7 @@ cudaError_t build_cta_units(Dims d, WaveUnits* out) {
     const size_t smem = cta_smem_bytes<T>();
     cudaFuncSetAttribute(gs27_cta_kernel<T, K, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs27_cta_kernel<T, K, W, D>, (W + 1) * 32,
-                                                  smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs27_cta_kernel<T, K, W, D>, W * 32, smem);
     u.grid = wave_grid(u.n_units, per_sm);
     *out = u;
     return cudaGetLastError();
@@ -502,7 +477,8 @@ cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, Dims d, const
     a.status = c.status;
     a.rz = c.rz_partials;
     a.stall_unit = c.stall_unit;
-    gs27_cta_kernel<T, K, W, D><<<u.grid, (W + 1) * 32, cta_smem_bytes<T>(), st>>>(a);
+    a.mbox = u.d_mbox;
+    gs27_cta_kernel<T, K, W, D><<<u.grid, W * 32, cta_smem_bytes<T>(), st>>>(a);
     return cudaGetLastError();
 }
 

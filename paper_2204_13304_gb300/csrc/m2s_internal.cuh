@@ -83,7 +83,8 @@ struct WaveUnits {
     int2* d_origin;   // (u0, v0) of each unit
     int4* d_prod;     // producer unit indices (left, below, below-left, -1)
     int* d_flags;     // progress word per unit (0 at rest)
-    int* d_ctrl;      // [0] ticket, [1] exited CTAs
+    int* d_ctrl;      // [0] ticket, [1] exited CTAs, [2] launch tag (CTA kernel)
+    unsigned long long* d_mbox = nullptr;  // CTA kernel: tagged boundary rows
     int grid;         // CTAs launched
     int K;            // slots per lane (incl. the halo slot)
     int stencil;      // 27 or 7
