@@ -189,7 +189,9 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
     const T* B = a.b + a.off;
     T* Xo = a.x + a.off;
     T* Qo = a.Qout ? a.Qout + a.off : nullptr;
-    const bool want_rz = a.rz != nullptr;
+    // the fused r.z partial is used by the FP64 PCG only; compiling it out of
+    // the FP32 sweep keeps float->double conversions off the FP64 pipe
+    const bool want_rz = sizeof(T) == 8 && a.rz != nullptr;
 
     // row state: slot 1 (computed or replayed) and slot 0 (warp 0 only)
     T xm1 = 0, xm2 = 0, h1 = 0, h2 = 0, s21 = 0, s22 = 0;
@@ -279,7 +281,9 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
             const i64 p = L1 + step_dir * x1;
             Xo[p] = X1;
             if (Qo) Qo[p] = bv + N;
-            if (want_rz) rz = fma((double)bv, (double)X1, rz);
+            if constexpr (sizeof(T) == 8) {
+                if (want_rz) rz = fma((double)bv, (double)X1, rz);
+            }
             if (mb_out) mb_store<T>(a.mbox, p, X1, tag);
         }
         const T H = (xm2 + xm1) + X1;
