@@ -144,6 +144,79 @@ def cpu_baseline(n, budget_s=20.0):
     return per_iter, reps, time.perf_counter() - t0
 
 
+def oracle_iterations(n):
+    """Iterations the oracle's FP64 MG-PCG needs to reach 1e-10 on the n^3
+    problem, from the history tests/golden/make_hpcg_pcg_history.py wrote."""
+    path = os.path.join(ROOT, "tests", "golden", "hpcg_pcg_history_%d.txt" % n)
+    try:
+        with open(path) as f:
+            vals = [ln for ln in f if ln.strip() and not ln.startswith("#")]
+        return len(vals) - 1, "oracle iteration count from tests/golden/" + os.path.basename(path)
+    except OSError:
+        return None, "no stored oracle history for this size"
+
+
+def sweep_traffic(kernel_tag):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel's sources changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "%s.md" % kernel_tag)
+    try:
+        with open(path) as f:
+            txt = f.read()
+    except OSError:
+        return None, "no ncu summary"
+    kv = {}
+    for ln in txt.splitlines():
+        if ln.startswith("- ") and ":" in ln:
+            k, v = ln[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    h = hashlib.sha256()
+    for rel in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if kv.get("source_sha256") != h.hexdigest():
+        return None, "kernel changed since the ncu capture"
+    try:
+        return float(kv["dram_bytes_per_launch"]), "ncu capture " + os.path.basename(path)
+    except (KeyError, ValueError):
+        return None, "no DRAM figure in the ncu summary"
+
+
+# sources of the dominant kernel (its DRAM traffic is invalid once they change)
+SWEEP_SOURCES = ("paper_2204_13304_gb300/csrc/k_wave2.cu",
+                 "paper_2204_13304_gb300/csrc/m2s_wave_sync.cuh",
+                 "paper_2204_13304_gb300/csrc/m2s_internal.cuh")
+
+
+def profile_case(args):
+    """--profile-case: a few launches of one kernel on an n^3 grid, for an ncu
+    capture (nothing is printed but a marker)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2204_13304_gb300 as m
+    n = args.n
+    shape = (n, n, n)
+    f32 = args.profile_case.endswith("32")
+    dt = torch.float32 if f32 else torch.float64
+    g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.HPCG27, mg_levels=1,
+                     precond_dtype=m.DType.F32 if f32 else m.DType.F64)])
+    ones = torch.ones(shape, dtype=dt, device="cuda")
+    b = torch.empty_like(ones)
+    m.m2s_spmv(g.handle, 0, ones, b)
+    x = torch.zeros_like(ones)
+    for _ in range(3):
+        if args.profile_case.startswith("sweep"):
+            m.m2s_symgs(g.handle, 0, b, x, 1)
+        else:
+            m.m2s_spmv(g.handle, 0, b, x)
+    torch.cuda.synchronize()
+    g.close()
+    print("profile case %s n=%d done" % (args.profile_case, n))
+    return 0
+
+
 def run_reference(args):
     """--impl reference: the serial CPU oracle on the same problem, bounded."""
     ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
@@ -151,7 +224,15 @@ def run_reference(args):
         return 0
     import oracle
     oracle.lib()
-    iters_per_solve = 40  # typical FP64 MG-PCG iteration count to 1e-10 at 256^3
+    iters_per_solve, src = oracle_iterations(args.n)
+    if iters_per_solve is None:
+        # small grids: the oracle solves the whole problem to count
+        import numpy as np
+        shape = (args.n,) * 3
+        _, iters_per_solve, _, _ = oracle.pcg(oracle.HPCG27, oracle.apply(oracle.HPCG27,
+                                                                          np.ones(shape)),
+                                              4, max_iters=500, rtol=1e-10, fixed_iters=False)
+        src = "oracle iteration count of a full oracle solve"
     per_iter, reps, _ = cpu_baseline(args.n, budget_s=min(60.0, 10.0 * max(1, args.steps)))
     value = per_iter * iters_per_solve
     line = {
@@ -161,8 +242,8 @@ def run_reference(args):
         "data": "synthetic", "config": workload_config(args.n),
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "s",
                          "sample": "%d timed V-cycle+SpMV iterations of the %d^3 problem on 1 "
-                                   "host core, x %d iterations per solve" % (reps, args.n,
-                                                                          iters_per_solve)},
+                                   "host core, x %d iterations per solve (%s)"
+                                   % (reps, args.n, iters_per_solve, src)},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -186,9 +267,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-case", choices=["sweep64", "sweep32", "spmv64", "spmv32"],
+                    help="run a few launches of one kernel for an ncu capture and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return profile_case(args)
 
     import numpy as np
     import torch
@@ -224,6 +309,9 @@ def main():
     barrier(ws)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the sweep kernels of the timed solves are bracketed by CUDA events on
+    # the stream they are launched on (the dominant kernel's live timing)
+    m.m2s_sweep_timing(g64.handle, True)
     e0.record(stream)
     for _ in range(args.steps):
         st, res64 = solve(g64)
@@ -231,6 +319,8 @@ def main():
     torch.cuda.synchronize()
     barrier(ws)
     t64 = e0.elapsed_time(e1) / 1e3 / args.steps
+    sweep_lv = [m.m2s_sweep_timing_read(g64.handle, lv) for lv in range(4)]
+    m.m2s_sweep_timing(g64.handle, False)
     clk = clocks.stop()
     x64 = x.clone()
 
@@ -281,16 +371,25 @@ def main():
         "spmv27_f32": {"ms": t_spmv32 * 1e3, "alg_GBs": 8 * rows / t_spmv32 / 1e9},
         "symgs_sweep_f32": {"ms": t_sweep32 * 1e3, "alg_GBs": 12 * rows / t_sweep32 / 1e9},
     }
-    # dominant kernel of the FP64 solve: the Gauss-Seidel sweep, bound by the
-    # FP64 issue rate; 27 FP64 operations per row by definition (26 neighbour
-    # terms + the division), against 629 G FP64 ops/s.
-    ach = 27 * rows / t_sweep64 / 1e9
-    roof = {"kernel": "symgs_sweep_f64 (gs27_wave_kernel<double>)", "bound": "alu",
-            "achieved": ach, "peak": FP64_OPS_PEAK / 1e9, "unit": "G FP64 op/s",
-            "frac": ach / (FP64_OPS_PEAK / 1e9), "traffic": None,
-            "hbm_frac": 24 * rows / t_sweep64 / 1e9 / hbm,
-            "peak_note": "FP64 issue rate 152 SMs x 2 lanes/clk x 2.07 GHz; HBM %s %.0f GB/s"
-                         % (peak_kind, hbm)}
+    # dominant kernel of the FP64 solve: the Gauss-Seidel sweep on the finest
+    # level, bound by the FP64 issue rate; 27 FP64 operations per row by
+    # definition (26 neighbour terms + the division), against 629 G FP64
+    # op/s.  Its launch duration is the live event timing of the timed solves.
+    n_l0, ms_l0, _ = sweep_lv[0]
+    t_launch = ms_l0 / 1e3 / max(1, n_l0)
+    ach = 27 * rows / t_launch / 1e9
+    traffic, traffic_src = sweep_traffic("gs27_cta_kernel_f64_%d" % n)
+    roof = {"kernel": "gs27_cta_kernel<double,2,8,4> (Gauss-Seidel sweep, %d^3 level)" % n,
+            "bound": "alu", "achieved": ach, "peak": FP64_OPS_PEAK / 1e9,
+            "unit": "G FP64 op/s", "frac": ach / (FP64_OPS_PEAK / 1e9), "traffic": traffic,
+            "traffic_source": traffic_src,
+            "launches_timed": n_l0, "ms_per_launch": t_launch * 1e3,
+            "alg_bytes_per_launch": 24 * rows,
+            "hbm_GBs": 24 * rows / t_launch / 1e9,
+            "hbm_frac": 24 * rows / t_launch / 1e9 / hbm,
+            "peak_note": "FP64 issue rate 152 SMs x 2 lanes/clk x 2.07 GHz (derived); HBM %s "
+                         "%.0f GB/s" % (peak_kind, hbm)}
+    sweep_share = sum(v[1] for v in sweep_lv) / 1e3 / args.steps / t64
 
     # end to end through the public API with host buffers
     e2e = None
@@ -326,15 +425,20 @@ def main():
         "fp32_precond": {"value": t32, "unit": "s", "iters": res32.iters,
                          "rel_resid": res32.rel_resid, "rel_err_vs_fp64_solution": err32,
                          "speedup_vs_fp64": t64 / t32},
-        "kernels": kern, "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps,
+        "kernels": kern, "sweep_share_of_solve": sweep_share,
+        "sweep_ms_per_launch_by_level": [v[1] / max(1, v[0]) for v in sweep_lv],
+        "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
         per_iter, reps, _ = cpu_baseline(n)
-        line["cpu_baseline"] = {"value": per_iter * res64.iters, "unit": "s", "cores": 1,
+        oit, src = oracle_iterations(n)
+        if oit is None:
+            oit, src = res64.iters, "iteration count of the GPU solve"
+        line["cpu_baseline"] = {"value": per_iter * oit, "unit": "s", "cores": 1,
                                 "kind": "oracle",
                                 "sample": "%d V-cycle+SpMV iterations of the %d^3 problem on one "
-                                          "host core, x %d iterations" % (reps, n, res64.iters)}
+                                          "host core, x %d iterations (%s)" % (reps, n, oit, src)}
     if rank == 0:
         print(json.dumps(line))
     g64.close()

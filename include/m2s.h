@@ -230,6 +230,34 @@ m2s_status m2s_symgs_noalloc(int nx, int ny, int nz, m2s_dtype dtype,
                              const void* b, void* x, int n_sym_sweeps,
                              void* stream);
 
+/* Shape of the 27-point sweep units (performance tuning; the paper's
+ * task partitioning is fixed at compile time and has no counterpart): each
+ * unit of the wavefront is one thread block of `warps` warps (4 or 8), one
+ * grid plane per warp.  level = -1 sets every level.  The result of a sweep
+ * does not depend on the shape; the b.x partials of the V-cycle's last
+ * sweep are summed in a different order, so PCG iterates may differ in the
+ * last bits.  Synchronises the device and reallocates the schedules: do not
+ * call it while work of this grid is in flight or during stream capture.
+ * Errors: M2S_ERR_INVALID_ARG (not a 27-point grid, level or warps out of
+ * range), M2S_ERR_CUDA / M2S_ERR_OOM from the reallocation. */
+m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps);
+
+/* Per-launch timing of the Gauss-Seidel sweeps (instrumentation; the
+ * paper has no counterpart).  enable = 1 clears the counters and, from the
+ * next sweep on, brackets every sweep kernel the grid launches (any entry
+ * point, any level, either dtype) with a pair of CUDA events recorded on the
+ * stream the sweep is launched on; enable = 0 stops recording.  At most
+ * 16384 launches per level are recorded, later ones are counted as dropped.
+ * Events are created by the library (no device memory is allocated).
+ * m2s_sweep_timing_read waits for the recorded events and returns, for
+ * `level`, the number of recorded launches, their summed device time in
+ * milliseconds and the number of dropped launches (any output may be NULL).
+ * Errors: M2S_ERR_INVALID_ARG for a NULL grid or a level out of range,
+ * M2S_ERR_CUDA if an event cannot be created or read. */
+m2s_status m2s_sweep_timing(m2s_grid* grid, int enable);
+m2s_status m2s_sweep_timing_read(m2s_grid* grid, int level, int* launches,
+                                 double* total_ms, int* dropped);
+
 /* Fault-injection hook for tests (host side; nothing faults on the GPU):
  * in the next Gauss-Seidel sweep on `level`, wavefront unit `unit` (in ticket
  * order) neither computes nor publishes its progress.  The units that wait

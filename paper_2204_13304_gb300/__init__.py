@@ -72,6 +72,7 @@ EXPORTS = (
     "m2s_symgs", "m2s_gs_sweep", "m2s_mg_restrict", "m2s_mg_prolong", "m2s_mg_vcycle",
     "m2s_pcg_solve", "m2s_ssor_sweep", "m2s_adjoint_solve", "m2s_kappa_grad",
     "m2s_set_spin_limit", "m2s_debug_stall_unit", "m2s_symgs_noalloc", "m2s_status_string",
+    "m2s_sweep_timing", "m2s_sweep_timing_read", "m2s_set_sweep_warps",
 )
 
 
@@ -110,6 +111,10 @@ def load():
         "m2s_debug_stall_unit": ([vp, i, i], i),
         "m2s_symgs_noalloc": ([i, i, i, i, vp, vp, i, vp], i),
         "m2s_status_string": ([i], ctypes.c_char_p),
+        "m2s_sweep_timing": ([vp, i], i),
+        "m2s_set_sweep_warps": ([vp, i, i], i),
+        "m2s_sweep_timing_read": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(d),
+                                   ctypes.POINTER(i)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -204,6 +209,25 @@ def m2s_set_spin_limit(grid, limit_ns):
 
 def m2s_debug_stall_unit(grid, level, unit):
     return _check(load().m2s_debug_stall_unit(grid, int(level), int(unit)), "m2s_debug_stall_unit")
+
+
+def m2s_set_sweep_warps(grid, level, warps):
+    """Warps (4 or 8) per 27-point sweep unit on `level` (-1: all levels)."""
+    return _check(load().m2s_set_sweep_warps(grid, int(level), int(warps)), "m2s_set_sweep_warps")
+
+
+def m2s_sweep_timing(grid, enable=True):
+    """Start (clearing the counters) or stop per-launch event timing of the
+    grid's Gauss-Seidel sweep kernels."""
+    return _check(load().m2s_sweep_timing(grid, 1 if enable else 0), "m2s_sweep_timing")
+
+
+def m2s_sweep_timing_read(grid, level):
+    """(recorded launches, summed device ms, dropped launches) of `level`."""
+    n, ms, dr = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    _check(load().m2s_sweep_timing_read(grid, int(level), ctypes.byref(n), ctypes.byref(ms),
+                                        ctypes.byref(dr)), "m2s_sweep_timing_read")
+    return n.value, ms.value, dr.value
 
 
 def m2s_symgs_noalloc(b, x, n_sym_sweeps=1, stream=None):

@@ -5,28 +5,29 @@
 // of its 13 lower neighbours and the precomputed old-neighbour sum Q, on the
 // point hyperplane t = x + 2y + 4z with rows (u, v) = (y + z, z).  What
 // changes is how the wavefront is mapped onto the GPU, after measuring a
-// GB300: an L2 hit costs ~460 cycles, a GPU-scope release (membar) ~830
-// cycles of stall, a shared-memory handoff between warps ~250 cycles, a
-// global producer->consumer handoff ~1800 cycles, and FP64 instructions
-// issue at one warp-instruction per ~64 cycles per SM sub-partition.
+// GB300: an FP64 warp instruction occupies a sub-partition's FP64 pipe for
+// ~64 clocks (dependent latency ~66), an L2 hit costs ~460 clocks, a
+// GPU-scope release ~830 clocks of stall and drains the warp's outstanding
+// loads, a shared-memory handoff between warps ~250 clocks and a global
+// producer->consumer handoff ~1800.
 //
-//  * Units are CTAs of W compute warps stacked in v (warp w owns K-1
-//    computing planes plus one halo plane below them) and 32 lanes in u
-//    (lanes 0-1 are halo rows).  Warps of a CTA hand rows to each other
-//    through CTA-scope progress words in shared memory.
-//  * One extra "service" warp per CTA publishes the compute warps' progress
-//    to global memory (acquire at CTA scope, fence at GPU scope, store), so
-//    the compute warps never stall on a GPU-scope membar.
-//  * Q, b and halo rows are prefetched D steps ahead into a register ring
-//    (the step loop is unrolled by D so the ring is statically indexed): no
-//    memory latency sits on the per-step dependency chain; a consumer waits
-//    for its producers to have published step t + D before prefetching it.
+//  * Units are CTAs of W compute warps (4 or 8, chosen at run time) stacked
+//    in v, one computed plane per warp, and 32 lanes in u: lanes 0-1 replay
+//    the two rows of the unit to the left, warp 0 also replays the plane
+//    below from the unit underneath.  Units take tickets in topological
+//    order, sorted by the step at which they can start.
+//  * Values crossing units travel through a mailbox of tagged words (value
+//    and launch tag in one 64-bit relaxed store): a reader that sees the
+//    current tag has the value, so neither side fences.  Warps of a CTA
+//    pass their plane sums G through tagged shared-memory rings, with
+//    back-pressure from the consumer's progress word.
+//  * Q, b and replayed rows are prefetched D steps ahead into a register
+//    ring (the step loop is unrolled by D so the ring is statically
+//    indexed).  A warp votes once per step on all its tag checks; only a
+//    failed vote enters the bounded poll.
 //  * The 13-neighbour sum is evaluated separably: each row keeps its row
 //    3-sum H, the lane below passes H and S2 = H(u-1) + H(u), and the 3x3
-//    plane sum G = S2(u-1) + H(u) flows to the plane above: 9 floating-point
-//    operations per point.
-// Halo rows written by other CTAs or warps are loaded with ld.global.cg
-// (L2, coherent) after an acquire of the producer's progress word.
+//    plane sum G = S2(u-1) + H(u) flows to the plane above.
 #include <algorithm>
 #include <climits>
 #include <vector>
@@ -253,22 +254,53 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
         if (in1 && halo) good = Tagged<T>::unpack(regs_to_tw(q, bv), tag, &X1);
         if (in0) good = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &X0) && good;
         const TW* re = ring_in ? &sh.ring[w - 1][(tnow - 1) & (RING - 1)][lane] : nullptr;
-        const bool need_g = ring_in && __any_sync(FULL, comp);
-        if (need_g) good = Tagged<T>::unpack(*re, (unsigned)(tnow - 1 + BIAS), &gin) && good;
-        if (!__all_sync(FULL, good)) {
-            const unsigned long long t0 = global_ns();
-            for (;;) {
-                good = true;
-                if (in1 && halo)
-                    good = Tagged<T>::unpack(mb_load<T>(a.mbox, L1 + step_dir * x1), tag, &X1);
-                if (in0)
-                    good = Tagged<T>::unpack(mb_load<T>(a.mbox, L0 + step_dir * x0), tag, &X0) && good;
-                if (need_g)
-                    good = Tagged<T>::unpack(*(volatile const TW*)re, (unsigned)(tnow - 1 + BIAS), &gin) &&
-                           good;
-                if (__all_sync(FULL, good)) break;
-                if (fail()) { ok = false; return; }
-                if ((long long)(global_ns() - t0) > a.spin_ns) { timeout(); ok = false; return; }
+        const unsigned gtag = (unsigned)(tnow - 1 + BIAS);
+        if constexpr (sizeof(T) == 8) {
+            // The warp below writes a ring entry at each of its steps; this
+            // warp's step s reads the entry of its step s + 1 (all but the
+            // last), so the wait needs no vote.  A poll reloads only what is
+            // missing and reads the abort word and the clock once every 32
+            // polls, so that it costs one load.
+            bool okx = good, okg = true;
+            if (ring_in && s + 1 < S) okg = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin);
+            if (!__all_sync(FULL, okx && okg)) {
+                bool ok1 = !(in1 && halo), ok0 = !in0;
+                if (!ok1) ok1 = Tagged<T>::unpack(regs_to_tw(q, bv), tag, &X1);
+                if (!ok0) ok0 = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &X0);
+                unsigned long long t0 = 0;
+                for (int it = 1;; ++it) {
+                    if (!okg) okg = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin);
+                    if (!ok1) ok1 = Tagged<T>::unpack(mb_load<T>(a.mbox, L1 + step_dir * x1), tag, &X1);
+                    if (!ok0) ok0 = Tagged<T>::unpack(mb_load<T>(a.mbox, L0 + step_dir * x0), tag, &X0);
+                    if (__all_sync(FULL, ok1 && ok0 && okg)) break;
+                    if ((it & 31) == 0) {
+                        const unsigned long long now = global_ns();
+                        if (t0 == 0) t0 = now;
+                        if (fail()) { ok = false; return; }
+                        if ((long long)(now - t0) > a.spin_ns) { timeout(); ok = false; return; }
+                    }
+                }
+            }
+        } else {
+            // FP32: the plane-sum wait is taken when a lane computes, and a
+            // poll rereads every source and the abort word and clock: the
+            // longer poll leaves issue slots to the warp that shares the
+            // sub-partition, which measured faster for the cheap FP32 step.
+            const bool need_g = ring_in && __any_sync(FULL, comp);
+            if (need_g) good = Tagged<T>::unpack(*re, gtag, &gin) && good;
+            if (!__all_sync(FULL, good)) {
+                const unsigned long long t0 = global_ns();
+                for (;;) {
+                    good = true;
+                    if (in1 && halo)
+                        good = Tagged<T>::unpack(mb_load<T>(a.mbox, L1 + step_dir * x1), tag, &X1);
+                    if (in0)
+                        good = Tagged<T>::unpack(mb_load<T>(a.mbox, L0 + step_dir * x0), tag, &X0) && good;
+                    if (need_g) good = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin) && good;
+                    if (__all_sync(FULL, good)) break;
+                    if (fail()) { ok = false; return; }
+                    if ((long long)(global_ns() - t0) > a.spin_ns) { timeout(); ok = false; return; }
+                }
             }
         }
         // computed plane
@@ -393,28 +425,80 @@ __global__ void __launch_bounds__(W * 32, 1) gs27_cta_kernel(CtaArgs<T> a) {
 }  // namespace
 
 // Shapes of the CTA wavefront per element type: K register slots per lane
-// (one halo plane + K-1 computed planes), W compute warps per CTA, and D the
-// chunk length in steps (inputs are staged one chunk ahead, outputs flushed
-// and published once per chunk).
+// (one halo plane + K-1 computed planes) and D the depth of the input
+// prefetch ring in steps; the number W of compute warps per CTA is chosen at
+// run time (4 or 8).
 template <typename T> struct CtaShape;
-template <> struct CtaShape<double> { static constexpr int K = 2, W = 8, D = 4; };
-template <> struct CtaShape<float> { static constexpr int K = 2, W = 8, D = 8; };
+template <> struct CtaShape<double> { static constexpr int K = 2, D = 4; };
+template <> struct CtaShape<float> { static constexpr int K = 2, D = 8; };
 
-template <typename T>
+template <typename T, int W>
 size_t cta_smem_bytes() {
-    return sizeof(CtaShared<T, CtaShape<T>::W>);
+    return sizeof(CtaShared<T, W>);
+}
+
+template <typename T, int W>
+int cta_occupancy() {
+    constexpr int K = CtaShape<T>::K, D = CtaShape<T>::D;
+    const size_t smem = cta_smem_bytes<T, W>();
+    cudaFuncSetAttribute(gs27_cta_kernel<T, K, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs27_cta_kernel<T, K, W, D>, W * 32,
+                                                  smem);
+    return per_sm;
+}
+
+bool cta_warps_supported(int warps) { return warps == 4 || warps == 8; }
+
+// Default warps per unit (8: measured fastest at every level size from 32^3
+// to 256^3 on a GB300, in both precisions).
+int cta_default_warps(int dtype_is_f64, Dims d) {
+    (void)dtype_is_f64;
+    (void)d;
+    return 8;
+}
+
+int cta_rz_partials_max(Dims d) {
+    int m = 0;
+    for (int W : {4, 8}) {
+        std::vector<int2> org;
+        std::vector<int4> prod;
+        build_units_host(30, 1, 1, W + 1, d, org, prod);
+        m = std::max(m, (int)org.size() * W);
+    }
+    return m;
 }
 
 template <typename T>
-cudaError_t build_cta_units(Dims d, WaveUnits* out) {
-    constexpr int K = CtaShape<T>::K, W = CtaShape<T>::W, D = CtaShape<T>::D;
-    std::vector<int2> org;
+cudaError_t build_cta_units(Dims d, int W, WaveUnits* out) {
+    constexpr int K = CtaShape<T>::K;
+    if (!cta_warps_supported(W)) return cudaErrorInvalidValue;
+    std::vector<int2> org0, org;
     std::vector<int4> prod;
     // a CTA unit is 30 rows in u and W*(K-1) planes in v
-    build_units_host(30, 1, 1, W * (K - 1) + 1, d, org, prod);
+    const int lanes = 30, planes = W * (K - 1);
+    build_units_host(lanes, 1, 1, planes + 1, d, org0, prod);
+    // Ticket order: by the step at which a unit can start on an unloaded
+    // GPU (its right neighbour lags 2*lanes steps, the unit above 2*planes),
+    // ties by v.  Every producer (left, below, below-left) has a smaller
+    // key, so the order stays topological: a unit waits only on units with
+    // smaller tickets, which have started, and the sweep cannot deadlock.
+    std::vector<int> idx(org0.size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = (int)k;
+    auto key = [&](int k) {
+        return 2LL * lanes * (org0[k].x / lanes) + 2LL * planes * (org0[k].y / planes);
+    };
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        const long long ka = key(a), kb = key(b);
+        return ka != kb ? ka < kb : org0[a].y < org0[b].y;
+    });
+    org.resize(org0.size());
+    for (size_t k = 0; k < idx.size(); ++k) org[k] = org0[idx[k]];
     WaveUnits u{};
     u.n_units = (int)org.size();
     u.K = K;
+    u.W = W;
     u.stencil = 27;
     cudaError_t e;
     const size_t nu = std::max<size_t>(org.size(), 1);
@@ -444,22 +528,16 @@ cudaError_t build_cta_units(Dims d, WaveUnits* out) {
         free_wave_units(&u);
         return e;
     }
-    int per_sm = 0;
-    const size_t smem = cta_smem_bytes<T>();
-    cudaFuncSetAttribute(gs27_cta_kernel<T, K, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs27_cta_kernel<T, K, W, D>, W * 32, smem);
+    const int per_sm = W == 4 ? cta_occupancy<T, 4>() : cta_occupancy<T, 8>();
     u.grid = wave_grid(u.n_units, per_sm);
     *out = u;
     return cudaGetLastError();
 }
 
-int cta_units_per_rz(int dtype_is_f64) { return dtype_is_f64 ? CtaShape<double>::W : CtaShape<float>::W; }
-
 template <typename T>
 cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, Dims d, const T* Qin, T* Qout,
                             const T* b, T* x, cudaStream_t st) {
-    constexpr int K = CtaShape<T>::K, W = CtaShape<T>::W, D = CtaShape<T>::D;
+    constexpr int K = CtaShape<T>::K, D = CtaShape<T>::D;
     if (u.n_units == 0) return cudaSuccess;
     CtaArgs<T> a;
     a.nx = d.nx;
@@ -482,12 +560,17 @@ cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, Dims d, const
     a.rz = c.rz_partials;
     a.stall_unit = c.stall_unit;
     a.mbox = u.d_mbox;
-    gs27_cta_kernel<T, K, W, D><<<u.grid, W * 32, cta_smem_bytes<T>(), st>>>(a);
+    if (u.W == 4)
+        gs27_cta_kernel<T, K, 4, D><<<u.grid, 4 * 32, cta_smem_bytes<T, 4>(), st>>>(a);
+    else if (u.W == 8)
+        gs27_cta_kernel<T, K, 8, D><<<u.grid, 8 * 32, cta_smem_bytes<T, 8>(), st>>>(a);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-template cudaError_t build_cta_units<double>(Dims, WaveUnits*);
-template cudaError_t build_cta_units<float>(Dims, WaveUnits*);
+template cudaError_t build_cta_units<double>(Dims, int, WaveUnits*);
+template cudaError_t build_cta_units<float>(Dims, int, WaveUnits*);
 template cudaError_t launch_gs27_cta<double>(const WaveUnits&, const WaveCall&, Dims, const double*,
                                              double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_gs27_cta<float>(const WaveUnits&, const WaveCall&, Dims, const float*,

@@ -19,6 +19,7 @@ namespace {
 
 constexpr int kMaxLevels = 8;
 constexpr int kWaveK = 5;
+constexpr int kMaxTimed = 16384;  // recorded sweep launches per level
 
 template <typename T>
 struct Work {
@@ -58,6 +59,13 @@ struct m2s_grid {
     int stall_level = -1;  // test hook consumed by the next sweep on that level
     int stall_unit = -1;
     BlockOp blk;
+    // per-level event pairs bracketing sweep launches (m2s_sweep_timing)
+    struct Timing {
+        std::vector<cudaEvent_t> ev;  // 2 per recorded launch
+        int used = 0, dropped = 0;
+    };
+    bool timing = false;
+    std::vector<Timing> tim;
     std::vector<void*> allocs;
     cudaStream_t last_stream = nullptr;
 };
@@ -94,6 +102,8 @@ void destroy_grid(m2s_grid* g) {
     for (auto& pl : g->units32)
         for (auto& u : pl) free_wave_units(&u);
     for (void* p : g->allocs) cudaFree(p);
+    for (auto& t : g->tim)
+        for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
     delete g;
 }
 
@@ -156,11 +166,34 @@ cudaError_t op_sweep(m2s_grid* g, int i, int l, int rev, const T* Qin, T* Qout, 
         g->stall_level = -1;
         g->stall_unit = -1;
     }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (g->timing) {
+        m2s_grid::Timing& t = g->tim[l];
+        if (t.used >= kMaxTimed) {
+            ++t.dropped;
+        } else {
+            while ((int)t.ev.size() < 2 * (t.used + 1)) {
+                cudaEvent_t e;
+                cudaError_t er = cudaEventCreate(&e);
+                if (er != cudaSuccess) return er;
+                t.ev.push_back(e);
+            }
+            e0 = t.ev[2 * t.used];
+            e1 = t.ev[2 * t.used + 1];
+            ++t.used;
+            cudaError_t er = cudaEventRecord(e0, st);
+            if (er != cudaSuccess) return er;
+        }
+    }
+    cudaError_t e;
     if (g->op == M2S_OP_HPCG27) {
         const WaveUnits& u = sizeof(T) == 8 ? g->units[i][l] : g->units32[i][l];
-        return launch_gs27_cta<T>(u, c, d, Qin, Qout, b, x, st);
+        e = launch_gs27_cta<T>(u, c, d, Qin, Qout, b, x, st);
+    } else {
+        e = launch_gs7_wave<T>(g->units[i][l], c, d, klev<T>(g, l), Qin, Qout, b, x, st);
     }
-    return launch_gs7_wave<T>(g->units[i][l], c, d, klev<T>(g, l), Qin, Qout, b, x, st);
+    if (e == cudaSuccess && e1) e = cudaEventRecord(e1, st);
+    return e;
 }
 
 template <typename T>
@@ -213,8 +246,31 @@ cudaError_t gs_sweep(m2s_grid* g, int i, int l, const T* b, T* x, int rev, cudaS
     return op_sweep<T>(g, i, l, rev, w.Qa[l], nullptr, b, x, nullptr, st);
 }
 
-// b.x partials written per sweep unit by the last sweep of a V-cycle
-int rz_per_unit(m2s_grid* g) { return g->op == M2S_OP_HPCG27 ? cta_units_per_rz(1) : 1; }
+// b.x partials written by the last sweep of a V-cycle on the finest level
+int rz_partials(m2s_grid* g, int i) {
+    const WaveUnits& u = g->units[i][0];
+    return u.n_units * (g->op == M2S_OP_HPCG27 ? u.W : 1);
+}
+
+// (Re)build the 27-point sweep schedules of problem i on level l.
+cudaError_t build_level_units27(m2s_grid* g, int i, int l, int w64, int w32) {
+    WaveUnits a{}, b{};
+    cudaError_t e = build_cta_units<double>(g->dims[i][l], w64, &a);
+    if (e != cudaSuccess) {
+        free_wave_units(&a);
+        return e;
+    }
+    if ((e = build_cta_units<float>(g->dims[i][l], w32, &b)) != cudaSuccess) {
+        free_wave_units(&a);
+        free_wave_units(&b);
+        return e;
+    }
+    free_wave_units(&g->units[i][l]);
+    free_wave_units(&g->units32[i][l]);
+    g->units[i][l] = a;
+    g->units32[i][l] = b;
+    return cudaSuccess;
+}
 
 bool valid_level(m2s_grid* g, int level) { return g && level >= 0 && level < g->levels; }
 
@@ -240,7 +296,7 @@ m2s_status pcg_problem(m2s_grid* g, int i, const double* b, double* x, const m2s
     const bool f32 = g->pdtype == M2S_F32;
     const int nd = dot_num_partials(n);
     const int nst = g->op == M2S_OP_HPCG27 ? st27_num_partials(d) : nd;
-    const int nu = g->units[i][0].n_units * rz_per_unit(g);
+    const int nu = rz_partials(g, i);
 
     M2S_TRY(cudaMemsetAsync(x + off, 0, n * sizeof(double), st));
     M2S_TRY(cudaMemcpyAsync(r, b + off, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -357,6 +413,7 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     g->pdtype = pdt;
     g->has32 = op == M2S_OP_HPCG27 || (op == M2S_OP_DIFF7_KAPPA && pdt == M2S_F32);
     const int L = g->levels;
+    g->tim.resize(L);
     g->dims.assign(n_problems, std::vector<Dims>(L));
     g->ltot.assign(L, 0);
     for (int l = 0; l < L; ++l)
@@ -467,9 +524,8 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     for (int i = 0; i < n_problems; ++i)
         for (int l = 0; l < L; ++l) {
             if (op == M2S_OP_HPCG27) {
-                if ((e = build_cta_units<double>(g->dims[i][l], &g->units[i][l])) != cudaSuccess)
-                    return fail(e);
-                if ((e = build_cta_units<float>(g->dims[i][l], &g->units32[i][l])) != cudaSuccess)
+                if ((e = build_level_units27(g, i, l, cta_default_warps(1, g->dims[i][l]),
+                                             cta_default_warps(0, g->dims[i][l]))) != cudaSuccess)
                     return fail(e);
             } else if ((e = build_wave_units(7, kWaveK, g->dims[i][l], &g->units[i][l])) !=
                        cudaSuccess) {
@@ -488,7 +544,9 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     for (int i = 0; i < n_problems; ++i) {
         np = std::max(np, dot_num_partials(g->dims[i][0].n));
         np = std::max(np, st27_num_partials(g->dims[i][0]));
-        np = std::max(np, g->units[i][0].n_units * rz_per_unit(g));
+        // room for the b.x partials of any unit shape m2s_set_sweep_warps allows
+        np = std::max(np, op == M2S_OP_HPCG27 ? cta_rz_partials_max(g->dims[i][0])
+                                              : g->units[i][0].n_units);
     }
     g->npart = np;
     if ((e = galloc(g, &g->part, np)) != cudaSuccess) return fail(e);
@@ -510,6 +568,44 @@ m2s_status m2s_debug_stall_unit(m2s_grid* grid, int level, int unit) {
         return M2S_ERR_INVALID_ARG;
     grid->stall_level = level;
     grid->stall_unit = unit;
+    return M2S_OK;
+}
+
+m2s_status m2s_sweep_timing(m2s_grid* grid, int enable) {
+    if (!grid) return M2S_ERR_INVALID_ARG;
+    if (enable)
+        for (auto& t : grid->tim) t.used = t.dropped = 0;
+    grid->timing = enable != 0;
+    return M2S_OK;
+}
+
+m2s_status m2s_sweep_timing_read(m2s_grid* grid, int level, int* launches, double* total_ms,
+                                 int* dropped) {
+    if (!grid || level < 0 || level >= (int)grid->tim.size()) return M2S_ERR_INVALID_ARG;
+    const m2s_grid::Timing& t = grid->tim[level];
+    double ms = 0.0;
+    for (int k = 0; k < t.used; ++k) {
+        M2S_TRY(cudaEventSynchronize(t.ev[2 * k + 1]));
+        float f = 0.f;
+        M2S_TRY(cudaEventElapsedTime(&f, t.ev[2 * k], t.ev[2 * k + 1]));
+        ms += f;
+    }
+    if (launches) *launches = t.used;
+    if (total_ms) *total_ms = ms;
+    if (dropped) *dropped = t.dropped;
+    return M2S_OK;
+}
+
+m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps) {
+    if (!grid || grid->op != M2S_OP_HPCG27 || !cta_warps_supported(warps)) return M2S_ERR_INVALID_ARG;
+    if (level < -1 || level >= grid->levels) return M2S_ERR_INVALID_ARG;
+    M2S_TRY(cudaDeviceSynchronize());
+    for (int l = 0; l < grid->levels; ++l) {
+        if (level >= 0 && l != level) continue;
+        for (int i = 0; i < grid->np; ++i) {
+            M2S_TRY(build_level_units27(grid, i, l, warps, warps));
+        }
+    }
     return M2S_OK;
 }
 

@@ -88,6 +88,7 @@ struct WaveUnits {
     int grid;         // CTAs launched
     int K;            // slots per lane (incl. the halo slot)
     int stencil;      // 27 or 7
+    int W = 1;        // CTA kernel: compute warps (planes) per unit
 };
 struct WaveCall {
     int rev;              // 0 forward, 1 backward (reflected index space)
@@ -149,11 +150,13 @@ int wave_blocks_per_sm(int stencil);
 constexpr int kWaveSlots = 5;  // register slots per lane of the sweep kernels
 // CTA-pipelined 27-point sweep (k_wave2.cu)
 template <typename T>
-cudaError_t build_cta_units(Dims d, WaveUnits* out);
+cudaError_t build_cta_units(Dims d, int warps, WaveUnits* out);
+bool cta_warps_supported(int warps);
+int cta_default_warps(int dtype_is_f64, Dims d);
+int cta_rz_partials_max(Dims d);  // b.x partials of the largest schedule
 template <typename T>
 cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, Dims d, const T* Qin, T* Qout,
                             const T* b, T* x, cudaStream_t st);
-int cta_units_per_rz(int dtype_is_f64);
 void free_wave_units(WaveUnits* u);
 
 // Vector kernels (k_vec.cu).

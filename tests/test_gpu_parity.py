@@ -222,6 +222,65 @@ def test_sweep_timeout_is_reported_and_recoverable(m):
     assert err64(host(x), oracle.gs_forward(H27, b, x0)) <= TOL64
 
 
+@pytest.mark.parametrize("shape", [(5, 3, 4), (17, 33, 32), (33, 17, 35), (64, 64, 64),
+                                   (40, 11, 3), (40, 7, 3), (70, 5, 2)])
+@pytest.mark.parametrize("f32", [False, True])
+def test_sweep_unit_shapes_agree_bitwise(m, shape, f32):
+    """4- and 8-warp sweep units compute every point with the same
+    arithmetic: two symmetric sweeps agree bitwise, and with the oracle.
+    (40, 11, 3) and (40, 7, 3) need a unit without valid rows below a unit
+    whose lowest row reads the sums of the rows beside it (4 and 8 warps)."""
+    import torch
+    b, x0 = rnd(shape, 14), rnd(shape, 15)
+    dt = torch.float32 if f32 else torch.float64
+    out = []
+    for w in (4, 8):
+        g = make_grid(m, shape, levels=2, pdt=1 if f32 else 0)
+        m.m2s_set_sweep_warps(g.handle, -1, w)
+        x = dev(x0, dt)
+        m.m2s_symgs(g.handle, 0, dev(b, dt), x, 2)
+        out.append(host(x))
+    assert np.array_equal(out[0], out[1])
+    if f32:
+        assert err32(out[0], oracle.symgs_f32(H27, b, x0, 2)) <= TOL32
+    else:
+        assert err64(out[0], oracle.symgs(H27, b, x0, 2)) <= TOL64
+
+
+def test_mg_pcg_with_four_warp_units(m):
+    import torch
+    shape = (64, 64, 64)
+    g = make_grid(m, shape, levels=4)
+    m.m2s_set_sweep_warps(g.handle, -1, 4)
+    bh = oracle.apply(H27, np.ones(shape))
+    x = torch.empty(shape, dtype=torch.float64, device="cuda")
+    st, res = m.m2s_pcg_solve(g.handle, dev(bh), x, max_iters=20, fixed_iters=True)
+    ox, oit, ohist, ost = oracle.pcg(H27, bh, 4, max_iters=20, fixed_iters=True)
+    assert st == m.Status.OK and res.iters == 20
+    assert err(host(x), ox) <= TOL64
+    assert abs(res.resid_hist_last - ohist[-1]) <= 1e-8 * ohist[-1] + 1e-14 * ohist[0]
+
+
+def test_sweep_timing_counts_launches(m):
+    """Per-launch sweep timing: one event pair per sweep kernel on the level
+    it runs on, nothing recorded once disabled, results unchanged."""
+    shape = (24, 24, 24)
+    g = make_grid(m, shape, levels=2)
+    b, x0 = rnd(shape, 12), rnd(shape, 13)
+    m.m2s_sweep_timing(g.handle, True)
+    x = dev(x0)
+    m.m2s_symgs(g.handle, 0, dev(b), x, 2)
+    n0, ms0, dr0 = m.m2s_sweep_timing_read(g.handle, 0)
+    n1, ms1, _ = m.m2s_sweep_timing_read(g.handle, 1)
+    assert (n0, dr0, n1, ms1) == (4, 0, 0, 0.0) and ms0 > 0
+    assert err64(host(x), oracle.symgs(H27, b, x0, 2)) <= TOL64
+    m.m2s_sweep_timing(g.handle, False)
+    m.m2s_gs_sweep(g.handle, 0, dev(b), x, m.FORWARD)
+    assert m.m2s_sweep_timing_read(g.handle, 0)[0] == 4
+    m.m2s_sweep_timing(g.handle, True)
+    assert m.m2s_sweep_timing_read(g.handle, 0)[0] == 0
+
+
 # ---------------------------------------------------------------------------
 # a5-a7: restriction, prolongation, V-cycle
 # ---------------------------------------------------------------------------
