@@ -493,3 +493,36 @@ def test_batched_problems(m):
         ox, _, _, _ = oracle.pcg(K7, bb, 3, k, max_iters=10, fixed_iters=True)
         assert err(xh[off:off + n].reshape(s), ox) <= TOL64
         off += n
+
+
+# ---------------------------------------------------------------------------
+# full sizes: the FP64 MG-PCG solve against the oracle's stored history
+# (tests/golden/make_hpcg_pcg_history.py, which calls only the oracle)
+# ---------------------------------------------------------------------------
+def golden_history(n):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "hpcg_pcg_history_%d.txt" % n)
+    with open(path) as f:
+        return np.array([float(v) for v in f if v.strip() and not v.startswith("#")])
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_mg_pcg_full_size_matches_oracle_history(m, n):
+    """b = A*ones, x0 = 0, 4 levels, to 1e-10: the same iteration count as
+    the oracle, the same final residual norm (to rounding growth over the
+    solve), and x within the solve's error of ones."""
+    import torch
+    hist = golden_history(n)
+    shape = (n, n, n)
+    g = make_grid(m, shape, levels=4)
+    ones = torch.ones(shape, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(ones)
+    m.m2s_spmv(g.handle, 0, ones, b)
+    x = torch.empty_like(ones)
+    st, res = m.m2s_pcg_solve(g.handle, b, x, max_iters=500, rtol=1e-10, fixed_iters=False)
+    assert st == m.Status.OK
+    assert res.iters == len(hist) - 1
+    assert abs(res.resid_hist_last - hist[-1]) <= 1e-6 * hist[-1]
+    assert float((x - 1.0).abs().max()) < 1e-8
+    g.close()

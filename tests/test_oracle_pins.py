@@ -556,3 +556,21 @@ def test_inputs_deterministic_and_distributed():
     assert np.array_equal(k, gen.kappa_field(48, seed=9))
     s = gen.batch_sides(64)
     assert len(s) == 64 and set(s) <= set(gen.BATCH_SIDES) and len(set(s)) >= 4
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+def test_stored_pcg_histories_start_at_closed_form_norm_of_b(n):
+    """The stored oracle residual histories (tests/golden) start at
+    ||r0|| = ||b|| with b = A*ones, whose entries are 27 - prod(3 or 2 per
+    axis): 0 inside, 9 on faces, 15 on edges, 19 at corners; and they end
+    below 1e-10 ||b|| (the stopping rule), the step before not."""
+    import os
+    from math import comb
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "hpcg_pcg_history_%d.txt" % n)
+    with open(path) as f:
+        hist = np.array([float(v) for v in f if v.strip() and not v.startswith("#")])
+    bb = sum(comb(3, k) * 2 ** k * (n - 2) ** (3 - k) * (27 - 3 ** (3 - k) * 2 ** k) ** 2
+             for k in range(4))
+    assert abs(hist[0] - np.sqrt(bb)) <= 1e-12 * np.sqrt(bb)
+    assert hist[-1] <= 1e-10 * hist[0] < hist[-2]
