@@ -185,6 +185,7 @@ def sweep_traffic(kernel_tag):
 
 # sources of the dominant kernel (its DRAM traffic is invalid once they change)
 SWEEP_SOURCES = ("paper_2204_13304_gb300/csrc/k_wave2.cu",
+                 "paper_2204_13304_gb300/csrc/m2s_cta.cuh",
                  "paper_2204_13304_gb300/csrc/m2s_wave_sync.cuh",
                  "paper_2204_13304_gb300/csrc/m2s_internal.cuh")
 

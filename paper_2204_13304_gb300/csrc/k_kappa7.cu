@@ -8,7 +8,8 @@
 // a zero ghost value.  In matrix form a_pp = sum_f k_f and a_pq = -k_f.
 //
 // The face coefficients, the diagonal and its inverse are formed once per
-// level at set-up (kf[d][p] couples p and p - e_d, 0 on the boundary), so the
+// level at set-up (kf[d][p] couples p and p - e_d, kr[d][p] couples p and
+// p + e_d, 0 on the boundary), so the
 // SpMV costs 1 multiply + 6 FMAs per point: on GB300 FP64 issue, not HBM, is
 // the scarce resource.
 #include "m2s_internal.cuh"
@@ -78,6 +79,9 @@ __global__ void kappa_setup_kernel(Dims d, const double* __restrict__ kappa, Kap
     k.kf[0][p] = fxm;
     k.kf[1][p] = fym;
     k.kf[2][p] = fzm;
+    k.kr[0][p] = fxp;
+    k.kr[1][p] = fyp;
+    k.kr[2][p] = fzp;
     k.diag[p] = dg;
     k.invdiag[p] = T(1) / dg;
 }

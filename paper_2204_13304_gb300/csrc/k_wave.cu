@@ -1,6 +1,10 @@
-// Exact-order Gauss-Seidel sweeps as a persistent wavefront (paper Sec. 4.3.3
-// SymGS; Sec. 6.1 SewTh: partition, crossing dependences, compaction to one
-// monotone counter per producer, hyperplane parallelism).
+// Exact-order 27-point Gauss-Seidel sweeps as a persistent wavefront of
+// single-warp units (paper Sec. 4.3.3 SymGS; Sec. 6.1 SewTh: partition,
+// crossing dependences, compaction to one monotone counter per producer,
+// hyperplane parallelism).  This is the first GPU form of the sweep; the
+// allocation-free entry point uses it (it needs no mailbox), the grid
+// entry points use the CTA wavefronts of k_wave2.cu (27-point) and
+// k_wave7.cu (7-point).  The unit-table helpers below serve all of them.
 //
 // Every point p is updated in increasing lexicographic order in the sense of
 // the method: it sees the NEW values of its lower neighbours and the OLD
@@ -17,12 +21,11 @@
 // p' = n-1-p (x' = nx-1-x, ...): both stencils are symmetric under the
 // reflection, and the reflected lexicographic order is the decreasing order.
 //
-// Schedule.  27-point: the point hyperplane t = x + 2y + 4z satisfies every
+// Schedule.  The point hyperplane t = x + 2y + 4z satisfies every
 // dependence (Eq. "hyperplane" of Sec. 6.1.3 with unit partitions).  Rows
 // (y, z) are indexed by (u, v) = (y + z, z); row (u, v) handles x at time
 // t - 2u - 2v, and every row it depends on has smaller or equal (u, v), so
 // producer/consumer relations between units only point "down-left".
-// 7-point: t = x + y + z, (u, v) = (y, z).
 //
 // Units.  One warp = one unit: lane i <-> u, register slot j <-> v; the
 // first HL lanes and slot 0 are halo rows that REPLAY the producers' rows by
@@ -60,10 +63,6 @@ struct WaveArgs {
     T* Qout;
     const T* b;
     T* x;
-    const T* kf0;      // 7-point only: face coefficients (x, y, z)
-    const T* kf1;
-    const T* kf2;
-    const T* invdiag;  // 7-point only
     const int2* origin;
     const int4* prod;
     int n_units;
@@ -166,110 +165,12 @@ __device__ __forceinline__ void unit27(const WaveArgs<T>& a, int t) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// 7-point variable-kappa unit: HL = 1 halo lane, window depth 1.  The face
-// coefficients come from the level's face arrays: kf[d][p] couples p and
-// p - e_d; in the reflected (backward) space the lower neighbour of a point
-// is its physical upper neighbour, whose face is stored at p + e_d.
-// ---------------------------------------------------------------------------
-template <typename T, int K>
-__device__ __forceinline__ void unit7(const WaveArgs<T>& a, int t) {
-    constexpr int HL = 1;
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int2 org = a.origin[t];
-    const int4 pr = a.prod[t];
-    const int y = org.x - HL + lane;
-    const int tbase = (org.x - HL) + (org.y - 1);
-    const bool has_prod = pr.x >= 0 || pr.y >= 0 || pr.z >= 0;
-    const i64 sy = a.nx, sz = (i64)a.nx * a.ny;
-
-    bool rv[K];
-    i64 base[K];
-    const i64 dir = a.rev ? -1 : 1;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const int z = org.y - 1 + j;
-        rv[j] = z >= 0 && z < a.nz && y >= 0 && y < a.ny;
-        const i64 rb = rv[j] ? ((i64)z * a.ny + y) * a.nx : 0;
-        base[j] = a.rev ? a.off + a.n - 1 - rb : a.off + rb;
-    }
-    T w[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) w[j] = T(0);
-
-    double rz = 0.0;
-    int cached = 0;
-    const int S = a.nx + 31 + (K - 1);
-    const bool halo_lane = lane < HL;
-    for (int s = 0; s < S; ++s) {
-        const int tnow = s + tbase;
-        if (has_prod && tnow + BIAS > cached) {
-            if (!wait_producers(a.flags, pr, tnow + BIAS, &cached, a.status, a.spin_ns)) return;
-        }
-        T upw[K];
-#pragma unroll
-        for (int j = 1; j < K; ++j) upw[j] = __shfl_up_sync(FULL, w[j], 1);
-        T nv[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int x = s - lane - j;
-            const bool in = rv[j] && x >= 0 && x < a.nx;
-            nv[j] = T(0);
-            if (!in) continue;
-            const i64 p = base[j] + dir * x;
-            if (j == 0 || halo_lane) {
-                // lane 0 of slot 0 is nobody's neighbour in the 7-point
-                // stencil (no diagonal couplings): leave it at zero.
-                if (!(j == 0 && halo_lane)) nv[j] = __ldcg(a.x + p);
-            } else {
-                // lower neighbours: x-1 (own window), y-1 (lane below),
-                // z-1 (slot below); a missing neighbour holds 0.
-                const int zz = org.y - 1 + j;
-                T cx, cy, cz;
-                if (!a.rev) {
-                    cx = a.kf0[p];
-                    cy = a.kf1[p];
-                    cz = a.kf2[p];
-                } else {
-                    cx = x > 0 ? a.kf0[p + 1] : T(0);
-                    cy = y > 0 ? a.kf1[p + sy] : T(0);
-                    cz = zz > 0 ? a.kf2[p + sz] : T(0);
-                }
-                T N = cx * w[j];
-                N = fma(cy, upw[j], N);
-                N = fma(cz, w[j - 1], N);
-                const T q = a.Qin[p];
-                const T bp = a.b[p];
-                const T xn = (q + N) * a.invdiag[p];
-                a.x[p] = xn;
-                if (a.Qout) a.Qout[p] = bp + N;
-                if (a.rz) rz = fma((double)bp, (double)xn, rz);
-                nv[j] = xn;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < K; ++j) w[j] = nv[j];
-        if ((s + 1) % a.publish_every == 0) publish(a.flags + t, tnow + BIAS);
-    }
-    publish(a.flags + t, DONE);
-    if (a.rz) {
-        for (int o = 16; o > 0; o >>= 1) rz += __shfl_down_sync(FULL, rz, o);
-        if (lane == 0) a.rz[t] = rz;
-    }
-}
-
 template <typename T, int K>
 __global__ void __launch_bounds__(32) gs27_wave_kernel(WaveArgs<T> a) {
     run_units(a.n_units, a.flags, a.ctrl, a.status, [&](int t) { unit27<T, K>(a, t); },
               a.stall_unit);
 }
 
-template <typename T, int K>
-__global__ void __launch_bounds__(32) gs7_wave_kernel(WaveArgs<T> a) {
-    run_units(a.n_units, a.flags, a.ctrl, a.status, [&](int t) { unit7<T, K>(a, t); },
-              a.stall_unit);
-}
 
 }  // namespace
 
@@ -326,11 +227,9 @@ int wave_grid(int n_units, int per_sm) {
 }
 
 int wave_blocks_per_sm(int stencil) {
+    (void)stencil;
     int per_sm = 0;
-    if (stencil == 27)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs27_wave_kernel<double, 5>, 32, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs7_wave_kernel<double, 5>, 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs27_wave_kernel<double, 5>, 32, 0);
     return std::max(1, per_sm);
 }
 
@@ -367,15 +266,6 @@ cudaError_t build_units(int lanes, int skew, int corner, int K, Dims d, int per_
     return cudaSuccess;
 }
 
-cudaError_t build_wave_units(int stencil, int K, Dims d, WaveUnits* out) {
-    const int per_sm = wave_blocks_per_sm(stencil);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = stencil == 27 ? build_units(30, 1, 1, K, d, per_sm, out)
-                      : build_units(31, 0, 0, K, d, per_sm, out);
-    if (e == cudaSuccess) out->stencil = stencil;
-    return e;
-}
 
 void free_wave_units(WaveUnits* u) {
     if (u->d_origin) cudaFree(u->d_origin);
@@ -402,8 +292,6 @@ static WaveArgs<T> make_args(const WaveUnits& u, const WaveCall& c, Dims d, cons
     a.Qout = Qout;
     a.b = b;
     a.x = x;
-    a.kf0 = a.kf1 = a.kf2 = nullptr;
-    a.invdiag = nullptr;
     a.origin = u.d_origin;
     a.prod = u.d_prod;
     a.n_units = u.n_units;
@@ -424,29 +312,11 @@ cudaError_t launch_gs27_wave(const WaveUnits& u, const WaveCall& c, Dims d, cons
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_gs7_wave(const WaveUnits& u, const WaveCall& c, Dims d, const KappaLevel<T>& k,
-                            const T* Qin, T* Qout, const T* b, T* x, cudaStream_t st) {
-    if (u.n_units == 0) return cudaSuccess;
-    WaveArgs<T> a = make_args<T>(u, c, d, Qin, Qout, b, x);
-    a.kf0 = k.kf[0];
-    a.kf1 = k.kf[1];
-    a.kf2 = k.kf[2];
-    a.invdiag = k.invdiag;
-    gs7_wave_kernel<T, 5><<<u.grid, 32, 0, st>>>(a);
-    return cudaGetLastError();
-}
 
 template cudaError_t launch_gs27_wave<double>(const WaveUnits&, const WaveCall&, Dims,
                                               const double*, double*, const double*, double*,
                                               cudaStream_t);
 template cudaError_t launch_gs27_wave<float>(const WaveUnits&, const WaveCall&, Dims, const float*,
                                              float*, const float*, float*, cudaStream_t);
-template cudaError_t launch_gs7_wave<double>(const WaveUnits&, const WaveCall&, Dims,
-                                             const KappaLevel<double>&, const double*, double*,
-                                             const double*, double*, cudaStream_t);
-template cudaError_t launch_gs7_wave<float>(const WaveUnits&, const WaveCall&, Dims,
-                                            const KappaLevel<float>&, const float*, float*,
-                                            const float*, float*, cudaStream_t);
 
 }  // namespace m2s

@@ -1,0 +1,381 @@
+// Exact-order 7-point (variable kappa) Gauss-Seidel sweep, CTA-pipelined
+// wavefront.
+//
+// Paper Sec. 4.3.3 (Seidel-style stencils) and Sec. 6.1 (SewTh): every point
+// is updated in lexicographic order from the new values of its 3 lower
+// neighbours and the old-neighbour sum Q:
+//     x_p = (Q_p + k_x x_{p-e_x} + k_y x_{p-e_y} + k_z x_{p-e_z}) / a_pp,
+//     Q'_p = b_p + (the same lower sum)            (next sweep's Q),
+// and the backward sweep is the forward sweep in reflected index space, with
+// the coefficients of the upper faces (kr) in place of the lower ones (kf).
+// Points of the hyperplane t = x + y + z are independent.
+//
+// GPU mapping: a unit is a CTA of W warps; warp w owns plane z = z0 + w, lane
+// l row y = y0 - 1 + l (lane 0 replays row y0 - 1 of the unit to the left
+// from its mailbox, lanes 1-31 compute).  At local step s lane l of warp w is
+// at x = s - l - w: every thread of the CTA is on the same hyperplane, the
+// y - 1 neighbour is the lane below one step earlier (a shuffle of its
+// previous value), the z - 1 neighbour the warp below one step earlier
+// (a tagged shared-memory ring) or, for warp 0, the top warp of the unit
+// underneath (tagged mailbox).  The synchronisation pieces are those of the
+// 27-point sweep (k_wave2.cu): tagged words, a vote per step, bounded polls.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "m2s_cta.cuh"
+#include "m2s_internal.cuh"
+#include "m2s_wave_sync.cuh"
+
+namespace m2s {
+
+namespace {
+
+using namespace wave;
+using namespace cta;
+
+constexpr int LANES7 = 31;  // computing rows per unit
+
+template <typename T>
+struct Cta7Args {
+    int nx, ny, nz;
+    i64 n, off;
+    int rev;
+    long long spin_ns;
+    const T* Qin;
+    T* Qout;
+    const T* b;
+    T* x;
+    const T* k0;  // coefficient of the lower x / y / z neighbour in sweep
+    const T* k1;  // order, indexed like x (packed level arrays)
+    const T* k2;
+    const T* invd;
+    const int2* origin;  // (y0, z0) per unit, in ticket order
+    int n_units;
+    int* ctrl;
+    DevStatus* status;
+    double* rz;
+    int stall_unit;
+    u64* mbox;
+};
+
+template <typename T, int W>
+struct Cta7Shared {
+    typename Tagged<T>::W ring[W][RING][32];
+    volatile int prog[W];
+};
+
+template <typename T, int W, int D>
+__device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
+                                            Cta7Shared<T, W>& sh, unsigned tag) {
+    typedef typename Tagged<T>::W TW;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int2 org = a.origin[t];
+    const int y = org.x - 1 + lane;
+    const int z = org.y + w;
+    const bool halo = lane == 0;
+    const bool rv = y >= 0 && y < a.ny && z < a.nz;
+    const bool ring_in = w > 0;
+    const bool ring_out = w < W - 1;
+    const bool mb_out = !halo && (lane == 31 || w == W - 1);
+    const bool zmb = w == 0 && z >= 1;  // plane below from the unit underneath
+    const int nx = a.nx;
+    const i64 dir = a.rev ? -1 : 1;
+    const i64 r = rv ? ((i64)z * a.ny + y) * nx : 0;
+    const i64 L = a.rev ? a.n - 1 - r : r;  // problem-local index of x = 0
+    const i64 szd = dir * (i64)nx * a.ny;   // index step of the z - 1 neighbour
+    const T* Q = a.Qin + a.off;
+    const T* B = a.b + a.off;
+    const T* K0 = a.k0 + a.off;
+    const T* K1 = a.k1 + a.off;
+    const T* K2 = a.k2 + a.off;
+    const T* ID = a.invd + a.off;
+    T* Xo = a.x + a.off;
+    T* Qo = a.Qout ? a.Qout + a.off : nullptr;
+    const bool want_rz = sizeof(T) == 8 && a.rz != nullptr;
+    const int S = nx + LANES7 + W;
+
+    T xm1 = 0;
+    // prefetch ring: Q, b, the three coefficients and 1/a_pp (computing
+    // lanes) or the mailbox words of the replayed row (lane 0); the mailbox
+    // words of the plane below (warp 0)
+    T rq[D], rb[D], r0[D], r1[D], r2[D], rd[D], rz0[D], rz1[D];
+    auto fetch = [&](int k, int s) {
+        const int xx = s - lane - w;
+        T q = 0, bv = 0, c0 = 0, c1 = 0, c2 = 0, dd = 0, m0 = 0, m1 = 0;
+        if (rv && (unsigned)xx < (unsigned)nx) {
+            const i64 p = L + dir * xx;
+            if (!halo) {
+                q = __ldg(Q + p);
+                bv = __ldg(B + p);
+                c0 = __ldg(K0 + p);
+                c1 = __ldg(K1 + p);
+                c2 = __ldg(K2 + p);
+                dd = __ldg(ID + p);
+                if (zmb) tw_to_regs(mb_load<T>(a.mbox, p - szd), &m0, &m1);
+            } else {
+                tw_to_regs(mb_load<T>(a.mbox, p), &q, &bv);
+            }
+        }
+        rq[k] = q;
+        rb[k] = bv;
+        r0[k] = c0;
+        r1[k] = c1;
+        r2[k] = c2;
+        rd[k] = dd;
+        rz0[k] = m0;
+        rz1[k] = m1;
+    };
+#pragma unroll
+    for (int k = 0; k < D; ++k) fetch(k, k);
+
+    double rzs = 0.0;
+    bool ok = true;
+    int cachedC = -(1 << 30);
+    auto fail = [&]() -> bool {
+        int ab = 0;
+        if (lane == 0) ab = ld_relaxed_gpu(&a.status->abort);
+        return __shfl_sync(FULL, ab, 0) != 0;
+    };
+    auto timeout = [&]() {
+        if (lane == 0) {
+            atomicCAS(&a.status->err, 0, (int)M2S_ERR_TIMEOUT);
+            atomicExch(&a.status->abort, 1);
+        }
+    };
+    auto step = [&](int s, int k) {
+        const int xx = s - lane - w;
+        const T q = rq[k], bv = rb[k], c0 = r0[k], c1 = r1[k], c2 = r2[k], dd = rd[k];
+        const T m0 = rz0[k], m1 = rz1[k];
+        fetch(k, s + D);
+        const bool in = rv && (unsigned)xx < (unsigned)nx;
+        const bool comp = in && !halo;
+        // replayed row (lane 0), plane below (mailbox for warp 0, ring of the
+        // warp below, which writes an entry at each of its steps; this
+        // warp's step s reads the entry of its step s - 1)
+        T X1 = 0, zv = 0;
+        bool okx = true, okz = true, okr = true;
+        if (in && halo) okx = Tagged<T>::unpack(regs_to_tw(q, bv), tag, &X1);
+        if (comp && zmb) okz = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &zv);
+        const TW* re = ring_in ? &sh.ring[w - 1][(s - 1) & (RING - 1)][lane] : nullptr;
+        const unsigned rtag = (unsigned)(s - 1 + BIAS);
+        if (ring_in && s >= 1) okr = Tagged<T>::unpack(*(volatile const TW*)re, rtag, &zv);
+        if (!__all_sync(FULL, okx && okz && okr)) {
+            // poll only what is missing; the abort word and the clock are
+            // read once every 32 polls
+            const i64 p = L + dir * xx;
+            unsigned long long t0 = 0;
+            for (int it = 1;; ++it) {
+                if (!okr) okr = Tagged<T>::unpack(*(volatile const TW*)re, rtag, &zv);
+                if (!okx) okx = Tagged<T>::unpack(mb_load<T>(a.mbox, p), tag, &X1);
+                if (!okz) okz = Tagged<T>::unpack(mb_load<T>(a.mbox, p - szd), tag, &zv);
+                if (__all_sync(FULL, okx && okz && okr)) break;
+                if ((it & 31) == 0) {
+                    const unsigned long long now = global_ns();
+                    if (t0 == 0) t0 = now;
+                    if (fail()) { ok = false; return; }
+                    if ((long long)(now - t0) > a.spin_ns) { timeout(); ok = false; return; }
+                }
+            }
+        }
+        const T hu = __shfl_up_sync(FULL, xm1, 1);  // row y - 1 at this x
+        if (comp) {
+            T N = c0 * xm1;
+            N = fma(c1, hu, N);
+            N = fma(c2, zv, N);
+            X1 = (q + N) * dd;
+            const i64 p = L + dir * xx;
+            Xo[p] = X1;
+            if (Qo) Qo[p] = bv + N;
+            if constexpr (sizeof(T) == 8) {
+                if (want_rz) rzs = fma((double)bv, (double)X1, rzs);
+            }
+            if (mb_out) mb_store<T>(a.mbox, p, X1, tag);
+        } else if (!in) {
+            X1 = T(0);
+        }
+        xm1 = X1;
+        if (ring_out) {
+            // back-pressure: the entry this step overwrites (step s - RING)
+            // must have been read by the warp above (at its step s - RING + 1)
+            const int old = s - RING;
+            if (old >= 0 && old + 1 > cachedC) {
+                int c = 0, okk = 1;
+                if (lane == 0) {
+                    unsigned long long t0 = 0;
+                    for (int it = 1;; ++it) {
+                        c = sh.prog[w + 1];
+                        if (c >= old + 1) break;
+                        if ((it & 31) != 0) continue;
+                        const unsigned long long now = global_ns();
+                        if (t0 == 0) t0 = now;
+                        if (ld_relaxed_gpu(&a.status->abort) || (long long)(now - t0) > a.spin_ns) {
+                            atomicCAS(&a.status->err, 0, (int)M2S_ERR_TIMEOUT);
+                            atomicExch(&a.status->abort, 1);
+                            okk = 0;
+                            break;
+                        }
+                    }
+                }
+                okk = __shfl_sync(FULL, okk, 0);
+                cachedC = __shfl_sync(FULL, c, 0);
+                if (!okk) { ok = false; return; }
+            }
+            sh.ring[w][s & (RING - 1)][lane] = Tagged<T>::pack(X1, (unsigned)(s + BIAS));
+        }
+        __syncwarp();
+        if (lane == 0) sh.prog[w] = s;
+    };
+    for (int s0 = 0; ok && s0 < S; s0 += D) {
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+            if (ok) step(s0 + k, k);
+    }
+    __syncwarp();
+    if (lane == 0) sh.prog[w] = INT_MAX;
+    if (want_rz) {
+        for (int o = 16; o > 0; o >>= 1) rzs += __shfl_down_sync(FULL, rzs, o);
+        if (lane == 0) a.rz[(i64)t * W + w] = ok ? rzs : 0.0;
+    }
+}
+
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(W * 32, 1) gs7_cta_kernel(Cta7Args<T> a) {
+    __shared__ int s_ticket;
+    __shared__ unsigned s_tag;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    Cta7Shared<T, W>& sh = *reinterpret_cast<Cta7Shared<T, W>*>(dyn_smem);
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tag = (unsigned)ld_relaxed_gpu(&a.ctrl[2]) + 1u;
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&a.ctrl[0], 1);
+        // ring tags of an earlier unit of this CTA could match a step of
+        // this unit: clear the rings
+        for (int i = threadIdx.x; i < W * RING * 32; i += blockDim.x)
+            (&sh.ring[0][0][0])[i] = Tagged<T>::zero();
+        if (threadIdx.x < W) sh.prog[threadIdx.x] = -(1 << 30);
+        __syncthreads();
+        const int t = s_ticket;
+        if (t >= a.n_units) break;
+        int ab = 0;
+        if (threadIdx.x == 0) ab = ld_relaxed_gpu(&a.status->abort) || t == a.stall_unit;
+        ab = __syncthreads_or(ab);
+        if (!ab) sweep7_warp<T, W, D>(a, t, warp, sh, s_tag);
+        __syncthreads();
+    }
+    // exit protocol: the last CTA out resets the ticket and advances the tag
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int last = atomicAdd(&a.ctrl[1], 1) == (int)gridDim.x - 1;
+        if (last) {
+            a.ctrl[0] = 0;
+            a.ctrl[1] = 0;
+            a.ctrl[2] = a.ctrl[2] + 1;
+            a.status->abort = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <typename T> struct Cta7Shape;
+template <> struct Cta7Shape<double> { static constexpr int W = 8, D = 4; };
+template <> struct Cta7Shape<float> { static constexpr int W = 8, D = 8; };
+
+template <typename T>
+size_t cta7_smem_bytes() {
+    return sizeof(Cta7Shared<T, Cta7Shape<T>::W>);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t build_cta7_units(Dims d, WaveUnits* out) {
+    constexpr int W = Cta7Shape<T>::W, D = Cta7Shape<T>::D;
+    const int NY = (d.ny + LANES7 - 1) / LANES7, NZ = (d.nz + W - 1) / W;
+    std::vector<int2> org;
+    for (int Z = 0; Z < NZ; ++Z)
+        for (int Y = 0; Y < NY; ++Y) org.push_back(make_int2(Y * LANES7, Z * W));
+    // Ticket order by the step at which a unit could start on an idle GPU:
+    // the unit to the right lags LANES7 steps, the unit above W.  Producers
+    // (left, below) have smaller keys, so the order is topological.
+    std::stable_sort(org.begin(), org.end(), [&](int2 a, int2 b) {
+        const long long ka = (long long)a.x + (long long)(a.y / W) * W;
+        const long long kb = (long long)b.x + (long long)(b.y / W) * W;
+        return ka != kb ? ka < kb : a.y < b.y;
+    });
+    WaveUnits u{};
+    u.n_units = (int)org.size();
+    u.K = 2;
+    u.W = W;
+    u.stencil = 7;
+    cudaError_t e;
+    const size_t nu = std::max<size_t>(org.size(), 1);
+    if ((e = cudaMalloc(&u.d_origin, nu * sizeof(int2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&u.d_prod, sizeof(int4))) != cudaSuccess) { free_wave_units(&u); return e; }
+    if ((e = cudaMalloc(&u.d_flags, sizeof(int))) != cudaSuccess) { free_wave_units(&u); return e; }
+    if ((e = cudaMalloc(&u.d_ctrl, 4 * sizeof(int))) != cudaSuccess) { free_wave_units(&u); return e; }
+    const size_t mb = (size_t)std::max<i64>(d.n, 1) * sizeof(T) * 2;
+    if ((e = cudaMalloc(&u.d_mbox, mb)) != cudaSuccess) { free_wave_units(&u); return e; }
+    if ((e = cudaMemset(u.d_mbox, 0, mb)) != cudaSuccess ||
+        (e = cudaMemset(u.d_ctrl, 0, 4 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemcpy(u.d_origin, org.data(), org.size() * sizeof(int2),
+                        cudaMemcpyHostToDevice)) != cudaSuccess) {
+        free_wave_units(&u);
+        return e;
+    }
+    const size_t smem = cta7_smem_bytes<T>();
+    cudaFuncSetAttribute(gs7_cta_kernel<T, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs7_cta_kernel<T, W, D>, W * 32, smem);
+    u.grid = wave_grid(u.n_units, per_sm);
+    *out = u;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gs7_cta(const WaveUnits& u, const WaveCall& c, Dims d, const KappaLevel<T>& k,
+                           const T* Qin, T* Qout, const T* b, T* x, cudaStream_t st) {
+    constexpr int W = Cta7Shape<T>::W, D = Cta7Shape<T>::D;
+    if (u.n_units == 0) return cudaSuccess;
+    Cta7Args<T> a;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.nz = d.nz;
+    a.n = d.n;
+    a.off = d.off;
+    a.rev = c.rev;
+    a.spin_ns = c.spin_ns;
+    a.Qin = Qin;
+    a.Qout = Qout;
+    a.b = b;
+    a.x = x;
+    // sweep order's lower faces: kf (forward) or the upper faces kr
+    // (backward sweep = forward sweep in reflected index space)
+    a.k0 = c.rev ? k.kr[0] : k.kf[0];
+    a.k1 = c.rev ? k.kr[1] : k.kf[1];
+    a.k2 = c.rev ? k.kr[2] : k.kf[2];
+    a.invd = k.invdiag;
+    a.origin = u.d_origin;
+    a.n_units = u.n_units;
+    a.ctrl = u.d_ctrl;
+    a.status = c.status;
+    a.rz = c.rz_partials;
+    a.stall_unit = c.stall_unit;
+    a.mbox = u.d_mbox;
+    gs7_cta_kernel<T, W, D><<<u.grid, W * 32, cta7_smem_bytes<T>(), st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t build_cta7_units<double>(Dims, WaveUnits*);
+template cudaError_t build_cta7_units<float>(Dims, WaveUnits*);
+template cudaError_t launch_gs7_cta<double>(const WaveUnits&, const WaveCall&, Dims,
+                                            const KappaLevel<double>&, const double*, double*,
+                                            const double*, double*, cudaStream_t);
+template cudaError_t launch_gs7_cta<float>(const WaveUnits&, const WaveCall&, Dims,
+                                           const KappaLevel<float>&, const float*, float*,
+                                           const float*, float*, cudaStream_t);
+
+}  // namespace m2s

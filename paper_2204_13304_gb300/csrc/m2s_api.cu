@@ -18,7 +18,6 @@ using namespace m2s;
 namespace {
 
 constexpr int kMaxLevels = 8;
-constexpr int kWaveK = 5;
 constexpr int kMaxTimed = 16384;  // recorded sweep launches per level
 
 template <typename T>
@@ -190,7 +189,8 @@ cudaError_t op_sweep(m2s_grid* g, int i, int l, int rev, const T* Qin, T* Qout, 
         const WaveUnits& u = sizeof(T) == 8 ? g->units[i][l] : g->units32[i][l];
         e = launch_gs27_cta<T>(u, c, d, Qin, Qout, b, x, st);
     } else {
-        e = launch_gs7_wave<T>(g->units[i][l], c, d, klev<T>(g, l), Qin, Qout, b, x, st);
+        const WaveUnits& u = sizeof(T) == 8 ? g->units[i][l] : g->units32[i][l];
+        e = launch_gs7_cta<T>(u, c, d, klev<T>(g, l), Qin, Qout, b, x, st);
     }
     if (e == cudaSuccess && e1) e = cudaEventRecord(e1, st);
     return e;
@@ -249,7 +249,7 @@ cudaError_t gs_sweep(m2s_grid* g, int i, int l, const T* b, T* x, int rev, cudaS
 // b.x partials written by the last sweep of a V-cycle on the finest level
 int rz_partials(m2s_grid* g, int i) {
     const WaveUnits& u = g->units[i][0];
-    return u.n_units * (g->op == M2S_OP_HPCG27 ? u.W : 1);
+    return u.n_units * u.W;
 }
 
 // (Re)build the 27-point sweep schedules of problem i on level l.
@@ -487,13 +487,17 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
             if ((e = galloc(g, &g->kappa[l], g->ltot[l])) != cudaSuccess) return fail(e);
             KappaLevel<double>& k = g->k64[l];
             for (int c = 0; c < 3; ++c)
-                if ((e = galloc(g, &k.kf[c], g->ltot[l])) != cudaSuccess) return fail(e);
+                if ((e = galloc(g, &k.kf[c], g->ltot[l])) != cudaSuccess ||
+                    (e = galloc(g, &k.kr[c], g->ltot[l])) != cudaSuccess)
+                    return fail(e);
             if ((e = galloc(g, &k.diag, g->ltot[l])) != cudaSuccess) return fail(e);
             if ((e = galloc(g, &k.invdiag, g->ltot[l])) != cudaSuccess) return fail(e);
             if (g->has32) {
                 KappaLevel<float>& k3 = g->k32[l];
                 for (int c = 0; c < 3; ++c)
-                    if ((e = galloc(g, &k3.kf[c], g->ltot[l])) != cudaSuccess) return fail(e);
+                    if ((e = galloc(g, &k3.kf[c], g->ltot[l])) != cudaSuccess ||
+                        (e = galloc(g, &k3.kr[c], g->ltot[l])) != cudaSuccess)
+                        return fail(e);
                 if ((e = galloc(g, &k3.diag, g->ltot[l])) != cudaSuccess) return fail(e);
                 if ((e = galloc(g, &k3.invdiag, g->ltot[l])) != cudaSuccess) return fail(e);
             }
@@ -527,9 +531,12 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
                 if ((e = build_level_units27(g, i, l, cta_default_warps(1, g->dims[i][l]),
                                              cta_default_warps(0, g->dims[i][l]))) != cudaSuccess)
                     return fail(e);
-            } else if ((e = build_wave_units(7, kWaveK, g->dims[i][l], &g->units[i][l])) !=
-                       cudaSuccess) {
-                return fail(e);
+            } else {
+                if ((e = build_cta7_units<double>(g->dims[i][l], &g->units[i][l])) != cudaSuccess)
+                    return fail(e);
+                if (g->has32 &&
+                    (e = build_cta7_units<float>(g->dims[i][l], &g->units32[i][l])) != cudaSuccess)
+                    return fail(e);
             }
         }
     // PCG vectors
@@ -546,7 +553,7 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
         np = std::max(np, st27_num_partials(g->dims[i][0]));
         // room for the b.x partials of any unit shape m2s_set_sweep_warps allows
         np = std::max(np, op == M2S_OP_HPCG27 ? cta_rz_partials_max(g->dims[i][0])
-                                              : g->units[i][0].n_units);
+                                              : rz_partials(g, i));
     }
     g->npart = np;
     if ((e = galloc(g, &g->part, np)) != cudaSuccess) return fail(e);

@@ -108,14 +108,17 @@ cudaError_t launch_gs27_wave(const WaveUnits& u, const WaveCall& c, Dims d,
 // the coefficient of the face between p and p - e_d (0 on the boundary).
 template <typename T>
 struct KappaLevel {
-    T* kf[3];
+    T* kf[3];  // kf[d][p]: face between p and p - e_d (0 on the boundary)
+    T* kr[3];  // kr[d][p]: face between p and p + e_d (0 on the boundary)
     T* diag;
     T* invdiag;
 };
+// 7-point CTA wavefront sweep (k_wave7.cu): units of 31 rows x W planes.
 template <typename T>
-cudaError_t launch_gs7_wave(const WaveUnits& u, const WaveCall& c, Dims d,
-                            const KappaLevel<T>& k, const T* Qin, T* Qout,
-                            const T* b, T* x, cudaStream_t st);
+cudaError_t build_cta7_units(Dims d, WaveUnits* out);
+template <typename T>
+cudaError_t launch_gs7_cta(const WaveUnits& u, const WaveCall& c, Dims d, const KappaLevel<T>& k,
+                           const T* Qin, T* Qout, const T* b, T* x, cudaStream_t st);
 
 // Variable-kappa 7-point kernels (k_kappa7.cu).
 cudaError_t launch_kappa_coarsen(Dims f, Dims c, const double* kf, double* kc,
@@ -137,7 +140,6 @@ cudaError_t launch_restrict7(Dims f, Dims c, const KappaLevel<T>& k,
                              const T* r, const T* z, T* rc, cudaStream_t st);
 cudaError_t launch_kappa_grad(Dims d, const double* u, const double* lam,
                               double* g, cudaStream_t st);
-cudaError_t build_wave_units(int stencil, int K, Dims d, WaveUnits* out);
 cudaError_t build_units(int lanes, int skew, int corner, int K, Dims d, int per_sm,
                         WaveUnits* out);
 }  // namespace m2s
