@@ -13,6 +13,7 @@
 // SpMV costs 1 multiply + 6 FMAs per point: on GB300 FP64 issue, not HBM, is
 // the scarce resource.
 #include "m2s_internal.cuh"
+#include "m2s_pcg.cuh"
 
 namespace m2s {
 
@@ -179,6 +180,88 @@ __global__ void kappa_grad_kernel(Dims d, const double* __restrict__ u,
     g[p] = -s;
 }
 
+// Batched forms: one launch for all problems of a level, one CTA per chunk
+// of one problem (see Batch).
+template <typename T>
+__global__ void __launch_bounds__(B) spmv7_b_kernel(Batch b, KappaLevel<T> k,
+                                                    const T* __restrict__ xv, T* __restrict__ yv) {
+    i64 lo, hi;
+    const Dims d = b.dims[batch_locate(b, blockIdx.x, &lo, &hi)];
+    for (i64 p = lo + threadIdx.x; p < hi; p += B) {
+        const i64 i = p - d.off;
+        int x, y, z;
+        coords(i, d.nx, d.ny, &x, &y, &z);
+        yv[p] = apply7_at(d, k, xv, i, x, y, z);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(B) qinit7_b_kernel(Batch b, Batch c, int has_c, KappaLevel<T> k,
+                                                     int up, const T* __restrict__ xv,
+                                                     const T* __restrict__ xc,
+                                                     const T* __restrict__ bv, T* __restrict__ Q) {
+    i64 lo, hi;
+    const int pb = batch_locate(b, blockIdx.x, &lo, &hi);
+    const Dims d = b.dims[pb];
+    const Dims dc = has_c ? c.dims[pb] : d;
+    const i64 sy = d.nx, sz = (i64)d.nx * d.ny;
+    for (i64 p = lo + threadIdx.x; p < hi; p += B) {
+        int x, y, z;
+        coords(p - d.off, d.nx, d.ny, &x, &y, &z);
+        T s = bv[p];
+        if (up) {
+            if (x < d.nx - 1) s = fma(k.kf[0][p + 1], prolonged(xv, xc, dc, p + 1, x + 1, y, z), s);
+            if (y < d.ny - 1) s = fma(k.kf[1][p + sy], prolonged(xv, xc, dc, p + sy, x, y + 1, z), s);
+            if (z < d.nz - 1) s = fma(k.kf[2][p + sz], prolonged(xv, xc, dc, p + sz, x, y, z + 1), s);
+        } else {
+            if (x > 0) s = fma(k.kf[0][p], prolonged(xv, xc, dc, p - 1, x - 1, y, z), s);
+            if (y > 0) s = fma(k.kf[1][p], prolonged(xv, xc, dc, p - sy, x, y - 1, z), s);
+            if (z > 0) s = fma(k.kf[2][p], prolonged(xv, xc, dc, p - sz, x, y, z - 1), s);
+        }
+        Q[p] = s;
+    }
+}
+
+// chunks of the coarse level's batch
+template <typename T>
+__global__ void __launch_bounds__(B) restrict7_b_kernel(Batch f, Batch c, KappaLevel<T> k,
+                                                        const T* __restrict__ r,
+                                                        const T* __restrict__ zv,
+                                                        T* __restrict__ rc) {
+    i64 lo, hi;
+    const int pb = batch_locate(c, blockIdx.x, &lo, &hi);
+    const Dims dc = c.dims[pb], df = f.dims[pb];
+    for (i64 p = lo + threadIdx.x; p < hi; p += B) {
+        int cx, cy, cz;
+        coords(p - dc.off, dc.nx, dc.ny, &cx, &cy, &cz);
+        const int x = 2 * cx, y = 2 * cy, z = 2 * cz;
+        const i64 fi = ((i64)z * df.ny + y) * df.nx + x;
+        rc[p] = r[df.off + fi] - apply7_at(df, k, zv, fi, x, y, z);
+    }
+}
+
+__global__ void __launch_bounds__(B) kappa_grad_b_kernel(Batch b, const double* __restrict__ u,
+                                                         const double* __restrict__ lam,
+                                                         double* __restrict__ g) {
+    i64 lo, hi;
+    const Dims d = b.dims[batch_locate(b, blockIdx.x, &lo, &hi)];
+    const i64 sy = d.nx, sz = (i64)d.nx * d.ny;
+    for (i64 p = lo + threadIdx.x; p < hi; p += B) {
+        int x, y, z;
+        coords(p - d.off, d.nx, d.ny, &x, &y, &z);
+        const double uc = u[p], lc = lam[p];
+        const double bnd = lc * uc;
+        double s = 0.0;
+        s += z > 0 ? 0.5 * (lc - lam[p - sz]) * (uc - u[p - sz]) : bnd;
+        s += y > 0 ? 0.5 * (lc - lam[p - sy]) * (uc - u[p - sy]) : bnd;
+        s += x > 0 ? 0.5 * (lc - lam[p - 1]) * (uc - u[p - 1]) : bnd;
+        s += x < d.nx - 1 ? 0.5 * (lc - lam[p + 1]) * (uc - u[p + 1]) : bnd;
+        s += y < d.ny - 1 ? 0.5 * (lc - lam[p + sy]) * (uc - u[p + sy]) : bnd;
+        s += z < d.nz - 1 ? 0.5 * (lc - lam[p + sz]) * (uc - u[p + sz]) : bnd;
+        g[p] = -s;
+    }
+}
+
 unsigned blocks_for(i64 n) { return (unsigned)((n + B - 1) / B); }
 
 }  // namespace
@@ -226,13 +309,46 @@ cudaError_t launch_kappa_grad(Dims d, const double* u, const double* lam, double
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_spmv7_b(const Batch& b, const KappaLevel<T>& k, const T* x, T* y,
+                           cudaStream_t st) {
+    spmv7_b_kernel<T><<<b.nchunks, B, 0, st>>>(b, k, x, y);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_qinit7_b(const Batch& b, const Batch* c, const KappaLevel<T>& k, int up,
+                            const T* x, const T* xc, const T* bv, T* Q, cudaStream_t st) {
+    qinit7_b_kernel<T><<<b.nchunks, B, 0, st>>>(b, c ? *c : b, c != nullptr, k, up, x, xc, bv, Q);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict7_b(const Batch& f, const Batch& c, const KappaLevel<T>& k,
+                               const T* r, const T* z, T* rc, cudaStream_t st) {
+    restrict7_b_kernel<T><<<c.nchunks, B, 0, st>>>(f, c, k, r, z, rc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kappa_grad_b(const Batch& b, const double* u, const double* lam, double* g,
+                                cudaStream_t st) {
+    kappa_grad_b_kernel<<<b.nchunks, B, 0, st>>>(b, u, lam, g);
+    return cudaGetLastError();
+}
+
 #define M2S_INST7(T)                                                                            \
     template cudaError_t launch_kappa_setup<T>(Dims, const double*, KappaLevel<T>, cudaStream_t); \
     template cudaError_t launch_spmv7<T>(Dims, const KappaLevel<T>&, const T*, T*, cudaStream_t); \
     template cudaError_t launch_qinit7<T>(Dims, Dims, const KappaLevel<T>&, int, const T*,        \
                                           const T*, const T*, T*, cudaStream_t);                  \
     template cudaError_t launch_restrict7<T>(Dims, Dims, const KappaLevel<T>&, const T*,          \
-                                             const T*, T*, cudaStream_t);
+                                             const T*, T*, cudaStream_t);                         \
+    template cudaError_t launch_spmv7_b<T>(const Batch&, const KappaLevel<T>&, const T*, T*,      \
+                                           cudaStream_t);                                         \
+    template cudaError_t launch_qinit7_b<T>(const Batch&, const Batch*, const KappaLevel<T>&, int,  \
+                                            const T*, const T*, const T*, T*, cudaStream_t);      \
+    template cudaError_t launch_restrict7_b<T>(const Batch&, const Batch&, const KappaLevel<T>&,   \
+                                               const T*, const T*, T*, cudaStream_t);
 M2S_INST7(double)
 M2S_INST7(float)
 

@@ -1,11 +1,15 @@
-// CG vector kernels (paper Sec. 6.2.1: pointwise operations are fused into
-// their neighbours so that each vector is streamed as few times as possible).
+// CG vector kernels for every problem of a grid at once (paper Sec. 6.2.1:
+// pointwise operations are fused into their neighbours so that each vector
+// is streamed as few times as possible).
 //
-// Reductions are deterministic: every kernel writes one partial per CTA with
-// a fixed thread-to-element mapping and a fixed reduction tree, and a
-// single-CTA finaliser sums the partials in a fixed order.  The CG scalars
-// (rho, alpha, beta, |r|) live in device memory, so an iteration needs no
-// host round trip and can be captured in a CUDA graph.
+// The problems' vectors are packed back to back.  A batched launch gives
+// each CTA one chunk (kChunk elements) of one problem, found from the chunk
+// prefix by binary search, so one launch serves any number of problems and
+// the partial sums of a problem form a contiguous range.  Reductions are
+// deterministic: a fixed thread-to-element mapping and reduction tree per
+// CTA, and a finaliser CTA per problem that sums its partials in a fixed
+// order.  The CG scalars live in device memory: an iteration needs no host
+// round trip and can be captured in a CUDA graph.
 #include "m2s_internal.cuh"
 #include "m2s_pcg.cuh"
 
@@ -28,25 +32,28 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(VB) dot_kernel(i64 n, const T* __restrict__ a,
-                                                 const T* __restrict__ b, double* partials) {
+__global__ void __launch_bounds__(VB) dot_b_kernel(Batch b, const T* __restrict__ x,
+                                                   const T* __restrict__ y, double* partials) {
     __shared__ double sh[VB / 32];
+    i64 lo, hi;
+    batch_locate(b, blockIdx.x, &lo, &hi);
     double s = 0.0;
-    for (i64 i = blockIdx.x * (i64)VB + threadIdx.x; i < n; i += (i64)gridDim.x * VB)
-        s = fma((double)a[i], (double)b[i], s);
+    for (i64 i = lo + threadIdx.x; i < hi; i += VB) s = fma((double)x[i], (double)y[i], s);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 // z = double(z32); partial r.z and (if zold) r.zold
-__global__ void __launch_bounds__(VB) cast_up_dots_kernel(i64 n, const float* __restrict__ z32,
-                                                          const double* __restrict__ r,
-                                                          const double* __restrict__ zold,
-                                                          double* __restrict__ z,
-                                                          double* part_rz, double* part_rzo) {
+__global__ void __launch_bounds__(VB) cast_up_dots_b_kernel(Batch b, const float* __restrict__ z32,
+                                                            const double* __restrict__ r,
+                                                            const double* __restrict__ zold,
+                                                            double* __restrict__ z,
+                                                            double* part_rz, double* part_rzo) {
     __shared__ double sh[VB / 32];
+    i64 lo, hi;
+    batch_locate(b, blockIdx.x, &lo, &hi);
     double s = 0.0, so = 0.0;
-    for (i64 i = blockIdx.x * (i64)VB + threadIdx.x; i < n; i += (i64)gridDim.x * VB) {
+    for (i64 i = lo + threadIdx.x; i < hi; i += VB) {
         const double zi = (double)z32[i];
         const double ri = r[i];
         z[i] = zi;
@@ -67,16 +74,18 @@ __global__ void __launch_bounds__(VB) cast_down_kernel(i64 n, const double* __re
         r32[i] = (float)r[i];
 }
 
-// x += alpha p; r -= alpha q; partial r.r
-__global__ void __launch_bounds__(VB) update_kernel(i64 n, const PcgDev* __restrict__ s,
-                                                    const double* __restrict__ p,
-                                                    const double* __restrict__ q,
-                                                    double* __restrict__ x,
-                                                    double* __restrict__ r, double* partials) {
+// x += alpha p; r -= alpha q (alpha of the chunk's problem); partial r.r
+__global__ void __launch_bounds__(VB) update_b_kernel(Batch b, const PcgDev* __restrict__ s,
+                                                      const double* __restrict__ p,
+                                                      const double* __restrict__ q,
+                                                      double* __restrict__ x,
+                                                      double* __restrict__ r, double* partials) {
     __shared__ double sh[VB / 32];
-    const double alpha = s->alpha;
+    i64 lo, hi;
+    const int pb = batch_locate(b, blockIdx.x, &lo, &hi);
+    const double alpha = s[pb].alpha;
     double acc = 0.0;
-    for (i64 i = blockIdx.x * (i64)VB + threadIdx.x; i < n; i += (i64)gridDim.x * VB) {
+    for (i64 i = lo + threadIdx.x; i < hi; i += VB) {
         x[i] = fma(alpha, p[i], x[i]);
         const double ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
@@ -86,10 +95,21 @@ __global__ void __launch_bounds__(VB) update_kernel(i64 n, const PcgDev* __restr
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// Single-CTA reduction of `np` partials in a fixed order.
-__device__ __forceinline__ double reduce_partials(const double* part, int np, double* sh) {
+// pout = z + beta pin (beta of the chunk's problem); pout = z when first
+__global__ void __launch_bounds__(VB) paxpy_b_kernel(Batch b, const PcgDev* __restrict__ s,
+                                                     int first, const double* __restrict__ z,
+                                                     const double* __restrict__ pin,
+                                                     double* __restrict__ pout) {
+    i64 lo, hi;
+    const int pb = batch_locate(b, blockIdx.x, &lo, &hi);
+    const double beta = first ? 0.0 : s[pb].beta;
+    for (i64 i = lo + threadIdx.x; i < hi; i += VB) pout[i] = first ? z[i] : fma(beta, pin[i], z[i]);
+}
+
+// Sum of part[lo..hi) by one CTA in a fixed order.
+__device__ __forceinline__ double reduce_range(const double* part, int lo, int hi, double* sh) {
     double s = 0.0;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) s += part[i];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) sh[w] = s;
@@ -97,27 +117,36 @@ __device__ __forceinline__ double reduce_partials(const double* part, int np, do
     double t = 0.0;
     if (threadIdx.x == 0)
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    __syncthreads();
     return t;
 }
 
-__global__ void __launch_bounds__(1024) finalize_kernel(int kind, PcgDev* s, const double* part,
-                                                        int np, const double* part2, int np2,
-                                                        double* hist) {
+__global__ void __launch_bounds__(1024) finalize_b_kernel(int kind, PcgDev* st, const double* part,
+                                                          const int* pre, const double* part2,
+                                                          const int* pre2, double* hist,
+                                                          int hist_stride, double rtol2,
+                                                          int fixed) {
     __shared__ double sh[32];
-    const double v = reduce_partials(part, np, sh);
-    __syncthreads();
+    const int pb = blockIdx.x;
+    const double v = reduce_range(part, pre[pb], pre[pb + 1], sh);
     double v2 = 0.0;
-    if (part2) v2 = reduce_partials(part2, np2, sh);
+    if (part2) v2 = reduce_range(part2, pre2[pb], pre2[pb + 1], sh);
     if (threadIdx.x != 0) return;
+    PcgDev* s = st + pb;
+    double* h = hist ? hist + (i64)pb * hist_stride : nullptr;
     switch (kind) {
         case FIN_BB:
             s->bb = v;
             s->rr = v;
             s->iter = 0;
             s->status = 0;
-            if (hist) hist[0] = sqrt(v);
+            s->done = 0;
+            s->rtol2 = rtol2;
+            s->fixed = fixed;
+            if (h) h[0] = sqrt(v);
             break;
         case FIN_RHO: {
+            if (s->done) break;
             const bool first = s->iter == 0;
             s->rho = v;
             double beta = 0.0;
@@ -127,6 +156,10 @@ __global__ void __launch_bounds__(1024) finalize_kernel(int kind, PcgDev* s, con
             break;
         }
         case FIN_PQ: {
+            if (s->done) {
+                s->alpha = 0.0;
+                break;
+            }
             s->pq = v;
             const bool bad = !(v > 0.0) || !isfinite(v) || s->status != 0;
             s->alpha = bad ? 0.0 : s->rho / v;
@@ -134,11 +167,13 @@ __global__ void __launch_bounds__(1024) finalize_kernel(int kind, PcgDev* s, con
             break;
         }
         case FIN_RR: {
+            if (s->done) break;
             s->rr = v;
             s->rho_old = s->rho;
             s->iter += 1;
-            if (hist) hist[s->iter] = sqrt(v);
+            if (h && s->iter < hist_stride) h[s->iter] = sqrt(v);
             if (!isfinite(v)) s->status = (int)M2S_ERR_BREAKDOWN;
+            if (!s->fixed && v <= s->rtol2 * s->bb) s->done = 1;
             break;
         }
         case FIN_DOT:
@@ -147,74 +182,54 @@ __global__ void __launch_bounds__(1024) finalize_kernel(int kind, PcgDev* s, con
     }
 }
 
-int grid_for(i64 n) {
-    i64 g = (n + (i64)VB * 8 - 1) / ((i64)VB * 8);
-    if (g < 1) g = 1;
-    if (g > 2048) g = 2048;
-    return (int)g;
-}
+inline unsigned grid_of(const Batch& b) { return (unsigned)(b.nchunks > 0 ? b.nchunks : 1); }
 
 }  // namespace
 
-int dot_num_partials(i64 n) { return grid_for(n); }
-
 template <typename T>
-cudaError_t launch_dot_partials(i64 n, const T* a, const T* b, double* partials, int nparts,
-                                cudaStream_t st) {
-    (void)nparts;
-    dot_kernel<T><<<grid_for(n), VB, 0, st>>>(n, a, b, partials);
+cudaError_t launch_dot_b(const Batch& b, const T* x, const T* y, double* partials,
+                         cudaStream_t st) {
+    dot_b_kernel<T><<<grid_of(b), VB, 0, st>>>(b, x, y, partials);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cast_up_dots(i64 n, const float* z32, const double* r, const double* zold,
-                                double* z, double* part_rz, double* part_rzo, cudaStream_t st) {
-    cast_up_dots_kernel<<<grid_for(n), VB, 0, st>>>(n, z32, r, zold, z, part_rz, part_rzo);
+cudaError_t launch_cast_up_dots_b(const Batch& b, const float* z32, const double* r,
+                                  const double* zold, double* z, double* part_rz,
+                                  double* part_rzo, cudaStream_t st) {
+    cast_up_dots_b_kernel<<<grid_of(b), VB, 0, st>>>(b, z32, r, zold, z, part_rz, part_rzo);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cast_down(i64 n, const double* r, float* r32, cudaStream_t st) {
-    cast_down_kernel<<<grid_for(n), VB, 0, st>>>(n, r, r32);
+    i64 g = (n + (i64)VB * 8 - 1) / ((i64)VB * 8);
+    g = g < 1 ? 1 : (g > 4096 ? 4096 : g);
+    cast_down_kernel<<<(unsigned)g, VB, 0, st>>>(n, r, r32);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(i64 n, const PcgDev* s, const double* p, const double* q, double* x,
-                          double* r, double* partials, cudaStream_t st) {
-    update_kernel<<<grid_for(n), VB, 0, st>>>(n, s, p, q, x, r, partials);
+cudaError_t launch_update_b(const Batch& b, const PcgDev* s, const double* p, const double* q,
+                            double* x, double* r, double* partials, cudaStream_t st) {
+    update_b_kernel<<<grid_of(b), VB, 0, st>>>(b, s, p, q, x, r, partials);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(int kind, PcgDev* s, const double* part, int np, const double* part2,
-                            int np2, double* hist, cudaStream_t st) {
-    finalize_kernel<<<1, 1024, 0, st>>>(kind, s, part, np, part2, np2, hist);
+cudaError_t launch_paxpy_b(const Batch& b, const PcgDev* s, int first, const double* z,
+                           const double* pin, double* pout, cudaStream_t st) {
+    paxpy_b_kernel<<<grid_of(b), VB, 0, st>>>(b, s, first, z, pin, pout);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_dot_partials<double>(i64, const double*, const double*, double*, int,
-                                                 cudaStream_t);
-template cudaError_t launch_dot_partials<float>(i64, const float*, const float*, double*, int,
-                                                cudaStream_t);
-
-}  // namespace m2s
-
-namespace m2s {
-namespace {
-// pout = z + beta * pin  (beta == NULL: pout = z)
-__global__ void __launch_bounds__(256) paxpy_kernel(i64 n, const double* __restrict__ z,
-                                                    const double* __restrict__ pin,
-                                                    double* __restrict__ pout,
-                                                    const double* __restrict__ beta) {
-    const double b = beta ? *beta : 0.0;
-    for (i64 i = blockIdx.x * (i64)256 + threadIdx.x; i < n; i += (i64)gridDim.x * 256)
-        pout[i] = beta ? fma(b, pin[i], z[i]) : z[i];
-}
-}  // namespace
-
-cudaError_t launch_paxpy(i64 n, const double* z, const double* pin, double* pout,
-                         const double* beta, cudaStream_t st) {
-    i64 g = (n + 2047) / 2048;
-    if (g < 1) g = 1;
-    if (g > 2048) g = 2048;
-    paxpy_kernel<<<(unsigned)g, 256, 0, st>>>(n, z, pin, pout, beta);
+cudaError_t launch_finalize_b(int kind, PcgDev* s, int np, const double* part, const int* pre,
+                              const double* part2, const int* pre2, double* hist,
+                              int hist_stride, double rtol2, int fixed, cudaStream_t st) {
+    finalize_b_kernel<<<np, 1024, 0, st>>>(kind, s, part, pre, part2, pre2, hist, hist_stride,
+                                           rtol2, fixed);
     return cudaGetLastError();
 }
+
+template cudaError_t launch_dot_b<double>(const Batch&, const double*, const double*, double*,
+                                          cudaStream_t);
+template cudaError_t launch_dot_b<float>(const Batch&, const float*, const float*, double*,
+                                         cudaStream_t);
+
 }  // namespace m2s

@@ -273,6 +273,9 @@ void free_wave_units(WaveUnits* u) {
     if (u->d_flags) cudaFree(u->d_flags);
     if (u->d_ctrl) cudaFree(u->d_ctrl);
     if (u->d_mbox) cudaFree(u->d_mbox);
+    if (u->d_units) cudaFree(u->d_units);
+    if (u->d_dims) cudaFree(u->d_dims);
+    if (u->d_rzpre) cudaFree(u->d_rzpre);
     *u = WaveUnits{};
 }
 

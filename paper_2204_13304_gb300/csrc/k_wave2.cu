@@ -45,21 +45,18 @@ using namespace cta;
 
 template <typename T>
 struct CtaArgs {
-    int nx, ny, nz;
-    i64 n, off;
     int rev;
     long long spin_ns;
-    const T* Qin;
+    const T* Qin;  // packed level arrays of all problems
     T* Qout;
     const T* b;
     T* x;
-    const int2* origin;  // (u0, v0) per CTA unit
-    const int4* prod;    // left, below, below-left CTA units
+    const int4* units;  // (u0, v0, problem, first b.x partial) per unit
+    const Dims* dims;   // per problem: extent and packed offset
     int n_units;
-    int* flags;          // n_units * W progress words
     int* ctrl;
     DevStatus* status;
-    double* rz;          // per-unit partials of b.x (W per unit) or NULL
+    double* rz;          // b.x partials (W per unit) or NULL
     int stall_unit;
     unsigned long long* mbox;  // tagged copies of the rows other units read
 };
@@ -78,7 +75,9 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
     typedef typename Tagged<T>::W TW;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int2 org = a.origin[t];
+    const int4 un = a.units[t];
+    const int2 org = make_int2(un.x, un.y);
+    const Dims dd = a.dims[un.z];
     const int v1 = org.y + w, v0 = v1 - 1;
     const int u = org.x - 2 + lane;
     const int tbase = 2 * (org.x - 2) + 2 * v0;
@@ -87,19 +86,21 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
     const bool ring_in = w > 0;
     const bool ring_out = w < W - 1;
     const bool mb_out = !halo && (lane >= 30 || w == W - 1);
-    const int nx = a.nx;
+    const int nx = dd.nx;
     const int y1 = u - v1, y0 = u - v0;
-    const bool rv1 = v1 < a.nz && y1 >= 0 && y1 < a.ny;
-    const bool rv0 = !ring_in && v0 >= 0 && v0 < a.nz && y0 >= 0 && y0 < a.ny;
+    const bool rv1 = v1 < dd.nz && y1 >= 0 && y1 < dd.ny;
+    const bool rv0 = !ring_in && v0 >= 0 && v0 < dd.nz && y0 >= 0 && y0 < dd.ny;
     const i64 step_dir = a.rev ? -1 : 1;
     // problem-local index of x = 0 of both rows (meaningful only if valid)
-    const i64 r1 = ((i64)v1 * a.ny + y1) * nx, r0 = ((i64)v0 * a.ny + y0) * nx;
-    const i64 L1 = a.rev ? a.n - 1 - r1 : r1;
-    const i64 L0 = a.rev ? a.n - 1 - r0 : r0;
-    const T* Qin = a.Qin + a.off;
-    const T* B = a.b + a.off;
-    T* Xo = a.x + a.off;
-    T* Qo = a.Qout ? a.Qout + a.off : nullptr;
+    const i64 r1 = ((i64)v1 * dd.ny + y1) * nx, r0 = ((i64)v0 * dd.ny + y0) * nx;
+    const i64 L1 = a.rev ? dd.n - 1 - r1 : r1;
+    const i64 L0 = a.rev ? dd.n - 1 - r0 : r0;
+    const T* Qin = a.Qin + dd.off;
+    const T* B = a.b + dd.off;
+    T* Xo = a.x + dd.off;
+    T* Qo = a.Qout ? a.Qout + dd.off : nullptr;
+    // this problem's mailbox (indexed by the problem-local point)
+    u64* const mbox = a.mbox + dd.off * (sizeof(T) == 8 ? 2 : 1);
     // the fused r.z partial is used by the FP64 PCG only; compiling it out of
     // the FP32 sweep keeps float->double conversions off the FP64 pipe
     const bool want_rz = sizeof(T) == 8 && a.rz != nullptr;
@@ -120,12 +121,12 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
                 q = __ldg(Qin + p);
                 bv = __ldg(B + p);
             } else {
-                tw_to_regs(mb_load<T>(a.mbox, p), &q, &bv);
+                tw_to_regs(mb_load<T>(mbox, p), &q, &bv);
             }
         }
         const int x0 = x1 + 2;
         if (rv0 && (unsigned)x0 < (unsigned)nx)
-            tw_to_regs(mb_load<T>(a.mbox, L0 + step_dir * x0), &m0, &m1);
+            tw_to_regs(mb_load<T>(mbox, L0 + step_dir * x0), &m0, &m1);
         rq[k] = q;
         rb[k] = bv;
         ra0[k] = m0;
@@ -180,8 +181,8 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
                 unsigned long long t0 = 0;
                 for (int it = 1;; ++it) {
                     if (!okg) okg = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin);
-                    if (!ok1) ok1 = Tagged<T>::unpack(mb_load<T>(a.mbox, L1 + step_dir * x1), tag, &X1);
-                    if (!ok0) ok0 = Tagged<T>::unpack(mb_load<T>(a.mbox, L0 + step_dir * x0), tag, &X0);
+                    if (!ok1) ok1 = Tagged<T>::unpack(mb_load<T>(mbox, L1 + step_dir * x1), tag, &X1);
+                    if (!ok0) ok0 = Tagged<T>::unpack(mb_load<T>(mbox, L0 + step_dir * x0), tag, &X0);
                     if (__all_sync(FULL, ok1 && ok0 && okg)) break;
                     if ((it & 31) == 0) {
                         const unsigned long long now = global_ns();
@@ -203,9 +204,9 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
                 for (;;) {
                     good = true;
                     if (in1 && halo)
-                        good = Tagged<T>::unpack(mb_load<T>(a.mbox, L1 + step_dir * x1), tag, &X1);
+                        good = Tagged<T>::unpack(mb_load<T>(mbox, L1 + step_dir * x1), tag, &X1);
                     if (in0)
-                        good = Tagged<T>::unpack(mb_load<T>(a.mbox, L0 + step_dir * x0), tag, &X0) && good;
+                        good = Tagged<T>::unpack(mb_load<T>(mbox, L0 + step_dir * x0), tag, &X0) && good;
                     if (need_g) good = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin) && good;
                     if (__all_sync(FULL, good)) break;
                     if (fail()) { ok = false; return; }
@@ -226,7 +227,7 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
             if constexpr (sizeof(T) == 8) {
                 if (want_rz) rz = fma((double)bv, (double)X1, rz);
             }
-            if (mb_out) mb_store<T>(a.mbox, p, X1, tag);
+            if (mb_out) mb_store<T>(mbox, p, X1, tag);
         }
         const T H = (xm2 + xm1) + X1;
         xm2 = xm1;
@@ -288,7 +289,7 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
     if (lane == 0) sh.prog[w] = INT_MAX;
     if (want_rz) {
         for (int o = 16; o > 0; o >>= 1) rz += __shfl_down_sync(FULL, rz, o);
-        if (lane == 0) a.rz[(i64)t * W + w] = ok ? rz : 0.0;
+        if (lane == 0) a.rz[(i64)un.w + w] = ok ? rz : 0.0;
     }
 }
 
@@ -369,72 +370,94 @@ int cta_default_warps(int dtype_is_f64, Dims d) {
     return 8;
 }
 
-int cta_rz_partials_max(Dims d) {
+int cta_rz_partials_max(const std::vector<Dims>& dims) {
     int m = 0;
     for (int W : {4, 8}) {
-        std::vector<int2> org;
-        std::vector<int4> prod;
-        build_units_host(30, 1, 1, W + 1, d, org, prod);
-        m = std::max(m, (int)org.size() * W);
+        int tot = 0;
+        for (const Dims& d : dims) {
+            std::vector<int2> org;
+            std::vector<int4> prod;
+            build_units_host(30, 1, 1, W + 1, d, org, prod);
+            tot += (int)org.size() * W;
+        }
+        m = std::max(m, tot);
     }
     return m;
 }
 
+// Unit table of one level for all problems of a grid (one launch per level).
+// Within a problem the units are ordered by the step at which they can start
+// on an idle GPU (the unit to the right lags 2*lanes steps, the unit above
+// 2*planes); every producer (left, below, below-left) has a smaller key, so
+// the order stays topological: a unit waits only on units with smaller
+// tickets, which have started, and the sweep cannot deadlock.  Problems are
+// independent, so their lists are merged by the same key and all problems
+// advance together.
 template <typename T>
-cudaError_t build_cta_units(Dims d, int W, WaveUnits* out) {
+cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out) {
     constexpr int K = CtaShape<T>::K;
     if (!cta_warps_supported(W)) return cudaErrorInvalidValue;
-    std::vector<int2> org0, org;
-    std::vector<int4> prod;
-    // a CTA unit is 30 rows in u and W*(K-1) planes in v
     const int lanes = 30, planes = W * (K - 1);
-    build_units_host(lanes, 1, 1, planes + 1, d, org0, prod);
-    // Ticket order: by the step at which a unit can start on an unloaded
-    // GPU (its right neighbour lags 2*lanes steps, the unit above 2*planes),
-    // ties by v.  Every producer (left, below, below-left) has a smaller
-    // key, so the order stays topological: a unit waits only on units with
-    // smaller tickets, which have started, and the sweep cannot deadlock.
-    std::vector<int> idx(org0.size());
-    for (size_t k = 0; k < idx.size(); ++k) idx[k] = (int)k;
-    auto key = [&](int k) {
-        return 2LL * lanes * (org0[k].x / lanes) + 2LL * planes * (org0[k].y / planes);
+    struct Item {
+        long long key;
+        int v0, problem, local;
+        int2 org;
     };
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
-        const long long ka = key(a), kb = key(b);
-        return ka != kb ? ka < kb : org0[a].y < org0[b].y;
+    std::vector<Item> items;
+    std::vector<int> rzpre(dims.size() + 1, 0);
+    i64 words = 0;
+    for (size_t i = 0; i < dims.size(); ++i) {
+        std::vector<int2> org;
+        std::vector<int4> prod;
+        build_units_host(lanes, 1, 1, planes + 1, dims[i], org, prod);
+        std::vector<Item> mine;
+        for (const int2& o : org)
+            mine.push_back(Item{2LL * lanes * (o.x / lanes) + 2LL * planes * (o.y / planes), o.y,
+                                (int)i, 0, o});
+        std::stable_sort(mine.begin(), mine.end(), [](const Item& a, const Item& b) {
+            return a.key != b.key ? a.key < b.key : a.v0 < b.v0;
+        });
+        for (size_t k = 0; k < mine.size(); ++k) {
+            mine[k].local = (int)k;
+            items.push_back(mine[k]);
+        }
+        rzpre[i + 1] = rzpre[i] + (int)mine.size() * W;
+        words += std::max<i64>(dims[i].n, 0) * (sizeof(T) == 8 ? 2 : 1);
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
+        if (a.key != b.key) return a.key < b.key;
+        return a.problem != b.problem ? a.problem < b.problem : a.v0 < b.v0;
     });
-    org.resize(org0.size());
-    for (size_t k = 0; k < idx.size(); ++k) org[k] = org0[idx[k]];
+    std::vector<int4> units(items.size());
+    for (size_t k = 0; k < items.size(); ++k) {
+        const Item& it = items[k];
+        units[k] = make_int4(it.org.x, it.org.y, it.problem, rzpre[it.problem] + it.local * W);
+    }
     WaveUnits u{};
-    u.n_units = (int)org.size();
+    u.n_units = (int)units.size();
     u.K = K;
     u.W = W;
     u.stencil = 27;
+    u.np = (int)dims.size();
+    u.n_rz = rzpre.back();
     cudaError_t e;
-    const size_t nu = std::max<size_t>(org.size(), 1);
-    if ((e = cudaMalloc(&u.d_origin, nu * sizeof(int2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&u.d_prod, nu * sizeof(int4))) != cudaSuccess) { free_wave_units(&u); return e; }
-    if ((e = cudaMalloc(&u.d_flags, nu * W * sizeof(int))) != cudaSuccess) { free_wave_units(&u); return e; }
-    if ((e = cudaMalloc(&u.d_ctrl, 4 * sizeof(int))) != cudaSuccess) { free_wave_units(&u); return e; }
-    // mailbox: one tagged word (FP32) or two (FP64) per point of the level
-    if ((e = cudaMalloc(&u.d_mbox, (size_t)std::max<i64>(d.n, 1) * sizeof(T) * 2)) != cudaSuccess) {
+    const size_t nu = std::max<size_t>(units.size(), 1);
+    if ((e = cudaMalloc(&u.d_units, nu * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_dims, std::max<size_t>(dims.size(), 1) * sizeof(Dims))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_rzpre, rzpre.size() * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_ctrl, 4 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_mbox, (size_t)std::max<i64>(words, 1) * sizeof(u64))) != cudaSuccess) {
         free_wave_units(&u);
         return e;
     }
-    if ((e = cudaMemset(u.d_mbox, 0, (size_t)std::max<i64>(d.n, 1) * sizeof(T) * 2)) != cudaSuccess) {
-        free_wave_units(&u);
-        return e;
-    }
-    if (!org.empty() &&
-        ((e = cudaMemcpy(u.d_origin, org.data(), org.size() * sizeof(int2), cudaMemcpyHostToDevice)) !=
-             cudaSuccess ||
-         (e = cudaMemcpy(u.d_prod, prod.data(), prod.size() * sizeof(int4), cudaMemcpyHostToDevice)) !=
-             cudaSuccess)) {
-        free_wave_units(&u);
-        return e;
-    }
-    if ((e = cudaMemset(u.d_flags, 0, nu * W * sizeof(int))) != cudaSuccess ||
-        (e = cudaMemset(u.d_ctrl, 0, 4 * sizeof(int))) != cudaSuccess) {
+    if ((!units.empty() && (e = cudaMemcpy(u.d_units, units.data(), units.size() * sizeof(int4),
+                                           cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (!dims.empty() && (e = cudaMemcpy(u.d_dims, dims.data(), dims.size() * sizeof(Dims),
+                                          cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(u.d_rzpre, rzpre.data(), rzpre.size() * sizeof(int),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(u.d_ctrl, 0, 4 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(u.d_mbox, 0, (size_t)std::max<i64>(words, 1) * sizeof(u64))) != cudaSuccess) {
         free_wave_units(&u);
         return e;
     }
@@ -445,26 +468,20 @@ cudaError_t build_cta_units(Dims d, int W, WaveUnits* out) {
 }
 
 template <typename T>
-cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, Dims d, const T* Qin, T* Qout,
+cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, const T* Qin, T* Qout,
                             const T* b, T* x, cudaStream_t st) {
     constexpr int K = CtaShape<T>::K, D = CtaShape<T>::D;
     if (u.n_units == 0) return cudaSuccess;
     CtaArgs<T> a;
-    a.nx = d.nx;
-    a.ny = d.ny;
-    a.nz = d.nz;
-    a.n = d.n;
-    a.off = d.off;
     a.rev = c.rev;
     a.spin_ns = c.spin_ns;
     a.Qin = Qin;
     a.Qout = Qout;
     a.b = b;
     a.x = x;
-    a.origin = u.d_origin;
-    a.prod = u.d_prod;
+    a.units = u.d_units;
+    a.dims = u.d_dims;
     a.n_units = u.n_units;
-    a.flags = u.d_flags;
     a.ctrl = u.d_ctrl;
     a.status = c.status;
     a.rz = c.rz_partials;
@@ -479,11 +496,11 @@ cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, Dims d, const
     return cudaGetLastError();
 }
 
-template cudaError_t build_cta_units<double>(Dims, int, WaveUnits*);
-template cudaError_t build_cta_units<float>(Dims, int, WaveUnits*);
-template cudaError_t launch_gs27_cta<double>(const WaveUnits&, const WaveCall&, Dims, const double*,
+template cudaError_t build_cta_units<double>(const std::vector<Dims>&, int, WaveUnits*);
+template cudaError_t build_cta_units<float>(const std::vector<Dims>&, int, WaveUnits*);
+template cudaError_t launch_gs27_cta<double>(const WaveUnits&, const WaveCall&, const double*,
                                              double*, const double*, double*, cudaStream_t);
-template cudaError_t launch_gs27_cta<float>(const WaveUnits&, const WaveCall&, Dims, const float*,
+template cudaError_t launch_gs27_cta<float>(const WaveUnits&, const WaveCall&, const float*,
                                             float*, const float*, float*, cudaStream_t);
 
 }  // namespace m2s

@@ -38,8 +38,6 @@ constexpr int LANES7 = 31;  // computing rows per unit
 
 template <typename T>
 struct Cta7Args {
-    int nx, ny, nz;
-    i64 n, off;
     int rev;
     long long spin_ns;
     const T* Qin;
@@ -50,7 +48,8 @@ struct Cta7Args {
     const T* k1;  // order, indexed like x (packed level arrays)
     const T* k2;
     const T* invd;
-    const int2* origin;  // (y0, z0) per unit, in ticket order
+    const int4* units;  // (y0, z0, problem, first b.x partial), ticket order
+    const Dims* dims;   // per problem: extent and packed offset
     int n_units;
     int* ctrl;
     DevStatus* status;
@@ -71,28 +70,31 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
     typedef typename Tagged<T>::W TW;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int2 org = a.origin[t];
-    const int y = org.x - 1 + lane;
-    const int z = org.y + w;
+    const int4 un = a.units[t];
+    const Dims dm = a.dims[un.z];
+    const int y = un.x - 1 + lane;
+    const int z = un.y + w;
     const bool halo = lane == 0;
-    const bool rv = y >= 0 && y < a.ny && z < a.nz;
+    const bool rv = y >= 0 && y < dm.ny && z < dm.nz;
     const bool ring_in = w > 0;
     const bool ring_out = w < W - 1;
     const bool mb_out = !halo && (lane == 31 || w == W - 1);
     const bool zmb = w == 0 && z >= 1;  // plane below from the unit underneath
-    const int nx = a.nx;
+    const int nx = dm.nx;
     const i64 dir = a.rev ? -1 : 1;
-    const i64 r = rv ? ((i64)z * a.ny + y) * nx : 0;
-    const i64 L = a.rev ? a.n - 1 - r : r;  // problem-local index of x = 0
-    const i64 szd = dir * (i64)nx * a.ny;   // index step of the z - 1 neighbour
-    const T* Q = a.Qin + a.off;
-    const T* B = a.b + a.off;
-    const T* K0 = a.k0 + a.off;
-    const T* K1 = a.k1 + a.off;
-    const T* K2 = a.k2 + a.off;
-    const T* ID = a.invd + a.off;
-    T* Xo = a.x + a.off;
-    T* Qo = a.Qout ? a.Qout + a.off : nullptr;
+    const i64 r = rv ? ((i64)z * dm.ny + y) * nx : 0;
+    const i64 L = a.rev ? dm.n - 1 - r : r;  // problem-local index of x = 0
+    const i64 szd = dir * (i64)nx * dm.ny;   // index step of the z - 1 neighbour
+    const T* Q = a.Qin + dm.off;
+    const T* B = a.b + dm.off;
+    const T* K0 = a.k0 + dm.off;
+    const T* K1 = a.k1 + dm.off;
+    const T* K2 = a.k2 + dm.off;
+    const T* ID = a.invd + dm.off;
+    T* Xo = a.x + dm.off;
+    T* Qo = a.Qout ? a.Qout + dm.off : nullptr;
+    // this problem's mailbox (indexed by the problem-local point)
+    u64* const mbox = a.mbox + dm.off * (sizeof(T) == 8 ? 2 : 1);
     const bool want_rz = sizeof(T) == 8 && a.rz != nullptr;
     const int S = nx + LANES7 + W;
 
@@ -113,9 +115,9 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
                 c1 = __ldg(K1 + p);
                 c2 = __ldg(K2 + p);
                 dd = __ldg(ID + p);
-                if (zmb) tw_to_regs(mb_load<T>(a.mbox, p - szd), &m0, &m1);
+                if (zmb) tw_to_regs(mb_load<T>(mbox, p - szd), &m0, &m1);
             } else {
-                tw_to_regs(mb_load<T>(a.mbox, p), &q, &bv);
+                tw_to_regs(mb_load<T>(mbox, p), &q, &bv);
             }
         }
         rq[k] = q;
@@ -168,8 +170,8 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
             unsigned long long t0 = 0;
             for (int it = 1;; ++it) {
                 if (!okr) okr = Tagged<T>::unpack(*(volatile const TW*)re, rtag, &zv);
-                if (!okx) okx = Tagged<T>::unpack(mb_load<T>(a.mbox, p), tag, &X1);
-                if (!okz) okz = Tagged<T>::unpack(mb_load<T>(a.mbox, p - szd), tag, &zv);
+                if (!okx) okx = Tagged<T>::unpack(mb_load<T>(mbox, p), tag, &X1);
+                if (!okz) okz = Tagged<T>::unpack(mb_load<T>(mbox, p - szd), tag, &zv);
                 if (__all_sync(FULL, okx && okz && okr)) break;
                 if ((it & 31) == 0) {
                     const unsigned long long now = global_ns();
@@ -191,7 +193,7 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
             if constexpr (sizeof(T) == 8) {
                 if (want_rz) rzs = fma((double)bv, (double)X1, rzs);
             }
-            if (mb_out) mb_store<T>(a.mbox, p, X1, tag);
+            if (mb_out) mb_store<T>(mbox, p, X1, tag);
         } else if (!in) {
             X1 = T(0);
         }
@@ -236,7 +238,7 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
     if (lane == 0) sh.prog[w] = INT_MAX;
     if (want_rz) {
         for (int o = 16; o > 0; o >>= 1) rzs += __shfl_down_sync(FULL, rzs, o);
-        if (lane == 0) a.rz[(i64)t * W + w] = ok ? rzs : 0.0;
+        if (lane == 0) a.rz[(i64)un.w + w] = ok ? rzs : 0.0;
     }
 }
 
@@ -290,38 +292,72 @@ size_t cta7_smem_bytes() {
 
 }  // namespace
 
+// Unit table of one level for all problems of a grid (one launch per level):
+// units of 31 rows x W planes, ordered within a problem by the step at which
+// they could start on an idle GPU (the unit to the right lags 31 steps, the
+// unit above W; producers, left and below, have smaller keys, so the order
+// is topological), problems merged by the same key.
 template <typename T>
-cudaError_t build_cta7_units(Dims d, WaveUnits* out) {
+cudaError_t build_cta7_units(const std::vector<Dims>& dims, WaveUnits* out) {
     constexpr int W = Cta7Shape<T>::W, D = Cta7Shape<T>::D;
-    const int NY = (d.ny + LANES7 - 1) / LANES7, NZ = (d.nz + W - 1) / W;
-    std::vector<int2> org;
-    for (int Z = 0; Z < NZ; ++Z)
-        for (int Y = 0; Y < NY; ++Y) org.push_back(make_int2(Y * LANES7, Z * W));
-    // Ticket order by the step at which a unit could start on an idle GPU:
-    // the unit to the right lags LANES7 steps, the unit above W.  Producers
-    // (left, below) have smaller keys, so the order is topological.
-    std::stable_sort(org.begin(), org.end(), [&](int2 a, int2 b) {
-        const long long ka = (long long)a.x + (long long)(a.y / W) * W;
-        const long long kb = (long long)b.x + (long long)(b.y / W) * W;
-        return ka != kb ? ka < kb : a.y < b.y;
+    struct Item {
+        long long key;
+        int z0, problem, local, y0;
+    };
+    std::vector<Item> items;
+    std::vector<int> rzpre(dims.size() + 1, 0);
+    i64 words = 0;
+    for (size_t i = 0; i < dims.size(); ++i) {
+        const Dims& d = dims[i];
+        const int NY = (d.ny + LANES7 - 1) / LANES7, NZ = (d.nz + W - 1) / W;
+        std::vector<Item> mine;
+        for (int Z = 0; Z < NZ; ++Z)
+            for (int Y = 0; Y < NY; ++Y)
+                mine.push_back(Item{(long long)Y * LANES7 + (long long)Z * W, Z * W, (int)i, 0,
+                                    Y * LANES7});
+        std::stable_sort(mine.begin(), mine.end(), [](const Item& a, const Item& b) {
+            return a.key != b.key ? a.key < b.key : a.z0 < b.z0;
+        });
+        for (size_t k = 0; k < mine.size(); ++k) {
+            mine[k].local = (int)k;
+            items.push_back(mine[k]);
+        }
+        rzpre[i + 1] = rzpre[i] + (int)mine.size() * W;
+        words += std::max<i64>(d.n, 0) * (sizeof(T) == 8 ? 2 : 1);
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
+        if (a.key != b.key) return a.key < b.key;
+        return a.problem != b.problem ? a.problem < b.problem : a.z0 < b.z0;
     });
+    std::vector<int4> units(items.size());
+    for (size_t k = 0; k < items.size(); ++k)
+        units[k] = make_int4(items[k].y0, items[k].z0, items[k].problem,
+                             rzpre[items[k].problem] + items[k].local * W);
     WaveUnits u{};
-    u.n_units = (int)org.size();
+    u.n_units = (int)units.size();
     u.K = 2;
     u.W = W;
     u.stencil = 7;
+    u.np = (int)dims.size();
+    u.n_rz = rzpre.back();
     cudaError_t e;
-    const size_t nu = std::max<size_t>(org.size(), 1);
-    if ((e = cudaMalloc(&u.d_origin, nu * sizeof(int2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&u.d_prod, sizeof(int4))) != cudaSuccess) { free_wave_units(&u); return e; }
-    if ((e = cudaMalloc(&u.d_flags, sizeof(int))) != cudaSuccess) { free_wave_units(&u); return e; }
-    if ((e = cudaMalloc(&u.d_ctrl, 4 * sizeof(int))) != cudaSuccess) { free_wave_units(&u); return e; }
-    const size_t mb = (size_t)std::max<i64>(d.n, 1) * sizeof(T) * 2;
-    if ((e = cudaMalloc(&u.d_mbox, mb)) != cudaSuccess) { free_wave_units(&u); return e; }
-    if ((e = cudaMemset(u.d_mbox, 0, mb)) != cudaSuccess ||
+    const size_t nu = std::max<size_t>(units.size(), 1);
+    if ((e = cudaMalloc(&u.d_units, nu * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_dims, std::max<size_t>(dims.size(), 1) * sizeof(Dims))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_rzpre, rzpre.size() * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_ctrl, 4 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_mbox, (size_t)std::max<i64>(words, 1) * sizeof(u64))) != cudaSuccess) {
+        free_wave_units(&u);
+        return e;
+    }
+    if ((!units.empty() && (e = cudaMemcpy(u.d_units, units.data(), units.size() * sizeof(int4),
+                                           cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (!dims.empty() && (e = cudaMemcpy(u.d_dims, dims.data(), dims.size() * sizeof(Dims),
+                                          cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(u.d_rzpre, rzpre.data(), rzpre.size() * sizeof(int),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(u.d_ctrl, 0, 4 * sizeof(int))) != cudaSuccess ||
-        (e = cudaMemcpy(u.d_origin, org.data(), org.size() * sizeof(int2),
-                        cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (e = cudaMemset(u.d_mbox, 0, (size_t)std::max<i64>(words, 1) * sizeof(u64))) != cudaSuccess) {
         free_wave_units(&u);
         return e;
     }
@@ -336,16 +372,11 @@ cudaError_t build_cta7_units(Dims d, WaveUnits* out) {
 }
 
 template <typename T>
-cudaError_t launch_gs7_cta(const WaveUnits& u, const WaveCall& c, Dims d, const KappaLevel<T>& k,
+cudaError_t launch_gs7_cta(const WaveUnits& u, const WaveCall& c, const KappaLevel<T>& k,
                            const T* Qin, T* Qout, const T* b, T* x, cudaStream_t st) {
     constexpr int W = Cta7Shape<T>::W, D = Cta7Shape<T>::D;
     if (u.n_units == 0) return cudaSuccess;
     Cta7Args<T> a;
-    a.nx = d.nx;
-    a.ny = d.ny;
-    a.nz = d.nz;
-    a.n = d.n;
-    a.off = d.off;
     a.rev = c.rev;
     a.spin_ns = c.spin_ns;
     a.Qin = Qin;
@@ -358,7 +389,8 @@ cudaError_t launch_gs7_cta(const WaveUnits& u, const WaveCall& c, Dims d, const 
     a.k1 = c.rev ? k.kr[1] : k.kf[1];
     a.k2 = c.rev ? k.kr[2] : k.kf[2];
     a.invd = k.invdiag;
-    a.origin = u.d_origin;
+    a.units = u.d_units;
+    a.dims = u.d_dims;
     a.n_units = u.n_units;
     a.ctrl = u.d_ctrl;
     a.status = c.status;
@@ -369,12 +401,12 @@ cudaError_t launch_gs7_cta(const WaveUnits& u, const WaveCall& c, Dims d, const 
     return cudaGetLastError();
 }
 
-template cudaError_t build_cta7_units<double>(Dims, WaveUnits*);
-template cudaError_t build_cta7_units<float>(Dims, WaveUnits*);
-template cudaError_t launch_gs7_cta<double>(const WaveUnits&, const WaveCall&, Dims,
+template cudaError_t build_cta7_units<double>(const std::vector<Dims>&, WaveUnits*);
+template cudaError_t build_cta7_units<float>(const std::vector<Dims>&, WaveUnits*);
+template cudaError_t launch_gs7_cta<double>(const WaveUnits&, const WaveCall&,
                                             const KappaLevel<double>&, const double*, double*,
                                             const double*, double*, cudaStream_t);
-template cudaError_t launch_gs7_cta<float>(const WaveUnits&, const WaveCall&, Dims,
+template cudaError_t launch_gs7_cta<float>(const WaveUnits&, const WaveCall&,
                                            const KappaLevel<float>&, const float*, float*,
                                            const float*, float*, cudaStream_t);
 

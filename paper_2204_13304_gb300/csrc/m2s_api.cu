@@ -39,9 +39,15 @@ struct m2s_grid {
     std::vector<double*> kappa;
     std::vector<KappaLevel<double>> k64;
     std::vector<KappaLevel<float>> k32;
-    // sweep schedules per problem and level (27-point: one set per dtype)
-    std::vector<std::vector<WaveUnits>> units;
-    std::vector<std::vector<WaveUnits>> units32;
+    // sweep schedules per level, all problems in one launch (one set per dtype)
+    std::vector<WaveUnits> units;
+    std::vector<WaveUnits> units32;
+    // batched element kernels: per level the problems' dims and chunk prefix
+    std::vector<Batch> batch;
+    // prefix (np + 1) of the per-problem partials of the fused p-update +
+    // SpMV + p.Ap of the 27-point operator (one launch per problem)
+    int* d_st27pre = nullptr;
+    std::vector<int> h_st27pre;
     Work<double> w64;
     Work<float> w32;
     // PCG state (finest level, packed)
@@ -49,8 +55,9 @@ struct m2s_grid {
     float *r32 = nullptr, *z32 = nullptr;
     double *part = nullptr, *part2 = nullptr;
     int npart = 0;
-    PcgDev* dev = nullptr;
-    double* hist = nullptr;
+    PcgDev* dev = nullptr;   // one per problem
+    double* x_cur = nullptr;  // solution vector of the solve in progress
+    double* hist = nullptr;  // per problem: hist_cap + 1 residual norms
     int hist_cap = 0;
     DevStatus* status = nullptr;
     long long spin_ns = 4000000000LL;
@@ -96,10 +103,8 @@ cudaError_t galloc(m2s_grid* g, T** p, i64 count) {
 void destroy_grid(m2s_grid* g) {
     if (!g) return;
     cudaDeviceSynchronize();
-    for (auto& pl : g->units)
-        for (auto& u : pl) free_wave_units(&u);
-    for (auto& pl : g->units32)
-        for (auto& u : pl) free_wave_units(&u);
+    for (auto& u : g->units) free_wave_units(&u);
+    for (auto& u : g->units32) free_wave_units(&u);
     for (void* p : g->allocs) cudaFree(p);
     for (auto& t : g->tim)
         for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
@@ -127,6 +132,34 @@ WaveCall wave_call(m2s_grid* g, int rev, double* rz) {
     return c;
 }
 
+// Dims of every problem on level l.
+std::vector<Dims> level_dims(m2s_grid* g, int l) {
+    std::vector<Dims> v(g->np);
+    for (int i = 0; i < g->np; ++i) v[i] = g->dims[i][l];
+    return v;
+}
+
+// (Re)build the 27-point sweep schedules of level l (both dtypes).
+cudaError_t build_level_units27(m2s_grid* g, int l, int w64, int w32) {
+    WaveUnits a{}, b{};
+    const std::vector<Dims> dl = level_dims(g, l);
+    cudaError_t e = build_cta_units<double>(dl, w64, &a);
+    if (e != cudaSuccess) {
+        free_wave_units(&a);
+        return e;
+    }
+    if ((e = build_cta_units<float>(dl, w32, &b)) != cudaSuccess) {
+        free_wave_units(&a);
+        free_wave_units(&b);
+        return e;
+    }
+    free_wave_units(&g->units[l]);
+    free_wave_units(&g->units32[l]);
+    g->units[l] = a;
+    g->units32[l] = b;
+    return cudaSuccess;
+}
+
 Dims coarse_of(m2s_grid* g, int i, int l) {
     return (l + 1 < g->levels) ? g->dims[i][l + 1]
                                : Dims{(g->dims[i][l].nx + 1) / 2, (g->dims[i][l].ny + 1) / 2,
@@ -134,31 +167,44 @@ Dims coarse_of(m2s_grid* g, int i, int l) {
 }
 
 // ---------------------------------------------------------------------------
-// Operator-generic building blocks for problem i on level l.
+// Operator-generic building blocks on level l, for all problems of the grid:
+// the sweeps and the variable-kappa kernels are one launch each; the 27-point
+// tile kernels are launched once per problem.
 // ---------------------------------------------------------------------------
 template <typename T>
-cudaError_t op_spmv(m2s_grid* g, int i, int l, const T* x, T* y, cudaStream_t st) {
-    const Dims d = g->dims[i][l];
-    if (g->op == M2S_OP_HPCG27) return launch_st27<T>(ST27_SPMV, d, d, x, nullptr, nullptr, y, st);
-    return launch_spmv7<T>(d, klev<T>(g, l), x, y, st);
+cudaError_t op_spmv(m2s_grid* g, int l, const T* x, T* y, cudaStream_t st) {
+    if (g->op == M2S_OP_HPCG27) {
+        for (int i = 0; i < g->np; ++i) {
+            const Dims d = g->dims[i][l];
+            cudaError_t e = launch_st27<T>(ST27_SPMV, d, d, x, nullptr, nullptr, y, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    return launch_spmv7_b<T>(g->batch[l], klev<T>(g, l), x, y, st);
 }
 
 // Q = b + sum of the upper (up) or lower neighbours of (x + P xc).
 template <typename T>
-cudaError_t op_qinit(m2s_grid* g, int i, int l, int up, const T* x, const T* xc, const T* b, T* Q,
+cudaError_t op_qinit(m2s_grid* g, int l, int up, const T* x, const T* xc, const T* b, T* Q,
                      cudaStream_t st) {
-    const Dims d = g->dims[i][l];
     if (g->op == M2S_OP_HPCG27) {
-        if (xc) return launch_st27<T>(ST27_PROLONG_QUP, d, coarse_of(g, i, l), x, xc, b, Q, st);
-        return launch_st27<T>(up ? ST27_QUP : ST27_QLO, d, d, x, nullptr, b, Q, st);
+        for (int i = 0; i < g->np; ++i) {
+            const Dims d = g->dims[i][l];
+            cudaError_t e =
+                xc ? launch_st27<T>(ST27_PROLONG_QUP, d, coarse_of(g, i, l), x, xc, b, Q, st)
+                   : launch_st27<T>(up ? ST27_QUP : ST27_QLO, d, d, x, nullptr, b, Q, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
-    return launch_qinit7<T>(d, xc ? coarse_of(g, i, l) : d, klev<T>(g, l), up, x, xc, b, Q, st);
+    return launch_qinit7_b<T>(g->batch[l], xc ? &g->batch[l + 1] : nullptr, klev<T>(g, l), up, x,
+                              xc, b, Q, st);
 }
 
 template <typename T>
-cudaError_t op_sweep(m2s_grid* g, int i, int l, int rev, const T* Qin, T* Qout, const T* b, T* x,
+cudaError_t op_sweep(m2s_grid* g, int l, int rev, const T* Qin, T* Qout, const T* b, T* x,
                      double* rz, cudaStream_t st) {
-    const Dims d = g->dims[i][l];
     WaveCall c = wave_call(g, rev, rz);
     if (g->stall_level == l && g->stall_unit >= 0) {
         c.stall_unit = g->stall_unit;
@@ -184,92 +230,66 @@ cudaError_t op_sweep(m2s_grid* g, int i, int l, int rev, const T* Qin, T* Qout, 
             if (er != cudaSuccess) return er;
         }
     }
-    cudaError_t e;
-    if (g->op == M2S_OP_HPCG27) {
-        const WaveUnits& u = sizeof(T) == 8 ? g->units[i][l] : g->units32[i][l];
-        e = launch_gs27_cta<T>(u, c, d, Qin, Qout, b, x, st);
-    } else {
-        const WaveUnits& u = sizeof(T) == 8 ? g->units[i][l] : g->units32[i][l];
-        e = launch_gs7_cta<T>(u, c, d, klev<T>(g, l), Qin, Qout, b, x, st);
-    }
+    const WaveUnits& u = sizeof(T) == 8 ? g->units[l] : g->units32[l];
+    cudaError_t e = g->op == M2S_OP_HPCG27
+                        ? launch_gs27_cta<T>(u, c, Qin, Qout, b, x, st)
+                        : launch_gs7_cta<T>(u, c, klev<T>(g, l), Qin, Qout, b, x, st);
     if (e == cudaSuccess && e1) e = cudaEventRecord(e1, st);
     return e;
 }
 
 template <typename T>
-cudaError_t op_restrict(m2s_grid* g, int i, int l, const T* r, const T* z, T* rc, cudaStream_t st) {
-    const Dims f = g->dims[i][l], c = g->dims[i][l + 1];
-    if (g->op == M2S_OP_HPCG27) return launch_restrict27<T>(f, c, r, z, rc, st);
-    return launch_restrict7<T>(f, c, klev<T>(g, l), r, z, rc, st);
+cudaError_t op_restrict(m2s_grid* g, int l, const T* r, const T* z, T* rc, cudaStream_t st) {
+    if (g->op == M2S_OP_HPCG27) {
+        for (int i = 0; i < g->np; ++i) {
+            cudaError_t e = launch_restrict27<T>(g->dims[i][l], g->dims[i][l + 1], r, z, rc, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    return launch_restrict7_b<T>(g->batch[l], g->batch[l + 1], klev<T>(g, l), r, z, rc, st);
 }
 
-// V-cycle of problem i from level l: z = M_l^-1 r (r, z packed level-l
-// arrays).  rz (optional) receives the per-unit partials of r.z from the
-// last sweep of the finest level.
+// V-cycle from level l for all problems: z = M_l^-1 r (packed level-l
+// arrays).  rz (optional) receives the b.x partials of the last sweep of the
+// finest level, W per sweep unit.
 template <typename T>
-cudaError_t vcycle(m2s_grid* g, int i, int l, const T* r, T* z, double* rz, cudaStream_t st) {
+cudaError_t vcycle(m2s_grid* g, int l, const T* r, T* z, double* rz, cudaStream_t st) {
     Work<T>& w = work<T>(g);
     T* Qa = w.Qa[l];
     T* Qb = w.Qb[l];
     cudaError_t e;
     // pre-smoothing from z = 0: the old-neighbour sum is r itself
-    if ((e = op_sweep<T>(g, i, l, 0, r, Qb, r, z, nullptr, st)) != cudaSuccess) return e;
-    if (l == g->levels - 1)
-        return op_sweep<T>(g, i, l, 1, Qb, nullptr, r, z, rz, st);
-    if ((e = op_sweep<T>(g, i, l, 1, Qb, nullptr, r, z, nullptr, st)) != cudaSuccess) return e;
-    if ((e = op_restrict<T>(g, i, l, r, z, w.rc[l + 1], st)) != cudaSuccess) return e;
-    if ((e = vcycle<T>(g, i, l + 1, w.rc[l + 1], w.zc[l + 1], nullptr, st)) != cudaSuccess) return e;
+    if ((e = op_sweep<T>(g, l, 0, r, Qb, r, z, nullptr, st)) != cudaSuccess) return e;
+    if (l == g->levels - 1) return op_sweep<T>(g, l, 1, Qb, nullptr, r, z, rz, st);
+    if ((e = op_sweep<T>(g, l, 1, Qb, nullptr, r, z, nullptr, st)) != cudaSuccess) return e;
+    if ((e = op_restrict<T>(g, l, r, z, w.rc[l + 1], st)) != cudaSuccess) return e;
+    if ((e = vcycle<T>(g, l + 1, w.rc[l + 1], w.zc[l + 1], nullptr, st)) != cudaSuccess) return e;
     // prolongation fused into the old-neighbour sum of the post-smoothing
-    if ((e = op_qinit<T>(g, i, l, 1, z, w.zc[l + 1], r, Qa, st)) != cudaSuccess) return e;
-    if ((e = op_sweep<T>(g, i, l, 0, Qa, Qb, r, z, nullptr, st)) != cudaSuccess) return e;
-    return op_sweep<T>(g, i, l, 1, Qb, nullptr, r, z, rz, st);
+    if ((e = op_qinit<T>(g, l, 1, z, w.zc[l + 1], r, Qa, st)) != cudaSuccess) return e;
+    if ((e = op_sweep<T>(g, l, 0, Qa, Qb, r, z, nullptr, st)) != cudaSuccess) return e;
+    return op_sweep<T>(g, l, 1, Qb, nullptr, r, z, rz, st);
 }
 
 template <typename T>
-cudaError_t symgs(m2s_grid* g, int i, int l, const T* b, T* x, int sweeps, cudaStream_t st) {
+cudaError_t symgs(m2s_grid* g, int l, const T* b, T* x, int sweeps, cudaStream_t st) {
     Work<T>& w = work<T>(g);
     cudaError_t e;
-    if ((e = op_qinit<T>(g, i, l, 1, x, nullptr, b, w.Qa[l], st)) != cudaSuccess) return e;
+    if ((e = op_qinit<T>(g, l, 1, x, nullptr, b, w.Qa[l], st)) != cudaSuccess) return e;
     for (int s = 0; s < sweeps; ++s) {
-        if ((e = op_sweep<T>(g, i, l, 0, w.Qa[l], w.Qb[l], b, x, nullptr, st)) != cudaSuccess) return e;
+        if ((e = op_sweep<T>(g, l, 0, w.Qa[l], w.Qb[l], b, x, nullptr, st)) != cudaSuccess) return e;
         T* qn = (s + 1 < sweeps) ? w.Qa[l] : nullptr;
-        if ((e = op_sweep<T>(g, i, l, 1, w.Qb[l], qn, b, x, nullptr, st)) != cudaSuccess) return e;
+        if ((e = op_sweep<T>(g, l, 1, w.Qb[l], qn, b, x, nullptr, st)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t gs_sweep(m2s_grid* g, int i, int l, const T* b, T* x, int rev, cudaStream_t st) {
+cudaError_t gs_sweep(m2s_grid* g, int l, const T* b, T* x, int rev, cudaStream_t st) {
     Work<T>& w = work<T>(g);
     cudaError_t e;
-    if ((e = op_qinit<T>(g, i, l, rev ? 0 : 1, x, nullptr, b, w.Qa[l], st)) != cudaSuccess) return e;
-    return op_sweep<T>(g, i, l, rev, w.Qa[l], nullptr, b, x, nullptr, st);
-}
-
-// b.x partials written by the last sweep of a V-cycle on the finest level
-int rz_partials(m2s_grid* g, int i) {
-    const WaveUnits& u = g->units[i][0];
-    return u.n_units * u.W;
-}
-
-// (Re)build the 27-point sweep schedules of problem i on level l.
-cudaError_t build_level_units27(m2s_grid* g, int i, int l, int w64, int w32) {
-    WaveUnits a{}, b{};
-    cudaError_t e = build_cta_units<double>(g->dims[i][l], w64, &a);
-    if (e != cudaSuccess) {
-        free_wave_units(&a);
-        return e;
-    }
-    if ((e = build_cta_units<float>(g->dims[i][l], w32, &b)) != cudaSuccess) {
-        free_wave_units(&a);
-        free_wave_units(&b);
-        return e;
-    }
-    free_wave_units(&g->units[i][l]);
-    free_wave_units(&g->units32[i][l]);
-    g->units[i][l] = a;
-    g->units32[i][l] = b;
-    return cudaSuccess;
+    if ((e = op_qinit<T>(g, l, rev ? 0 : 1, x, nullptr, b, w.Qa[l], st)) != cudaSuccess) return e;
+    return op_sweep<T>(g, l, rev, w.Qa[l], nullptr, b, x, nullptr, st);
 }
 
 bool valid_level(m2s_grid* g, int level) { return g && level >= 0 && level < g->levels; }
@@ -283,70 +303,92 @@ m2s_status check_dtype(m2s_grid* g, m2s_dtype dt) {
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 // ---------------------------------------------------------------------------
-// PCG for problem i (finest level): x0 = 0, r0 = b.
+// PCG for all problems of the grid at once (finest level, packed): x0 = 0,
+// r0 = b, per-problem scalars; a problem that reaches its tolerance is
+// frozen on the device while the others iterate.
 // ---------------------------------------------------------------------------
-m2s_status pcg_problem(m2s_grid* g, int i, const double* b, double* x, const m2s_pcg_opts& o,
-                       m2s_pcg_result* out, cudaStream_t st) {
-    const Dims d = g->dims[i][0];
-    const i64 n = d.n, off = d.off;
-    double* r = g->r + off;
-    double* z = g->z + off;
-    double* zold = g->zold + off;
-    double* q = g->q + off;
-    const bool f32 = g->pdtype == M2S_F32;
-    const int nd = dot_num_partials(n);
-    const int nst = g->op == M2S_OP_HPCG27 ? st27_num_partials(d) : nd;
-    const int nu = rz_partials(g, i);
+cudaError_t pcg_iteration(m2s_grid* g, int k, cudaStream_t st) {
+    const Batch& b0 = g->batch[0];
+    const int np = g->np;
+    const i64 n = g->ltot[0];
+    const int stride = g->hist_cap + 1;
+    cudaError_t e;
+    // z = M^-1 r and rho = r.z
+    if (g->pdtype == M2S_F32) {
+        if ((e = launch_cast_down(n, g->r, g->r32, st)) != cudaSuccess) return e;
+        if ((e = vcycle<float>(g, 0, g->r32, g->z32, nullptr, st)) != cudaSuccess) return e;
+        double* zo = (k > 1) ? g->zold : nullptr;
+        if ((e = launch_cast_up_dots_b(b0, g->z32, g->r, zo, g->z, g->part, g->part2, st)) !=
+            cudaSuccess)
+            return e;
+        if ((e = launch_finalize_b(FIN_RHO, g->dev, np, g->part, b0.cstart, zo ? g->part2 : nullptr,
+                                   b0.cstart, nullptr, stride, 0.0, 0, st)) != cudaSuccess)
+            return e;
+    } else {
+        if ((e = vcycle<double>(g, 0, g->r, g->z, g->part, st)) != cudaSuccess) return e;
+        if ((e = launch_finalize_b(FIN_RHO, g->dev, np, g->part, g->units[0].d_rzpre, nullptr,
+                                   nullptr, nullptr, stride, 0.0, 0, st)) != cudaSuccess)
+            return e;
+    }
+    // p = z + beta p; q = A p; p.q   (p ping-pongs between p0 and p1)
+    double* pin = (k & 1) ? g->p1 : g->p0;
+    double* pout = (k & 1) ? g->p0 : g->p1;
+    if (g->op == M2S_OP_HPCG27) {
+        for (int i = 0; i < np; ++i) {
+            const double* beta = (k == 1) ? nullptr : &g->dev[i].beta;
+            if ((e = launch_pspmv_dot(g->dims[i][0], g->z, pin, pout, g->q, beta,
+                                      g->part + g->h_st27pre[i], st)) != cudaSuccess)
+                return e;
+        }
+        if ((e = launch_finalize_b(FIN_PQ, g->dev, np, g->part, g->d_st27pre, nullptr, nullptr,
+                                   nullptr, stride, 0.0, 0, st)) != cudaSuccess)
+            return e;
+    } else {
+        if ((e = launch_paxpy_b(b0, g->dev, k == 1, g->z, pin, pout, st)) != cudaSuccess) return e;
+        if ((e = op_spmv<double>(g, 0, pout, g->q, st)) != cudaSuccess) return e;
+        if ((e = launch_dot_b<double>(b0, pout, g->q, g->part, st)) != cudaSuccess) return e;
+        if ((e = launch_finalize_b(FIN_PQ, g->dev, np, g->part, b0.cstart, nullptr, nullptr,
+                                   nullptr, stride, 0.0, 0, st)) != cudaSuccess)
+            return e;
+    }
+    if ((e = launch_update_b(b0, g->dev, pout, g->q, g->x_cur, g->r, g->part, st)) != cudaSuccess)
+        return e;
+    if ((e = launch_finalize_b(FIN_RR, g->dev, np, g->part, b0.cstart, nullptr, nullptr, g->hist,
+                               stride, 0.0, 0, st)) != cudaSuccess)
+        return e;
+    if (g->pdtype == M2S_F32) std::swap(g->z, g->zold);
+    return cudaSuccess;
+}
 
-    M2S_TRY(cudaMemsetAsync(x + off, 0, n * sizeof(double), st));
-    M2S_TRY(cudaMemcpyAsync(r, b + off, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    M2S_TRY(launch_dot_partials<double>(n, r, r, g->part, nd, st));
-    M2S_TRY(launch_finalize(FIN_BB, g->dev, g->part, nd, nullptr, 0, g->hist, st));
-    PcgDev h{};
-    int k = 0;
-    for (k = 1; k <= o.max_iters; ++k) {
-        // z = M^-1 r and rho = r.z
-        if (g->levels <= 0) {
-            M2S_TRY(cudaMemcpyAsync(z, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            M2S_TRY(launch_dot_partials<double>(n, r, z, g->part, nd, st));
-            M2S_TRY(launch_finalize(FIN_RHO, g->dev, g->part, nd, nullptr, 0, nullptr, st));
-        } else if (f32) {
-            M2S_TRY(launch_cast_down(n, r, g->r32 + off, st));
-            M2S_TRY(vcycle<float>(g, i, 0, g->r32, g->z32, nullptr, st));
-            double* zo = (k > 1) ? zold : nullptr;
-            M2S_TRY(launch_cast_up_dots(n, g->z32 + off, r, zo, z, g->part, g->part2, st));
-            M2S_TRY(launch_finalize(FIN_RHO, g->dev, g->part, nd, zo ? g->part2 : nullptr, nd,
-                                    nullptr, st));
-        } else {
-            M2S_TRY(vcycle<double>(g, i, 0, g->r, g->z, g->part, st));
-            M2S_TRY(launch_finalize(FIN_RHO, g->dev, g->part, nu, nullptr, 0, nullptr, st));
-        }
-        // p = z + beta p; q = A p; p.q   (p ping-pongs between p0 and p1)
-        double* pin_b = (k & 1) ? g->p1 : g->p0;
-        double* pout_b = (k & 1) ? g->p0 : g->p1;
-        double* pout = pout_b + off;
-        const double* beta = (k == 1) ? nullptr : &g->dev->beta;
-        if (g->op == M2S_OP_HPCG27) {
-            M2S_TRY(launch_pspmv_dot(d, g->z, pin_b, pout_b, g->q, beta, g->part, st));
-            M2S_TRY(launch_finalize(FIN_PQ, g->dev, g->part, nst, nullptr, 0, nullptr, st));
-        } else {
-            M2S_TRY(launch_paxpy(n, z, pin_b + off, pout, beta, st));
-            M2S_TRY(op_spmv<double>(g, i, 0, pout_b, g->q, st));
-            M2S_TRY(launch_dot_partials<double>(n, pout, q, g->part, nd, st));
-            M2S_TRY(launch_finalize(FIN_PQ, g->dev, g->part, nd, nullptr, 0, nullptr, st));
-        }
-        M2S_TRY(launch_update(n, g->dev, pout, q, x + off, r, g->part, st));
-        M2S_TRY(launch_finalize(FIN_RR, g->dev, g->part, nd, nullptr, 0, g->hist, st));
-        if (f32) std::swap(g->z, g->zold), z = g->z + off, zold = g->zold + off;
+m2s_status pcg_batch(m2s_grid* g, const double* b, double* x, const m2s_pcg_opts& o,
+                     m2s_pcg_result* out, cudaStream_t st) {
+    const Batch& b0 = g->batch[0];
+    const int np = g->np;
+    const i64 n = g->ltot[0];
+    const int stride = g->hist_cap + 1;
+    g->x_cur = x;
+    M2S_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+    M2S_TRY(cudaMemcpyAsync(g->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    M2S_TRY(launch_dot_b<double>(b0, g->r, g->r, g->part, st));
+    M2S_TRY(launch_finalize_b(FIN_BB, g->dev, np, g->part, b0.cstart, nullptr, nullptr, g->hist,
+                              stride, o.rtol * o.rtol, o.fixed_iters ? 1 : 0, st));
+    std::vector<PcgDev> h(np);
+    for (int k = 1; k <= o.max_iters; ++k) {
+        M2S_TRY(pcg_iteration(g, k, st));
         const bool last = k == o.max_iters;
         if (!o.fixed_iters && (k % o.check_every == 0 || last)) {
-            M2S_TRY(cudaMemcpyAsync(&h, g->dev, sizeof(PcgDev), cudaMemcpyDeviceToHost, st));
+            M2S_TRY(cudaMemcpyAsync(h.data(), g->dev, np * sizeof(PcgDev), cudaMemcpyDeviceToHost,
+                                    st));
             M2S_TRY(cudaStreamSynchronize(st));
-            if (h.status != 0) break;
-            if (h.rr <= o.rtol * o.rtol * h.bb) break;
+            bool all_done = true, bad = false;
+            for (const PcgDev& s : h) {
+                all_done = all_done && s.done;
+                bad = bad || s.status != 0;
+            }
+            if (all_done || bad) break;
         }
     }
-    M2S_TRY(cudaMemcpyAsync(&h, g->dev, sizeof(PcgDev), cudaMemcpyDeviceToHost, st));
+    M2S_TRY(cudaMemcpyAsync(h.data(), g->dev, np * sizeof(PcgDev), cudaMemcpyDeviceToHost, st));
     M2S_TRY(cudaStreamSynchronize(st));
     DevStatus ds;
     M2S_TRY(cudaMemcpy(&ds, g->status, sizeof(DevStatus), cudaMemcpyDeviceToHost));
@@ -354,13 +396,23 @@ m2s_status pcg_problem(m2s_grid* g, int i, const double* b, double* x, const m2s
         cudaMemset(g->status, 0, sizeof(DevStatus));
         return (m2s_status)ds.err;
     }
+    bool bad = false, all_done = true;
     if (out) {
-        out->iters = h.iter;
-        out->resid_hist_last = std::sqrt(h.rr);
-        out->rel_resid = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+        out->iters = 0;
+        out->rel_resid = 0.0;
+        out->resid_hist_last = 0.0;
     }
-    if (h.status != 0) return M2S_ERR_BREAKDOWN;
-    if (!o.fixed_iters && !(h.rr <= o.rtol * o.rtol * h.bb) && h.bb > 0) return M2S_ERR_NOT_CONVERGED;
+    for (const PcgDev& s : h) {
+        bad = bad || s.status != 0;
+        all_done = all_done && (s.done || !(s.bb > 0));
+        if (out) {
+            out->iters = std::max(out->iters, s.iter);
+            out->resid_hist_last = std::max(out->resid_hist_last, std::sqrt(s.rr));
+            out->rel_resid = std::max(out->rel_resid, s.bb > 0 ? std::sqrt(s.rr / s.bb) : 0.0);
+        }
+    }
+    if (bad) return M2S_ERR_BREAKDOWN;
+    if (!o.fixed_iters && !all_done) return M2S_ERR_NOT_CONVERGED;
     return M2S_OK;
 }
 
@@ -441,8 +493,9 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     cudaError_t e = cudaSuccess;
     if ((e = galloc(g, &g->status, 1)) != cudaSuccess) return fail(e);
     if ((e = cudaMemsetAsync(g->status, 0, sizeof(DevStatus), st)) != cudaSuccess) return fail(e);
-    if ((e = galloc(g, &g->dev, 1)) != cudaSuccess) return fail(e);
-    if ((e = cudaMemsetAsync(g->dev, 0, sizeof(PcgDev), st)) != cudaSuccess) return fail(e);
+    if ((e = galloc(g, &g->dev, n_problems)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(g->dev, 0, n_problems * sizeof(PcgDev), st)) != cudaSuccess)
+        return fail(e);
 
     if (op == M2S_OP_BLOCK7_5x5) {
         e = block_create(&g->blk, descs, n_problems, g->dims, st,
@@ -522,23 +575,40 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
             }
         }
     }
-    // sweep schedules
-    g->units.assign(n_problems, std::vector<WaveUnits>(L));
-    g->units32.assign(n_problems, std::vector<WaveUnits>(L));
-    for (int i = 0; i < n_problems; ++i)
-        for (int l = 0; l < L; ++l) {
-            if (op == M2S_OP_HPCG27) {
-                if ((e = build_level_units27(g, i, l, cta_default_warps(1, g->dims[i][l]),
-                                             cta_default_warps(0, g->dims[i][l]))) != cudaSuccess)
-                    return fail(e);
-            } else {
-                if ((e = build_cta7_units<double>(g->dims[i][l], &g->units[i][l])) != cudaSuccess)
-                    return fail(e);
-                if (g->has32 &&
-                    (e = build_cta7_units<float>(g->dims[i][l], &g->units32[i][l])) != cudaSuccess)
-                    return fail(e);
-            }
+    // batched element kernels: per level the problems' dims and chunk prefix
+    g->batch.assign(L, Batch{});
+    for (int l = 0; l < L; ++l) {
+        std::vector<Dims> dl = level_dims(g, l);
+        std::vector<int> cs(n_problems + 1, 0);
+        for (int i = 0; i < n_problems; ++i)
+            cs[i + 1] = cs[i] + (int)((dl[i].n + kChunk - 1) / kChunk);
+        Dims* dd = nullptr;
+        int* dc = nullptr;
+        if ((e = galloc(g, &dd, n_problems)) != cudaSuccess ||
+            (e = galloc(g, &dc, n_problems + 1)) != cudaSuccess ||
+            (e = cudaMemcpy(dd, dl.data(), n_problems * sizeof(Dims), cudaMemcpyHostToDevice)) !=
+                cudaSuccess ||
+            (e = cudaMemcpy(dc, cs.data(), (n_problems + 1) * sizeof(int),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e);
+        g->batch[l] = Batch{n_problems, dd, dc, cs.back()};
+    }
+    // sweep schedules, one unit table per level and dtype for all problems
+    g->units.assign(L, WaveUnits{});
+    g->units32.assign(L, WaveUnits{});
+    for (int l = 0; l < L; ++l) {
+        if (op == M2S_OP_HPCG27) {
+            if ((e = build_level_units27(g, l, cta_default_warps(1, g->dims[0][l]),
+                                         cta_default_warps(0, g->dims[0][l]))) != cudaSuccess)
+                return fail(e);
+        } else {
+            if ((e = build_cta7_units<double>(level_dims(g, l), &g->units[l])) != cudaSuccess)
+                return fail(e);
+            if (g->has32 &&
+                (e = build_cta7_units<float>(level_dims(g, l), &g->units32[l])) != cudaSuccess)
+                return fail(e);
         }
+    }
     // PCG vectors
     const i64 n0 = g->ltot[0];
     for (double** p : {&g->r, &g->z, &g->zold, &g->p0, &g->p1, &g->q})
@@ -547,19 +617,24 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
         if ((e = galloc(g, &g->r32, n0)) != cudaSuccess) return fail(e);
         if ((e = galloc(g, &g->z32, n0)) != cudaSuccess) return fail(e);
     }
-    int np = 0;
-    for (int i = 0; i < n_problems; ++i) {
-        np = std::max(np, dot_num_partials(g->dims[i][0].n));
-        np = std::max(np, st27_num_partials(g->dims[i][0]));
-        // room for the b.x partials of any unit shape m2s_set_sweep_warps allows
-        np = std::max(np, op == M2S_OP_HPCG27 ? cta_rz_partials_max(g->dims[i][0])
-                                              : rz_partials(g, i));
-    }
+    // partial sums: chunks of the finest level, the 27-point fused SpMV's
+    // tiles of every problem, or the b.x partials of any sweep schedule
+    g->h_st27pre.assign(n_problems + 1, 0);
+    for (int i = 0; i < n_problems; ++i)
+        g->h_st27pre[i + 1] = g->h_st27pre[i] + st27_num_partials(g->dims[i][0]);
+    if ((e = galloc(g, &g->d_st27pre, n_problems + 1)) != cudaSuccess ||
+        (e = cudaMemcpy(g->d_st27pre, g->h_st27pre.data(), (n_problems + 1) * sizeof(int),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+    int np = std::max(g->batch[0].nchunks, g->h_st27pre.back());
+    np = std::max(np, op == M2S_OP_HPCG27 ? cta_rz_partials_max(level_dims(g, 0))
+                                          : g->units[0].n_rz);
     g->npart = np;
     if ((e = galloc(g, &g->part, np)) != cudaSuccess) return fail(e);
     if ((e = galloc(g, &g->part2, np)) != cudaSuccess) return fail(e);
     g->hist_cap = 4096;
-    if ((e = galloc(g, &g->hist, g->hist_cap + 1)) != cudaSuccess) return fail(e);
+    if ((e = galloc(g, &g->hist, (i64)(g->hist_cap + 1) * n_problems)) != cudaSuccess)
+        return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
     *out = g;
     return M2S_OK;
@@ -609,9 +684,7 @@ m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps) {
     M2S_TRY(cudaDeviceSynchronize());
     for (int l = 0; l < grid->levels; ++l) {
         if (level >= 0 && l != level) continue;
-        for (int i = 0; i < grid->np; ++i) {
-            M2S_TRY(build_level_units27(grid, i, l, warps, warps));
-        }
+        M2S_TRY(build_level_units27(grid, l, warps, warps));
     }
     return M2S_OK;
 }
@@ -646,10 +719,8 @@ m2s_status m2s_spmv(m2s_grid* g, int level, m2s_dtype dtype, const void* x, void
         return cuda_status(block_apply(&g->blk, (const double*)x, (double*)y, S(stream)));
     }
     if (check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
-    for (int i = 0; i < g->np; ++i) {
-        if (dtype == M2S_F64) M2S_TRY(op_spmv<double>(g, i, level, (const double*)x, (double*)y, S(stream)));
-        else M2S_TRY(op_spmv<float>(g, i, level, (const float*)x, (float*)y, S(stream)));
-    }
+    if (dtype == M2S_F64) M2S_TRY(op_spmv<double>(g, level, (const double*)x, (double*)y, S(stream)));
+    else M2S_TRY(op_spmv<float>(g, level, (const float*)x, (float*)y, S(stream)));
     return M2S_OK;
 }
 
@@ -658,12 +729,10 @@ m2s_status m2s_symgs(m2s_grid* g, int level, m2s_dtype dtype, const void* b, voi
     if (!valid_level(g, level) || !b || !x || b == x || n_sym_sweeps < 0) return M2S_ERR_INVALID_ARG;
     if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
     if (n_sym_sweeps == 0) return M2S_OK;
-    for (int i = 0; i < g->np; ++i) {
-        if (dtype == M2S_F64)
-            M2S_TRY(symgs<double>(g, i, level, (const double*)b, (double*)x, n_sym_sweeps, S(stream)));
-        else
-            M2S_TRY(symgs<float>(g, i, level, (const float*)b, (float*)x, n_sym_sweeps, S(stream)));
-    }
+    if (dtype == M2S_F64)
+        M2S_TRY(symgs<double>(g, level, (const double*)b, (double*)x, n_sym_sweeps, S(stream)));
+    else
+        M2S_TRY(symgs<float>(g, level, (const float*)b, (float*)x, n_sym_sweeps, S(stream)));
     return M2S_OK;
 }
 
@@ -673,12 +742,10 @@ m2s_status m2s_gs_sweep(m2s_grid* g, int level, m2s_dtype dtype, const void* b, 
     if (direction != M2S_FORWARD && direction != M2S_BACKWARD) return M2S_ERR_INVALID_ARG;
     if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
     const int rev = direction == M2S_BACKWARD;
-    for (int i = 0; i < g->np; ++i) {
-        if (dtype == M2S_F64)
-            M2S_TRY(gs_sweep<double>(g, i, level, (const double*)b, (double*)x, rev, S(stream)));
-        else
-            M2S_TRY(gs_sweep<float>(g, i, level, (const float*)b, (float*)x, rev, S(stream)));
-    }
+    if (dtype == M2S_F64)
+        M2S_TRY(gs_sweep<double>(g, level, (const double*)b, (double*)x, rev, S(stream)));
+    else
+        M2S_TRY(gs_sweep<float>(g, level, (const float*)b, (float*)x, rev, S(stream)));
     return M2S_OK;
 }
 
@@ -686,12 +753,12 @@ m2s_status m2s_mg_restrict(m2s_grid* g, int level, m2s_dtype dtype, const void* 
                            void* rc, void* stream) {
     if (!g || level < 0 || level + 1 >= g->levels || !r || !z || !rc) return M2S_ERR_INVALID_ARG;
     if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
-    for (int i = 0; i < g->np; ++i) {
-        if (dtype == M2S_F64)
-            M2S_TRY(op_restrict<double>(g, i, level, (const double*)r, (const double*)z, (double*)rc, S(stream)));
-        else
-            M2S_TRY(op_restrict<float>(g, i, level, (const float*)r, (const float*)z, (float*)rc, S(stream)));
-    }
+    if (dtype == M2S_F64)
+        M2S_TRY(op_restrict<double>(g, level, (const double*)r, (const double*)z, (double*)rc,
+                                    S(stream)));
+    else
+        M2S_TRY(op_restrict<float>(g, level, (const float*)r, (const float*)z, (float*)rc,
+                                   S(stream)));
     return M2S_OK;
 }
 
@@ -710,12 +777,10 @@ m2s_status m2s_mg_prolong(m2s_grid* g, int level, m2s_dtype dtype, const void* z
 m2s_status m2s_mg_vcycle(m2s_grid* g, m2s_dtype dtype, const void* r, void* z, void* stream) {
     if (!g || !r || !z || r == z) return M2S_ERR_INVALID_ARG;
     if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
-    for (int i = 0; i < g->np; ++i) {
-        if (dtype == M2S_F64)
-            M2S_TRY(vcycle<double>(g, i, 0, (const double*)r, (double*)z, nullptr, S(stream)));
-        else
-            M2S_TRY(vcycle<float>(g, i, 0, (const float*)r, (float*)z, nullptr, S(stream)));
-    }
+    if (dtype == M2S_F64)
+        M2S_TRY(vcycle<double>(g, 0, (const double*)r, (double*)z, nullptr, S(stream)));
+    else
+        M2S_TRY(vcycle<float>(g, 0, (const float*)r, (float*)z, nullptr, S(stream)));
     return M2S_OK;
 }
 
@@ -726,27 +791,13 @@ m2s_status m2s_pcg_solve(m2s_grid* g, const double* b, double* x, const m2s_pcg_
     m2s_pcg_opts o = *opts;
     if (o.max_iters < 1 || o.max_iters > g->hist_cap || !(o.rtol >= 0)) return M2S_ERR_INVALID_ARG;
     if (o.check_every < 1) o.check_every = 1;
-    m2s_status worst = M2S_OK;
-    m2s_pcg_result agg{};
-    agg.rel_resid = 0;
-    for (int i = 0; i < g->np; ++i) {
-        m2s_pcg_result res{};
-        m2s_status s = pcg_problem(g, i, b, x, o, &res, S(stream));
-        if (s != M2S_OK && worst == M2S_OK) worst = s;
-        if (s == M2S_ERR_TIMEOUT || s == M2S_ERR_CUDA || s == M2S_ERR_OOM) return s;
-        agg.iters = std::max(agg.iters, res.iters);
-        agg.rel_resid = std::max(agg.rel_resid, res.rel_resid);
-        agg.resid_hist_last = std::max(agg.resid_hist_last, res.resid_hist_last);
-    }
-    if (out) *out = agg;
-    return worst;
+    return pcg_batch(g, b, x, o, out, S(stream));
 }
 
 m2s_status m2s_kappa_grad(m2s_grid* g, const double* u, const double* lambda, double* dLdkappa,
                           void* stream) {
     if (!g || !u || !lambda || !dLdkappa || g->op != M2S_OP_DIFF7_KAPPA) return M2S_ERR_INVALID_ARG;
-    for (int i = 0; i < g->np; ++i)
-        M2S_TRY(launch_kappa_grad(g->dims[i][0], u, lambda, dLdkappa, S(stream)));
+    M2S_TRY(launch_kappa_grad_b(g->batch[0], u, lambda, dLdkappa, S(stream)));
     return M2S_OK;
 }
 

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "m2s.h"
 
 namespace m2s {
@@ -89,6 +91,14 @@ struct WaveUnits {
     int K;            // slots per lane (incl. the halo slot)
     int stencil;      // 27 or 7
     int W = 1;        // CTA kernel: compute warps (planes) per unit
+    // CTA kernels, all problems of a level in one launch: per unit (u0, v0,
+    // problem, first b.x partial), per problem its dims and the prefix of
+    // its b.x partials (np + 1 entries)
+    int4* d_units = nullptr;
+    Dims* d_dims = nullptr;
+    int* d_rzpre = nullptr;
+    int np = 0;
+    int n_rz = 0;     // b.x partials of one launch (units x W)
 };
 struct WaveCall {
     int rev;              // 0 forward, 1 backward (reflected index space)
@@ -115,9 +125,9 @@ struct KappaLevel {
 };
 // 7-point CTA wavefront sweep (k_wave7.cu): units of 31 rows x W planes.
 template <typename T>
-cudaError_t build_cta7_units(Dims d, WaveUnits* out);
+cudaError_t build_cta7_units(const std::vector<Dims>& dims, WaveUnits* out);
 template <typename T>
-cudaError_t launch_gs7_cta(const WaveUnits& u, const WaveCall& c, Dims d, const KappaLevel<T>& k,
+cudaError_t launch_gs7_cta(const WaveUnits& u, const WaveCall& c, const KappaLevel<T>& k,
                            const T* Qin, T* Qout, const T* b, T* x, cudaStream_t st);
 
 // Variable-kappa 7-point kernels (k_kappa7.cu).
@@ -142,9 +152,6 @@ cudaError_t launch_kappa_grad(Dims d, const double* u, const double* lam,
                               double* g, cudaStream_t st);
 cudaError_t build_units(int lanes, int skew, int corner, int K, Dims d, int per_sm,
                         WaveUnits* out);
-}  // namespace m2s
-#include <vector>
-namespace m2s {
 void build_units_host(int lanes, int skew, int corner, int K, Dims d, std::vector<int2>& org,
                       std::vector<int4>& prod);
 int wave_grid(int n_units, int per_sm);
@@ -152,19 +159,15 @@ int wave_blocks_per_sm(int stencil);
 constexpr int kWaveSlots = 5;  // register slots per lane of the sweep kernels
 // CTA-pipelined 27-point sweep (k_wave2.cu)
 template <typename T>
-cudaError_t build_cta_units(Dims d, int warps, WaveUnits* out);
+cudaError_t build_cta_units(const std::vector<Dims>& dims, int warps, WaveUnits* out);
 bool cta_warps_supported(int warps);
 int cta_default_warps(int dtype_is_f64, Dims d);
-int cta_rz_partials_max(Dims d);  // b.x partials of the largest schedule
+// b.x partials of the largest schedule of these problems
+int cta_rz_partials_max(const std::vector<Dims>& dims);
 template <typename T>
-cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, Dims d, const T* Qin, T* Qout,
+cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, const T* Qin, T* Qout,
                             const T* b, T* x, cudaStream_t st);
 void free_wave_units(WaveUnits* u);
 
-// Vector kernels (k_vec.cu).
-template <typename T>
-cudaError_t launch_dot_partials(i64 n, const T* a, const T* b, double* partials,
-                                int nparts, cudaStream_t st);
-int dot_num_partials(i64 n);
 
 }  // namespace m2s

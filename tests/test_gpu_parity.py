@@ -526,3 +526,69 @@ def test_mg_pcg_full_size_matches_oracle_history(m, n):
     assert abs(res.resid_hist_last - hist[-1]) <= 1e-6 * hist[-1]
     assert float((x - 1.0).abs().max()) < 1e-8
     g.close()
+
+
+def test_batched_problems_converge_separately(m):
+    """Form 2: one handle, problems of different sizes solved to 1e-10 in one
+    batched PCG; each problem freezes where its own solve stops, so each
+    matches the oracle's solve of that problem alone."""
+    import torch
+    shapes = [(12, 12, 12), (20, 20, 20), (16, 16, 16), (9, 9, 9)]
+    kaps = [gen.kappa_field(s[0], seed=40 + i) for i, s in enumerate(shapes)]
+    descs = [dict(nx=s[2], ny=s[1], nz=s[0], op=m.Op.DIFF7_KAPPA, mg_levels=2, kappa=dev(k))
+             for s, k in zip(shapes, kaps)]
+    g = m.Grid(descs)
+    bs = [rnd(s, 60 + i) for i, s in enumerate(shapes)]
+    b = dev(np.concatenate([x.ravel() for x in bs]))
+    x = torch.empty_like(b)
+    st, res = m.m2s_pcg_solve(g.handle, b, x, max_iters=300, rtol=1e-10, fixed_iters=False)
+    assert st == m.Status.OK
+    xh = host(x)
+    off, its = 0, []
+    for s, k, bb in zip(shapes, kaps, bs):
+        n = int(np.prod(s))
+        ox, oit, _, ost = oracle.pcg(K7, bb, 2, k, max_iters=300, rtol=1e-10, fixed_iters=False)
+        its.append(oit)
+        assert ost == 0
+        assert np.max(np.abs(xh[off:off + n].reshape(s) - ox)) <= 1e-9 * np.max(np.abs(ox))
+        off += n
+    assert len(set(its)) > 1 and res.iters == max(its)
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_batched_hpcg27_sweeps_and_pcg(m, f32):
+    """Form 2 with the 27-point operator: uneven shapes in one handle; one
+    sweep launch per level serves all problems."""
+    import torch
+    shapes = [(7, 17, 5), (17, 33, 32), (5, 3, 4)]
+    dt = torch.float32 if f32 else torch.float64
+    descs = [dict(nx=s[2], ny=s[1], nz=s[0], op=m.Op.HPCG27, mg_levels=2) for s in shapes]
+    g = m.Grid(descs)
+    bs = [rnd(s, 70 + i) for i, s in enumerate(shapes)]
+    xs = [rnd(s, 80 + i) for i, s in enumerate(shapes)]
+    b = dev(np.concatenate([v.ravel() for v in bs]), dt)
+    x = dev(np.concatenate([v.ravel() for v in xs]), dt)
+    m.m2s_symgs(g.handle, 0, b, x, 2)
+    xh = host(x)
+    off = 0
+    for s, bb, x0 in zip(shapes, bs, xs):
+        n = int(np.prod(s))
+        if f32:
+            assert err32(xh[off:off + n].reshape(s), oracle.symgs_f32(H27, bb, x0, 2)) <= TOL32
+        else:
+            assert err64(xh[off:off + n].reshape(s), oracle.symgs(H27, bb, x0, 2)) <= TOL64
+        off += n
+    if f32:
+        return
+    bh = [oracle.apply(H27, np.ones(s)) for s in shapes]
+    bd = dev(np.concatenate([v.ravel() for v in bh]))
+    xx = torch.empty_like(bd)
+    st, res = m.m2s_pcg_solve(g.handle, bd, xx, max_iters=10, fixed_iters=True)
+    assert st == m.Status.OK and res.iters == 10
+    xh = host(xx)
+    off = 0
+    for s, bb in zip(shapes, bh):
+        n = int(np.prod(s))
+        ox, _, _, _ = oracle.pcg(H27, bb, 2, max_iters=10, fixed_iters=True)
+        assert err(xh[off:off + n].reshape(s), ox) <= TOL64
+        off += n
