@@ -218,6 +218,162 @@ def profile_case(args):
     return 0
 
 
+def time_cuda(torch, fn, reps=1, warm=1):
+    """Mean device time of fn() in seconds (CUDA events on the current stream)."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    c.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(c) / 1e3 / reps
+
+
+def other_configs(m, torch, hbm):
+    """The other workload configurations of the hot path, measured in the same
+    run (synthetic seeded inputs, m2s_inputs): 32^3 SGS-PCG, NPB-LU-shaped
+    162^3 x 5 block SSOR, 256^3 variable-kappa MG-PCG in FP64 and with the
+    FP32 preconditioner, and 64 batched variable-kappa problems with the
+    adjoint."""
+    import numpy as np
+    import m2s_inputs as gen
+    out = {}
+
+    def guarded(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as e:  # report, keep the bench line
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        torch.cuda.synchronize()
+
+    def cfg1():
+        n = 32
+        shape = (n, n, n)
+        g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.HPCG27, mg_levels=1)])
+        ones = torch.ones(shape, dtype=torch.float64, device="cuda")
+        b = torch.empty_like(ones)
+        m.m2s_spmv(g.handle, 0, ones, b)
+        x = torch.zeros_like(ones)
+        t_spmv = time_cuda(torch, lambda: m.m2s_spmv(g.handle, 0, ones, b), 20, 3)
+        t_sgs = time_cuda(torch, lambda: m.m2s_symgs(g.handle, 0, b, x, 1), 20, 3)
+        xx = torch.empty_like(ones)
+        res = [None]
+
+        def pcg():
+            res[0] = m.m2s_pcg_solve(g.handle, b, xx, max_iters=50, fixed_iters=True)[1]
+
+        t_pcg = time_cuda(torch, pcg, 3, 1)
+        g.close()
+        return {"workload": "HPCG 27-point 32^3, b = A*ones: one SpMV, one symmetric GS, "
+                            "50 SGS-PCG iterations (FP64)",
+                "spmv_us": t_spmv * 1e6, "symgs_us": t_sgs * 1e6, "sgs_pcg_50_ms": t_pcg * 1e3,
+                "rel_resid_50": res[0].rel_resid, "bound": "latency (working set in L2)"}
+
+    def cfg4():
+        n = 256
+        shape = (n, n, n)
+        kap = torch.from_numpy(gen.kappa_field(n)).cuda()
+        r = {"workload": "variable-kappa 7-point 256^3 (log kappa ~ N(0,1) smoothed, sigma 4), "
+                         "b = A*ones, MG-PCG (4 levels) to 1e-10"}
+        xs = {}
+        for name, pdt in (("fp64", m.DType.F64), ("fp32_precond", m.DType.F32)):
+            g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.DIFF7_KAPPA, mg_levels=4, kappa=kap,
+                             precond_dtype=pdt)])
+            ones = torch.ones(shape, dtype=torch.float64, device="cuda")
+            b = torch.empty_like(ones)
+            m.m2s_spmv(g.handle, 0, ones, b)
+            x = torch.empty_like(ones)
+            res = [None]
+
+            def solve():
+                res[0] = m.m2s_pcg_solve(g.handle, b, x, max_iters=1000, rtol=1e-10,
+                                         fixed_iters=False)[1]
+
+            t = time_cuda(torch, solve, 1, 1)
+            m.m2s_sweep_timing(g.handle, True)
+            solve()
+            k, ms, _ = m.m2s_sweep_timing_read(g.handle, 0)
+            m.m2s_sweep_timing(g.handle, False)
+            xs[name] = x.clone()
+            r[name] = {"s": t, "iters": res[0].iters, "rel_resid": res[0].rel_resid,
+                       "sweep_ms_256": ms / max(1, k),
+                       "max_err_vs_ones": float((x - 1.0).abs().max())}
+            g.close()
+        r["fp32_precond"]["rel_err_vs_fp64_solution"] = float(
+            (xs["fp32_precond"] - xs["fp64"]).abs().max() / xs["fp64"].abs().max())
+        r["fp32_precond"]["speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_precond"]["s"]
+        return r
+
+    def cfg3():
+        n = 162
+        D, L, U, rhs = gen.block_ssor_inputs(n)
+        dd, ld, ud = [torch.from_numpy(a).cuda() for a in (D, L, U)]
+        del D, L, U
+        g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.BLOCK7_5x5, mg_levels=1, D=dd, L=ld, U=ud)])
+        del dd, ld, ud
+        b = torch.from_numpy(rhs).cuda()
+        u = torch.zeros_like(b)
+        m.m2s_ssor_sweep(g.handle, b, u, 1.2, 1)
+        u.zero_()
+        t = time_cuda(torch, lambda: m.m2s_ssor_sweep(g.handle, b, u, 1.2, 50), 1, 0)
+        y = torch.empty_like(b)
+        m.m2s_spmv(g.handle, 0, u, y)
+        rel = float((b - y).norm() / b.norm())
+        pts = n ** 3
+        it = t / 50
+        g.close()
+        return {"workload": "NPB-LU-shaped block SSOR 162^3 x 5 unknowns, omega 1.2, "
+                            "50 iterations from u = 0 (FP64)",
+                "s_50_iters": t, "ms_per_iter": it * 1e3,
+                "alg_GBs": 2440.0 * pts / it / 1e9, "hbm_frac": 2440.0 * pts / it / 1e9 / hbm,
+                "alg_bytes_note": "2.44 KB/point/iteration: the fused floor (residual into the "
+                                  "lower sweep, update into the upper)",
+                "rel_resid_after_50": rel}
+
+    def cfg5():
+        sides = gen.batch_sides(64)
+        kaps = [torch.from_numpy(gen.kappa_field(s_, seed=gen.BASE_SEED + i)).cuda()
+                for i, s_ in enumerate(sides)]
+        descs = [dict(nx=s_, ny=s_, nz=s_, op=m.Op.DIFF7_KAPPA, mg_levels=3, kappa=k)
+                 for s_, k in zip(sides, kaps)]
+        g = m.Grid(descs)
+        ntot = sum(s_ ** 3 for s_ in sides)
+        b = torch.ones(ntot, dtype=torch.float64, device="cuda")
+        u = torch.empty_like(b)
+        tgt = torch.from_numpy(np.concatenate(
+            [gen.target((s_, s_, s_), seed=gen.BASE_SEED + i).ravel()
+             for i, s_ in enumerate(sides)])).cuda()
+        lam = torch.empty_like(b)
+        gk = torch.empty_like(b)
+        res = [None, None]
+
+        def fwd():
+            res[0] = m.m2s_pcg_solve(g.handle, b, u, max_iters=1000, rtol=1e-10,
+                                     fixed_iters=False)[1]
+
+        def adj():
+            res[1] = m.m2s_adjoint_solve(g.handle, u, u - tgt, lam, gk, max_iters=1000,
+                                         rtol=1e-10)[1]
+
+        tf = time_cuda(torch, fwd, 1, 1)
+        ta = time_cuda(torch, adj, 1, 1)
+        g.close()
+        return {"workload": "64 variable-kappa problems, cube sides from {32,48,64,96,128} by "
+                            "seed (%d points), b = 1, MG-PCG (3 levels) to 1e-10, then the "
+                            "adjoint solve and dL/dkappa, u_target ~ U(0,1)" % ntot,
+                "forward_s": tf, "adjoint_s": ta, "iters_max_forward": res[0].iters,
+                "iters_max_adjoint": res[1].iters}
+
+    guarded("hpcg_32", cfg1)
+    guarded("kappa_256", cfg4)
+    guarded("block_ssor_162x5", cfg3)
+    guarded("batched_adjoint_64", cfg5)
+    return out
+
+
 def run_reference(args):
     """--impl reference: the serial CPU oracle on the same problem, bounded."""
     ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
@@ -268,6 +424,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workload configurations (32^3 SGS-PCG, block SSOR, "
+                         "variable-kappa, batched adjoint)")
     ap.add_argument("--profile-case", choices=["sweep64", "sweep32", "spmv64", "spmv32"],
                     help="run a few launches of one kernel for an ncu capture and exit")
     args = ap.parse_args()
@@ -414,6 +573,8 @@ def main():
         e2e = {"value": te, "unit": "s", "h2d_bytes_per_step": rows * 8,
                "d2h_bytes_per_step": rows * 8}
 
+    configs = None if args.no_configs else other_configs(m, torch, hbm)
+
     value = max_over_ranks(ws, t64) / ws
     launches = launches_per_solve(res64.iters)
     line = {
@@ -429,6 +590,7 @@ def main():
         "kernels": kern, "sweep_share_of_solve": sweep_share,
         "sweep_ms_per_launch_by_level": [v[1] / max(1, v[0]) for v in sweep_lv],
         "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps,
+        "other_configs": configs,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -242,6 +242,18 @@ m2s_status m2s_symgs_noalloc(int nx, int ny, int nz, m2s_dtype dtype,
  * range), M2S_ERR_CUDA / M2S_ERR_OOM from the reallocation. */
 m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps);
 
+/* CUDA-graph replay of the PCG iteration (default on).  From the second
+ * iteration on, m2s_pcg_solve records one iteration of each parity (the
+ * search-direction buffers alternate) into a CUDA graph on the caller's
+ * stream and replays it, so an iteration costs one graph launch instead of
+ * one launch per kernel.  The graphs are kept for the solution pointer of
+ * the solve that captured them and rebuilt when it changes; they are not
+ * used while per-launch sweep timing is on.  Results are identical with and
+ * without graphs (the same kernels run in the same order).  enable = 0
+ * releases the graphs and launches every kernel.  Errors:
+ * M2S_ERR_INVALID_ARG for a NULL grid. */
+m2s_status m2s_set_graphs(m2s_grid* grid, int enable);
+
 /* Per-launch timing of the Gauss-Seidel sweeps (instrumentation; the
  * paper has no counterpart).  enable = 1 clears the counters and, from the
  * next sweep on, brackets every sweep kernel the grid launches (any entry

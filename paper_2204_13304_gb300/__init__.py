@@ -72,7 +72,7 @@ EXPORTS = (
     "m2s_symgs", "m2s_gs_sweep", "m2s_mg_restrict", "m2s_mg_prolong", "m2s_mg_vcycle",
     "m2s_pcg_solve", "m2s_ssor_sweep", "m2s_adjoint_solve", "m2s_kappa_grad",
     "m2s_set_spin_limit", "m2s_debug_stall_unit", "m2s_symgs_noalloc", "m2s_status_string",
-    "m2s_sweep_timing", "m2s_sweep_timing_read", "m2s_set_sweep_warps",
+    "m2s_sweep_timing", "m2s_sweep_timing_read", "m2s_set_sweep_warps", "m2s_set_graphs",
 )
 
 
@@ -113,6 +113,7 @@ def load():
         "m2s_status_string": ([i], ctypes.c_char_p),
         "m2s_sweep_timing": ([vp, i], i),
         "m2s_set_sweep_warps": ([vp, i, i], i),
+        "m2s_set_graphs": ([vp, i], i),
         "m2s_sweep_timing_read": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(d),
                                    ctypes.POINTER(i)], i),
     }
@@ -214,6 +215,11 @@ def m2s_debug_stall_unit(grid, level, unit):
 def m2s_set_sweep_warps(grid, level, warps):
     """Warps (4 or 8) per 27-point sweep unit on `level` (-1: all levels)."""
     return _check(load().m2s_set_sweep_warps(grid, int(level), int(warps)), "m2s_set_sweep_warps")
+
+
+def m2s_set_graphs(grid, enable=True):
+    """CUDA-graph replay of the PCG iteration on (default) or off."""
+    return _check(load().m2s_set_graphs(grid, 1 if enable else 0), "m2s_set_graphs")
 
 
 def m2s_sweep_timing(grid, enable=True):

@@ -52,6 +52,7 @@ struct m2s_grid {
     Work<float> w32;
     // PCG state (finest level, packed)
     double *r = nullptr, *z = nullptr, *zold = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
+    double *z_base = nullptr, *zold_base = nullptr;  // z / zold at the start of every solve
     float *r32 = nullptr, *z32 = nullptr;
     double *part = nullptr, *part2 = nullptr;
     int npart = 0;
@@ -72,6 +73,14 @@ struct m2s_grid {
     };
     bool timing = false;
     std::vector<Timing> tim;
+    // CUDA graphs of one PCG iteration (k even, k odd >= 3), captured for
+    // the solution vector x_graph and replayed while it stays the same
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;  // records the graphs (capture is not
+                                        // allowed on the legacy default stream)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    double* x_graph = nullptr;
+    int graph_launches = 0;  // iterations replayed from a graph (statistics)
     std::vector<void*> allocs;
     cudaStream_t last_stream = nullptr;
 };
@@ -108,6 +117,9 @@ void destroy_grid(m2s_grid* g) {
     for (void* p : g->allocs) cudaFree(p);
     for (auto& t : g->tim)
         for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
+    for (cudaGraphExec_t& ge : g->graph)
+        if (ge) cudaGraphExecDestroy(ge);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
 }
 
@@ -367,14 +379,55 @@ m2s_status pcg_batch(m2s_grid* g, const double* b, double* x, const m2s_pcg_opts
     const i64 n = g->ltot[0];
     const int stride = g->hist_cap + 1;
     g->x_cur = x;
+    // the FP32 form swaps z and zold every iteration: start from the same
+    // assignment in every solve (the captured graphs rely on it)
+    g->z = g->z_base;
+    g->zold = g->zold_base;
     M2S_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), st));
     M2S_TRY(cudaMemcpyAsync(g->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     M2S_TRY(launch_dot_b<double>(b0, g->r, g->r, g->part, st));
     M2S_TRY(launch_finalize_b(FIN_BB, g->dev, np, g->part, b0.cstart, nullptr, nullptr, g->hist,
                               stride, o.rtol * o.rtol, o.fixed_iters ? 1 : 0, st));
     std::vector<PcgDev> h(np);
+    // graphs are replayed only when nothing host-side varies between
+    // iterations of the same parity: no per-launch timing, no pending stall
+    const bool graphs = g->use_graphs && !g->timing && g->stall_unit < 0;
+    if (!graphs || g->x_graph != x) {
+        for (cudaGraphExec_t& ge : g->graph)
+            if (ge) cudaGraphExecDestroy(ge), ge = nullptr;
+        g->x_graph = nullptr;
+    }
     for (int k = 1; k <= o.max_iters; ++k) {
-        M2S_TRY(pcg_iteration(g, k, st));
+        if (graphs && k >= 2) {
+            cudaGraphExec_t& ge = g->graph[k & 1];
+            if (!ge) {
+                // record this iteration once on the grid's own stream (its
+                // launches are recorded, not run), then replay it on st
+                cudaGraph_t gr = nullptr;
+                if (!g->cap_stream)
+                    M2S_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+                M2S_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+                const cudaError_t ce = pcg_iteration(g, k, g->cap_stream);
+                const cudaError_t ee = cudaStreamEndCapture(g->cap_stream, &gr);
+                if (ce != cudaSuccess || ee != cudaSuccess) {
+                    if (gr) cudaGraphDestroy(gr);
+                    return cuda_status(ce != cudaSuccess ? ce : ee);
+                }
+                const cudaError_t ie = cudaGraphInstantiate(&ge, gr, 0);
+                cudaGraphDestroy(gr);
+                if (ie != cudaSuccess) {
+                    ge = nullptr;
+                    return cuda_status(ie);
+                }
+                g->x_graph = x;
+            } else if (g->pdtype == M2S_F32) {
+                std::swap(g->z, g->zold);  // the host-side state a run would leave
+            }
+            M2S_TRY(cudaGraphLaunch(ge, st));
+            ++g->graph_launches;
+        } else {
+            M2S_TRY(pcg_iteration(g, k, st));
+        }
         const bool last = k == o.max_iters;
         if (!o.fixed_iters && (k % o.check_every == 0 || last)) {
             M2S_TRY(cudaMemcpyAsync(h.data(), g->dev, np * sizeof(PcgDev), cudaMemcpyDeviceToHost,
@@ -617,6 +670,8 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
         if ((e = galloc(g, &g->r32, n0)) != cudaSuccess) return fail(e);
         if ((e = galloc(g, &g->z32, n0)) != cudaSuccess) return fail(e);
     }
+    g->z_base = g->z;
+    g->zold_base = g->zold;
     // partial sums: chunks of the finest level, the 27-point fused SpMV's
     // tiles of every problem, or the b.x partials of any sweep schedule
     g->h_st27pre.assign(n_problems + 1, 0);
@@ -686,6 +741,12 @@ m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps) {
         if (level >= 0 && l != level) continue;
         M2S_TRY(build_level_units27(grid, l, warps, warps));
     }
+    return M2S_OK;
+}
+
+m2s_status m2s_set_graphs(m2s_grid* grid, int enable) {
+    if (!grid) return M2S_ERR_INVALID_ARG;
+    grid->use_graphs = enable != 0;
     return M2S_OK;
 }
 

@@ -592,3 +592,25 @@ def test_batched_hpcg27_sweeps_and_pcg(m, f32):
         ox, _, _, _ = oracle.pcg(H27, bb, 2, max_iters=10, fixed_iters=True)
         assert err(xh[off:off + n].reshape(s), ox) <= TOL64
         off += n
+
+
+@pytest.mark.parametrize("kind,pdt", [(H27, 0), (H27, 1), (K7, 0), (K7, 1)])
+def test_graph_replay_matches_launches(m, kind, pdt):
+    """CUDA-graph replay of the PCG iteration gives bitwise the same solve as
+    launching every kernel, also when a second solve reuses the graphs."""
+    import torch
+    shape = (24, 20, 28)
+    kap = gen.kappa_field(0, seed=23, shape=shape) if kind == K7 else None
+    bh = oracle.apply(kind, np.ones(shape), kap)
+    plain = make_grid(m, shape, op=kind, levels=3, kappa=kap, pdt=pdt)
+    m.m2s_set_graphs(plain.handle, False)
+    replay = make_grid(m, shape, op=kind, levels=3, kappa=kap, pdt=pdt)
+    out = []
+    for g in (plain, replay, replay):
+        x = torch.empty(shape, dtype=torch.float64, device="cuda")
+        st, res = m.m2s_pcg_solve(g.handle, dev(bh), x, max_iters=200, rtol=1e-10, fixed_iters=False,
+                                  check_every=3)
+        assert st == m.Status.OK
+        out.append((host(x), res.iters, res.rel_resid))
+    assert out[0][1] == out[1][1] == out[2][1]
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[1][0], out[2][0])
