@@ -242,6 +242,19 @@ m2s_status m2s_symgs_noalloc(int nx, int ny, int nz, m2s_dtype dtype,
  * range), M2S_ERR_CUDA / M2S_ERR_OOM from the reallocation. */
 m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps);
 
+/* Autotuner of the 27-point sweep units (form 2: tile shapes chosen by
+ * measurement; the paper's partitioning has no counterpart).  For every
+ * level and both dtypes it times `reps` forward sweeps with each unit shape
+ * m2s_set_sweep_warps allows (4 and 8 warps) on the grid's own scratch
+ * vectors and keeps the faster one.  chosen (host, optional, 2 * mg_levels
+ * ints) receives the warps per unit of each level, FP64 then FP32.  It
+ * synchronises the stream and reallocates the schedules: do not call it
+ * while work of this grid is in flight or during stream capture.  The
+ * result of a sweep does not depend on the shape.  Errors:
+ * M2S_ERR_INVALID_ARG (NULL grid, not a 27-point grid, reps < 1),
+ * M2S_ERR_CUDA, M2S_ERR_OOM, M2S_ERR_TIMEOUT. */
+m2s_status m2s_autotune_sweeps(m2s_grid* grid, int reps, void* stream, int* chosen);
+
 /* CUDA-graph replay of the PCG iteration (default on).  From the second
  * iteration on, m2s_pcg_solve records one iteration of each parity (the
  * search-direction buffers alternate) into a CUDA graph on the caller's

@@ -73,6 +73,7 @@ EXPORTS = (
     "m2s_pcg_solve", "m2s_ssor_sweep", "m2s_adjoint_solve", "m2s_kappa_grad",
     "m2s_set_spin_limit", "m2s_debug_stall_unit", "m2s_symgs_noalloc", "m2s_status_string",
     "m2s_sweep_timing", "m2s_sweep_timing_read", "m2s_set_sweep_warps", "m2s_set_graphs",
+    "m2s_autotune_sweeps",
 )
 
 
@@ -114,6 +115,7 @@ def load():
         "m2s_sweep_timing": ([vp, i], i),
         "m2s_set_sweep_warps": ([vp, i, i], i),
         "m2s_set_graphs": ([vp, i], i),
+        "m2s_autotune_sweeps": ([vp, i, vp, ctypes.POINTER(i)], i),
         "m2s_sweep_timing_read": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(d),
                                    ctypes.POINTER(i)], i),
     }
@@ -215,6 +217,15 @@ def m2s_debug_stall_unit(grid, level, unit):
 def m2s_set_sweep_warps(grid, level, warps):
     """Warps (4 or 8) per 27-point sweep unit on `level` (-1: all levels)."""
     return _check(load().m2s_set_sweep_warps(grid, int(level), int(warps)), "m2s_set_sweep_warps")
+
+
+def m2s_autotune_sweeps(grid, levels, reps=3, stream=None):
+    """Time 4- and 8-warp sweep units on every level and keep the faster;
+    returns [(warps FP64, warps FP32) per level]."""
+    out = (ctypes.c_int * (2 * levels))()
+    _check(load().m2s_autotune_sweeps(grid, int(reps), _stream(stream), out),
+           "m2s_autotune_sweeps")
+    return [(out[2 * l], out[2 * l + 1]) for l in range(levels)]
 
 
 def m2s_set_graphs(grid, enable=True):

@@ -744,6 +744,77 @@ m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps) {
     return M2S_OK;
 }
 
+m2s_status m2s_autotune_sweeps(m2s_grid* g, int reps, void* stream, int* chosen) {
+    if (!g || g->op != M2S_OP_HPCG27 || reps < 1) return M2S_ERR_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    cudaEvent_t e0, e1;
+    M2S_TRY(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_status(e);
+    }
+    const bool timing = g->timing;
+    g->timing = false;
+    // scratch: the grid's own work vectors (their contents are not kept
+    // between calls); b = 0 and x = 0, so the sweeps compute zeros
+    auto time_sweeps = [&](int l, bool f64, float* ms) -> cudaError_t {
+        const i64 n = g->ltot[l];
+        cudaError_t er;
+        if (f64) {
+            double* b = l == 0 ? g->r : g->w64.rc[l];
+            double* x = l == 0 ? g->z : g->w64.zc[l];
+            if ((er = cudaMemsetAsync(b, 0, n * sizeof(double), st)) != cudaSuccess ||
+                (er = cudaMemsetAsync(x, 0, n * sizeof(double), st)) != cudaSuccess ||
+                (er = gs_sweep<double>(g, l, b, x, 0, st)) != cudaSuccess ||
+                (er = cudaEventRecord(e0, st)) != cudaSuccess)
+                return er;
+            for (int k = 0; k < reps; ++k)
+                if ((er = op_sweep<double>(g, l, 0, g->w64.Qa[l], nullptr, b, x, nullptr, st)) !=
+                    cudaSuccess)
+                    return er;
+        } else {
+            float* b = l == 0 ? g->r32 : g->w32.rc[l];
+            float* x = l == 0 ? g->z32 : g->w32.zc[l];
+            if ((er = cudaMemsetAsync(b, 0, n * sizeof(float), st)) != cudaSuccess ||
+                (er = cudaMemsetAsync(x, 0, n * sizeof(float), st)) != cudaSuccess ||
+                (er = gs_sweep<float>(g, l, b, x, 0, st)) != cudaSuccess ||
+                (er = cudaEventRecord(e0, st)) != cudaSuccess)
+                return er;
+            for (int k = 0; k < reps; ++k)
+                if ((er = op_sweep<float>(g, l, 0, g->w32.Qa[l], nullptr, b, x, nullptr, st)) !=
+                    cudaSuccess)
+                    return er;
+        }
+        if ((er = cudaEventRecord(e1, st)) != cudaSuccess ||
+            (er = cudaEventSynchronize(e1)) != cudaSuccess)
+            return er;
+        return cudaEventElapsedTime(ms, e0, e1);
+    };
+    for (int l = 0; l < g->levels && e == cudaSuccess; ++l) {
+        int best[2] = {8, 8};
+        float best_ms[2] = {1e30f, 1e30f};
+        for (int w : {4, 8}) {
+            if ((e = build_level_units27(g, l, w, w)) != cudaSuccess) break;
+            for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
+                float ms = 0.f;
+                if ((e = time_sweeps(l, f == 0, &ms)) != cudaSuccess) break;
+                if (ms < best_ms[f]) best_ms[f] = ms, best[f] = w;
+            }
+        }
+        if (e == cudaSuccess) e = build_level_units27(g, l, best[0], best[1]);
+        if (chosen && e == cudaSuccess) {
+            chosen[2 * l] = best[0];
+            chosen[2 * l + 1] = best[1];
+        }
+    }
+    g->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_status(e);
+    return m2s_grid_sync(g, stream);
+}
+
 m2s_status m2s_set_graphs(m2s_grid* grid, int enable) {
     if (!grid) return M2S_ERR_INVALID_ARG;
     grid->use_graphs = enable != 0;

@@ -614,3 +614,17 @@ def test_graph_replay_matches_launches(m, kind, pdt):
         out.append((host(x), res.iters, res.rel_resid))
     assert out[0][1] == out[1][1] == out[2][1]
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[1][0], out[2][0])
+
+
+def test_autotuned_sweep_units_keep_the_result(m):
+    """The autotuner picks a unit shape per level and dtype from {4, 8}
+    warps; the sweeps' result does not depend on the choice."""
+    import torch
+    shape = (33, 17, 35)
+    b, x0 = rnd(shape, 16), rnd(shape, 17)
+    g = make_grid(m, shape, levels=3)
+    chosen = m.m2s_autotune_sweeps(g.handle, 3, reps=2)
+    assert len(chosen) == 3 and all(w in (4, 8) for pair in chosen for w in pair)
+    x = dev(x0)
+    m.m2s_symgs(g.handle, 0, dev(b), x, 2)
+    assert err64(host(x), oracle.symgs(H27, b, x0, 2)) <= TOL64
