@@ -20,7 +20,10 @@
 // halo row replayed from the producer) and K register slots in z.
 #include <algorithm>
 
+#include <climits>
+
 #include "m2s_block.cuh"
+#include "m2s_cta.cuh"
 #include "m2s_wave_sync.cuh"
 
 namespace m2s {
@@ -29,8 +32,6 @@ namespace {
 
 using namespace wave;
 
-constexpr int KB = 3;  // slots per lane (incl. the halo slot)
-constexpr int GROUPS = 6;
 
 __device__ __forceinline__ void coords(i64 i, int nx, int ny, int* x, int* y, int* z) {
     *x = (int)(i % nx);
@@ -140,99 +141,241 @@ __global__ void block_apply_kernel(Dims d, const double* __restrict__ D,
     }
 }
 
-struct BlockWaveArgs {
-    int nx, ny, nz;
-    i64 n, off;
-    int rev, publish_every;
+// ---------------------------------------------------------------------------
+// Block sweeps as a CTA wavefront (the design of the 7-point sweep in
+// k_wave7.cu, with a group of five lanes per grid point).  A unit is a CTA of
+// BW warps, warp w owning plane z = z0 + w; lane 5g + c of a warp holds
+// component c of the point in row y = y0 - 1 + g (group 0 replays row y0 - 1
+// of the unit to the left from its mailbox, groups 1-5 compute, lanes 30-31
+// idle).  At local step s group g of warp w is at x = s - g - w: the whole
+// CTA is on one hyperplane x + y + z.  The x - 1 neighbour is the group's own
+// previous 5-vector, the y - 1 neighbour the group below one step earlier
+// (shuffles), the z - 1 neighbour the warp below one step earlier (a tagged
+// shared-memory ring) or, for warp 0, the top warp of the unit underneath
+// (tagged mailbox).  Each lane then does 15 FMAs: its row of the three 5x5
+// coupling blocks against the three neighbour vectors.  The backward sweep
+// is the forward sweep in reflected index space with N in place of M.
+// ---------------------------------------------------------------------------
+constexpr int BW = 8;      // warps (planes) per unit
+constexpr int BROWS = 5;   // computing rows (groups 1-5) per unit
+constexpr int BD = 2;      // prefetch depth in steps
+
+struct BlockCtaArgs {
+    int rev;
     long long spin_ns;
     const double* coup;  // [n][3][25]: M (forward) or N (backward)
     const double* rhs;   // [n][5]: s (forward) or v (backward)
     double* out;         // [n][5]: v or w
     double* u;           // backward only: u += cu * w  (may be NULL)
     double cu;
-    const int2* origin;
-    const int4* prod;
+    const int4* units;   // (y0, z0, problem, 0) in ticket order
+    const Dims* dims;
     int n_units;
-    int* flags;
     int* ctrl;
     DevStatus* status;
+    int stall_unit;
+    cta::u64* mbox;      // per point and component one tagged value (2 words)
 };
 
-__device__ __forceinline__ void unit_block(const BlockWaveArgs& a, int t) {
+struct BlockShared {
+    cta::Tagged<double>::W ring[BW][cta::RING][32];
+    volatile int prog[BW];
+};
+
+__device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, BlockShared& sh,
+                                           unsigned tag) {
+    using namespace cta;
+    typedef Tagged<double>::W TW;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int gi = lane / 5, ci = lane - 5 * (lane / 5);
-    const int gbase = 5 * gi;
-    const bool active = gi < GROUPS;
-    const int2 org = a.origin[t];
-    const int4 pr = a.prod[t];
-    const int y = org.x - 1 + gi;
-    const int tbase = (org.x - 1) + (org.y - 1);
-    const bool has_prod = pr.x >= 0 || pr.y >= 0;
-
-    bool rv[KB];
-    i64 base[KB];
+    const int g = lane / 5, c = lane - 5 * (lane / 5);
+    const int gb = 5 * (g < 6 ? g : 0);  // first lane of the group
+    const int4 un = a.units[t];
+    const Dims dm = a.dims[un.z];
+    const int y = un.x - 1 + g;
+    const int z = un.y + w;
+    const bool lane_ok = g < 6;
+    const bool halo = g == 0;
+    const bool rv = lane_ok && y >= 0 && y < dm.ny && z < dm.nz;
+    const bool ring_in = w > 0, ring_out = w < BW - 1;
+    const bool mb_out = lane_ok && !halo && (g == BROWS || w == BW - 1);
+    const bool zmb = w == 0 && z >= 1;
+    const int nx = dm.nx;
     const i64 dir = a.rev ? -1 : 1;
+    const i64 r = rv ? ((i64)z * dm.ny + y) * nx : 0;
+    const i64 L = a.rev ? dm.n - 1 - r : r;  // problem-local point of x = 0
+    const i64 szd = dir * (i64)nx * dm.ny;
+    const double* C = a.coup + dm.off * 75;
+    const double* R = a.rhs + dm.off * 5;
+    double* O = a.out + dm.off * 5;
+    double* U = a.u ? a.u + dm.off * 5 : nullptr;
+    u64* const mbox = a.mbox + dm.off * 10;  // 5 components x 2 words per point
+    const int S = nx + BROWS + 1 + BW;
+
+    // prefetch: the lane's rows of the three coupling blocks and its rhs
+    // component (computing lanes), its component of the replayed row
+    // (group 0), its component of the plane below (warp 0)
+    double pc[BD][15], pr[BD], pm0[BD], pm1[BD];
+    auto fetch = [&](int k, int s) {
+        const int xx = s - g - w;
+        const bool in = rv && (unsigned)xx < (unsigned)nx;
+        const i64 p = L + dir * xx;
 #pragma unroll
-    for (int j = 0; j < KB; ++j) {
-        const int z = org.y - 1 + j;
-        rv[j] = active && z >= 0 && z < a.nz && y >= 0 && y < a.ny;
-        const i64 rb = rv[j] ? ((i64)z * a.ny + y) * a.nx : 0;
-        base[j] = a.rev ? a.off + a.n - 1 - rb : a.off + rb;
-    }
-    double w[KB];
+        for (int d = 0; d < 3; ++d)
 #pragma unroll
-    for (int j = 0; j < KB; ++j) w[j] = 0.0;
-    int cached = 0;
-    const int S = a.nx + (GROUPS - 1) + (KB - 1);
-    const int src_self = active ? gbase : 0;
-    const int src_below = active && gi > 0 ? gbase - 5 : 0;
-    for (int s = 0; s < S; ++s) {
-        const int tnow = s + tbase;
-        if (has_prod && tnow + BIAS > cached) {
-            if (!wait_producers(a.flags, pr, tnow + BIAS, &cached, a.status, a.spin_ns)) return;
+            for (int j = 0; j < 5; ++j)
+                pc[k][5 * d + j] = (in && !halo) ? __ldg(C + p * 75 + d * 25 + c * 5 + j) : 0.0;
+        double m0 = 0.0, m1 = 0.0;
+        if (in && halo) tw_to_regs(mb_load<double>(mbox, p * 5 + c), &m0, &m1);
+        if (in && !halo && zmb) tw_to_regs(mb_load<double>(mbox, (p - szd) * 5 + c), &m0, &m1);
+        pr[k] = (in && !halo) ? __ldg(R + p * 5 + c) : 0.0;
+        pm0[k] = m0;
+        pm1[k] = m1;
+    };
+#pragma unroll
+    for (int k = 0; k < BD; ++k) fetch(k, k);
+
+    double xprev = 0.0;  // this lane's component at the previous step
+    bool ok = true;
+    int cachedC = -(1 << 30);
+    auto fail = [&]() -> bool {
+        int ab = 0;
+        if (lane == 0) ab = ld_relaxed_gpu(&a.status->abort);
+        return __shfl_sync(FULL, ab, 0) != 0;
+    };
+    auto timeout = [&]() {
+        if (lane == 0) {
+            atomicCAS(&a.status->err, 0, (int)M2S_ERR_TIMEOUT);
+            atomicExch(&a.status->abort, 1);
         }
-        double nv[KB];
+    };
+    auto step = [&](int s, int k) {
+        const int xx = s - g - w;
+        double cf[15];
 #pragma unroll
-        for (int j = KB - 1; j >= 0; --j) {
-            // neighbour 5-vectors: own point at x-1, row y-1 at x, plane z-1 at x
-            double vx[5], vy[5], vz[5];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                vx[c] = __shfl_sync(FULL, w[j], src_self + c);
-                vy[c] = __shfl_sync(FULL, w[j], src_below + c);
-                vz[c] = (j > 0) ? __shfl_sync(FULL, w[j > 0 ? j - 1 : 0], src_self + c) : 0.0;
-            }
-            const int x = s - gi - j;
-            const bool in = rv[j] && x >= 0 && x < a.nx;
-            nv[j] = 0.0;
-            if (!in) continue;
-            const i64 p = base[j] + dir * x;
-            if (gi == 0 || j == 0) {
-                if (!(gi == 0 && j == 0)) nv[j] = __ldcg(a.out + p * 5 + ci);
-            } else {
-                const double* C = a.coup + p * 75 + ci * 5;
-                double acc = a.rhs[p * 5 + ci];
-#pragma unroll
-                for (int c = 0; c < 5; ++c) acc = fma(-C[c], vx[c], acc);
-#pragma unroll
-                for (int c = 0; c < 5; ++c) acc = fma(-C[25 + c], vy[c], acc);
-#pragma unroll
-                for (int c = 0; c < 5; ++c) acc = fma(-C[50 + c], vz[c], acc);
-                a.out[p * 5 + ci] = acc;
-                if (a.u) a.u[p * 5 + ci] = fma(a.cu, acc, a.u[p * 5 + ci]);
-                nv[j] = acc;
+        for (int j = 0; j < 15; ++j) cf[j] = pc[k][j];
+        const double rh = pr[k], m0 = pm0[k], m1 = pm1[k];
+        fetch(k, s + BD);
+        const bool in = rv && (unsigned)xx < (unsigned)nx;
+        const bool comp = in && !halo;
+        double X = 0.0, zc = 0.0;
+        bool okx = true, okz = true, okr = true;
+        if (in && halo) okx = Tagged<double>::unpack(regs_to_tw(m0, m1), tag, &X);
+        if (comp && zmb) okz = Tagged<double>::unpack(regs_to_tw(m0, m1), tag, &zc);
+        const TW* re = ring_in ? &sh.ring[w - 1][(s - 1) & (RING - 1)][lane] : nullptr;
+        const unsigned rtag = (unsigned)(s - 1 + BIAS);
+        if (ring_in && s >= 1) okr = Tagged<double>::unpack(*(volatile const TW*)re, rtag, &zc);
+        if (!__all_sync(FULL, okx && okz && okr)) {
+            const i64 p = L + dir * xx;
+            unsigned long long t0 = 0;
+            for (int it = 1;; ++it) {
+                if (!okr) okr = Tagged<double>::unpack(*(volatile const TW*)re, rtag, &zc);
+                if (!okx) okx = Tagged<double>::unpack(mb_load<double>(mbox, p * 5 + c), tag, &X);
+                if (!okz)
+                    okz = Tagged<double>::unpack(mb_load<double>(mbox, (p - szd) * 5 + c), tag, &zc);
+                if (__all_sync(FULL, okx && okz && okr)) break;
+                if ((it & 31) == 0) {
+                    const unsigned long long now = global_ns();
+                    if (t0 == 0) t0 = now;
+                    if (fail()) { ok = false; return; }
+                    if ((long long)(now - t0) > a.spin_ns) { timeout(); ok = false; return; }
+                }
             }
         }
+        // neighbour 5-vectors: x - 1 (own group, previous step), y - 1 (the
+        // group below, previous step), z - 1 (warp below / unit underneath)
+        const int gy = g >= 1 && g < 6 ? gb - 5 : 0;
+        double acc = rh;
 #pragma unroll
-        for (int j = 0; j < KB; ++j) w[j] = nv[j];
-        if ((s + 1) % a.publish_every == 0) publish(a.flags + t, tnow + BIAS);
+        for (int j = 0; j < 5; ++j) {
+            const double vx = __shfl_sync(FULL, xprev, gb + j);
+            const double vy = __shfl_sync(FULL, xprev, gy + j);
+            const double vz = __shfl_sync(FULL, zc, gb + j);
+            acc = fma(-cf[j], vx, acc);
+            acc = fma(-cf[5 + j], vy, acc);
+            acc = fma(-cf[10 + j], vz, acc);
+        }
+        if (comp) {
+            X = acc;
+            const i64 p = L + dir * xx;
+            O[p * 5 + c] = X;
+            if (U) U[p * 5 + c] = fma(a.cu, X, U[p * 5 + c]);
+            if (mb_out) mb_store<double>(mbox, p * 5 + c, X, tag);
+        } else if (!in) {
+            X = 0.0;
+        }
+        xprev = X;
+        if (ring_out) {
+            const int old = s - RING;
+            if (old >= 0 && old + 1 > cachedC) {
+                int cc2 = 0, okk = 1;
+                if (lane == 0) {
+                    unsigned long long t0 = 0;
+                    for (int it = 1;; ++it) {
+                        cc2 = sh.prog[w + 1];
+                        if (cc2 >= old + 1) break;
+                        if ((it & 31) != 0) continue;
+                        const unsigned long long now = global_ns();
+                        if (t0 == 0) t0 = now;
+                        if (ld_relaxed_gpu(&a.status->abort) || (long long)(now - t0) > a.spin_ns) {
+                            atomicCAS(&a.status->err, 0, (int)M2S_ERR_TIMEOUT);
+                            atomicExch(&a.status->abort, 1);
+                            okk = 0;
+                            break;
+                        }
+                    }
+                }
+                okk = __shfl_sync(FULL, okk, 0);
+                cachedC = __shfl_sync(FULL, cc2, 0);
+                if (!okk) { ok = false; return; }
+            }
+            sh.ring[w][s & (RING - 1)][lane] = Tagged<double>::pack(X, (unsigned)(s + BIAS));
+        }
+        __syncwarp();
+        if (lane == 0) sh.prog[w] = s;
+    };
+    for (int s0 = 0; ok && s0 < S; s0 += BD) {
+#pragma unroll
+        for (int k = 0; k < BD; ++k)
+            if (ok) step(s0 + k, k);
     }
-    publish(a.flags + t, DONE);
+    __syncwarp();
+    if (lane == 0) sh.prog[w] = INT_MAX;
 }
 
-__global__ void __launch_bounds__(32) block_wave_kernel(BlockWaveArgs a) {
-    run_units(a.n_units, a.flags, a.ctrl, a.status, [&](int t) { unit_block(a, t); });
+__global__ void __launch_bounds__(BW * 32, 1) block_cta_kernel(BlockCtaArgs a) {
+    __shared__ int s_ticket;
+    __shared__ unsigned s_tag;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    BlockShared& sh = *reinterpret_cast<BlockShared*>(dyn_smem);
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tag = (unsigned)ld_relaxed_gpu(&a.ctrl[2]) + 1u;
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&a.ctrl[0], 1);
+        for (int i = threadIdx.x; i < BW * cta::RING * 32; i += blockDim.x)
+            (&sh.ring[0][0][0])[i] = cta::Tagged<double>::zero();
+        if (threadIdx.x < BW) sh.prog[threadIdx.x] = -(1 << 30);
+        __syncthreads();
+        const int t = s_ticket;
+        if (t >= a.n_units) break;
+        int ab = 0;
+        if (threadIdx.x == 0) ab = ld_relaxed_gpu(&a.status->abort) || t == a.stall_unit;
+        ab = __syncthreads_or(ab);
+        if (!ab) block_warp(a, t, warp, sh, s_tag);
+        __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int last = atomicAdd(&a.ctrl[1], 1) == (int)gridDim.x - 1;
+        if (last) {
+            a.ctrl[0] = 0;
+            a.ctrl[1] = 0;
+            a.ctrl[2] = a.ctrl[2] + 1;
+            a.status->abort = 0;
+            __threadfence();
+        }
+    }
 }
 
 unsigned nblk(i64 n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -272,22 +415,57 @@ cudaError_t block_create(BlockOp* b, const m2s_grid_desc* descs, int n_problems,
                                  cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
             return e;
     }
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_wave_kernel, 32, 0)) !=
-        cudaSuccess)
+    // sweep units of all problems: 5 rows x BW planes, ordered by the step
+    // at which they could start on an idle GPU (the unit to the right lags
+    // BROWS steps, the unit above BW; producers have smaller keys), problems
+    // merged by the same key
+    struct Item {
+        long long key;
+        int z0, problem, y0;
+    };
+    std::vector<Item> items;
+    for (int i = 0; i < n_problems; ++i) {
+        const Dims& d = b->dims[i];
+        for (int Z = 0; Z < (d.nz + BW - 1) / BW; ++Z)
+            for (int Y = 0; Y < (d.ny + BROWS - 1) / BROWS; ++Y)
+                items.push_back(Item{(long long)Y * BROWS + (long long)Z * BW, Z * BW, i, Y * BROWS});
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) {
+        if (x.key != y.key) return x.key < y.key;
+        return x.problem != y.problem ? x.problem < y.problem : x.z0 < y.z0;
+    });
+    std::vector<int4> units(items.size());
+    for (size_t k = 0; k < items.size(); ++k)
+        units[k] = make_int4(items[k].y0, items[k].z0, items[k].problem, 0);
+    WaveUnits& u = b->sweep;
+    u = WaveUnits{};
+    u.n_units = (int)units.size();
+    u.np = n_problems;
+    u.W = BW;
+    if ((e = cudaMalloc(&u.d_units, std::max<size_t>(units.size(), 1) * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_dims, n_problems * sizeof(Dims))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_ctrl, 4 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_mbox, n * 10 * sizeof(unsigned long long))) != cudaSuccess)
         return e;
-    b->units.resize(n_problems);
-    for (int i = 0; i < n_problems; ++i)
-        if ((e = build_units(GROUPS - 1, 0, 0, KB, b->dims[i], per_sm, &b->units[i])) != cudaSuccess)
-            return e;
+    if ((!units.empty() && (e = cudaMemcpy(u.d_units, units.data(), units.size() * sizeof(int4),
+                                           cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(u.d_dims, b->dims.data(), n_problems * sizeof(Dims),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(u.d_ctrl, 0, 4 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(u.d_mbox, 0, n * 10 * sizeof(unsigned long long))) != cudaSuccess)
+        return e;
+    const int smem = (int)sizeof(BlockShared);
+    cudaFuncSetAttribute(block_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_cta_kernel, BW * 32,
+                                                           smem)) != cudaSuccess)
+        return e;
+    u.grid = wave_grid(u.n_units, per_sm);
     b->omega = -1.0;
     return cudaSuccess;
 }
 
-void block_free_units(BlockOp* b) {
-    for (auto& u : b->units) free_wave_units(&u);
-    b->units.clear();
-}
+void block_free_units(BlockOp* b) { free_wave_units(&b->sweep); }
 
 cudaError_t block_apply(BlockOp* b, const double* u, double* y, cudaStream_t st) {
     for (int i = 0; i < b->np; ++i) {
@@ -318,38 +496,34 @@ cudaError_t block_ssor_iter(BlockOp* b, const double* rhs, double* u, double ome
         if (d.n == 0) continue;
         block_apply_kernel<true><<<nblk(d.n, 128), 128, 0, st>>>(d, b->D, b->L, b->U, b->Dinv,
                                                                  rhs, u, b->s);
-        const WaveUnits& un = b->units[i];
-        BlockWaveArgs a;
-        a.nx = d.nx;
-        a.ny = d.ny;
-        a.nz = d.nz;
-        a.n = d.n;
-        a.off = d.off;
-        a.publish_every = 4;
-        a.spin_ns = spin_ns;
-        a.origin = un.d_origin;
-        a.prod = un.d_prod;
-        a.n_units = un.n_units;
-        a.flags = un.d_flags;
-        a.ctrl = un.d_ctrl;
-        a.status = status;
-        // lower sweep: v = s - M v (increasing p)
-        a.rev = 0;
-        a.coup = b->M;
-        a.rhs = b->s;
-        a.out = b->v;
-        a.u = nullptr;
-        a.cu = 0.0;
-        block_wave_kernel<<<un.grid, 32, 0, st>>>(a);
-        // upper sweep: w = v - N w (decreasing p), u += w(2-w) w
-        a.rev = 1;
-        a.coup = b->N;
-        a.rhs = b->v;
-        a.out = b->w;
-        a.u = u;
-        a.cu = cu;
-        block_wave_kernel<<<un.grid, 32, 0, st>>>(a);
     }
+    const WaveUnits& un = b->sweep;
+    if (un.n_units == 0) return cudaGetLastError();
+    BlockCtaArgs a;
+    a.spin_ns = spin_ns;
+    a.units = un.d_units;
+    a.dims = un.d_dims;
+    a.n_units = un.n_units;
+    a.ctrl = un.d_ctrl;
+    a.status = status;
+    a.stall_unit = -1;
+    a.mbox = un.d_mbox;
+    // lower sweep: v = s - M v (increasing p)
+    a.rev = 0;
+    a.coup = b->M;
+    a.rhs = b->s;
+    a.out = b->v;
+    a.u = nullptr;
+    a.cu = 0.0;
+    block_cta_kernel<<<un.grid, BW * 32, sizeof(BlockShared), st>>>(a);
+    // upper sweep: w = v - N w (decreasing p), u += w(2-w) w
+    a.rev = 1;
+    a.coup = b->N;
+    a.rhs = b->v;
+    a.out = b->w;
+    a.u = u;
+    a.cu = cu;
+    block_cta_kernel<<<un.grid, BW * 32, sizeof(BlockShared), st>>>(a);
     return cudaGetLastError();
 }
 

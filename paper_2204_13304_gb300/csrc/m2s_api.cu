@@ -114,6 +114,7 @@ void destroy_grid(m2s_grid* g) {
     cudaDeviceSynchronize();
     for (auto& u : g->units) free_wave_units(&u);
     for (auto& u : g->units32) free_wave_units(&u);
+    block_free_units(&g->blk);
     for (void* p : g->allocs) cudaFree(p);
     for (auto& t : g->tim)
         for (cudaEvent_t e : t.ev) cudaEventDestroy(e);

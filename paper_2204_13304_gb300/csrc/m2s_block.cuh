@@ -21,7 +21,7 @@ struct BlockOp {
     double* v = nullptr;        // [npts][5] lower-sweep result
     double* w = nullptr;        // [npts][5] upper-sweep result
     double omega = -1.0;        // omega that M and N were built for
-    std::vector<WaveUnits> units;  // per problem
+    WaveUnits sweep;            // CTA wavefront units of all problems (one launch)
 };
 
 using BlockAlloc = std::function<cudaError_t(void**, size_t)>;

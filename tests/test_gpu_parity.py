@@ -406,6 +406,31 @@ def test_block_ssor(m, shape):
     assert err64(host(u), oracle.ssor(D, L, U, 1.2, b, u0, 5)) <= TOL64
 
 
+def test_block_ssor_batched(m):
+    """Two block problems of different shapes in one handle: one sweep launch
+    serves both; each matches the oracle."""
+    import torch
+    shapes = [(9, 12, 7), (6, 17, 5)]
+    inputs = [gen.block_ssor_inputs(0, shape=s, seed=50 + i) for i, s in enumerate(shapes)]
+    descs = []
+    for s, (D, L, U, b) in zip(shapes, inputs):
+        nz, ny, nx = s
+        descs.append(dict(nx=nx, ny=ny, nz=nz, op=m.Op.BLOCK7_5x5, mg_levels=1,
+                          D=dev(D), L=dev(L), U=dev(U)))
+    g = m.Grid(descs)
+    u0s = [rnd(s + (5,), 30 + i) for i, s in enumerate(shapes)]
+    u = dev(np.concatenate([v.ravel() for v in u0s]))
+    bb = dev(np.concatenate([inp[3].ravel() for inp in inputs]))
+    m.m2s_ssor_sweep(g.handle, bb, u, 1.2, 4)
+    m.m2s_grid_sync(g.handle)
+    uh = host(u)
+    off = 0
+    for s, (D, L, U, b), u0 in zip(shapes, inputs, u0s):
+        n = int(np.prod(s)) * 5
+        assert err64(uh[off:off + n].reshape(s + (5,)), oracle.ssor(D, L, U, 1.2, b, u0, 4)) <= TOL64
+        off += n
+
+
 def test_block_ssor_omega_change(m):
     import torch
     shape = (6, 5, 7)
