@@ -58,7 +58,8 @@ struct CtaArgs {
     DevStatus* status;
     double* rz;          // b.x partials (W per unit) or NULL
     int stall_unit;
-    unsigned long long* mbox;  // tagged copies of the rows other units read
+    unsigned long long* mbox;  // tagged x of the rows the unit to the right replays
+    unsigned long long* mbg;   // tagged plane sums G the unit above reads
 };
 
 // One compute warp of a CTA unit: lane = row u (lanes 0-1 replay the rows
@@ -78,41 +79,47 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
     const int4 un = a.units[t];
     const int2 org = make_int2(un.x, un.y);
     const Dims dd = a.dims[un.z];
-    const int v1 = org.y + w, v0 = v1 - 1;
+    const int v1 = org.y + w;
     const int u = org.x - 2 + lane;
-    const int tbase = 2 * (org.x - 2) + 2 * v0;
+    const int tbase = 2 * (org.x - 2) + 2 * (v1 - 1);
     const T inv26 = Lit<T>::inv26();
     const bool halo = lane < 2;
     const bool ring_in = w > 0;
     const bool ring_out = w < W - 1;
-    const bool mb_out = !halo && (lane >= 30 || w == W - 1);
+    const bool top = w == W - 1;
+    const bool mb_out = !halo && lane >= 30;
     const int nx = dd.nx;
-    const int y1 = u - v1, y0 = u - v0;
+    const int y1 = u - v1;
     const bool rv1 = v1 < dd.nz && y1 >= 0 && y1 < dd.ny;
-    const bool rv0 = !ring_in && v0 >= 0 && v0 < dd.nz && y0 >= 0 && y0 < dd.ny;
+    // plane sums of the plane below from the unit underneath (warp 0), and
+    // for the unit above (top warp: published at the point of the row above)
+    const bool g_in = !ring_in && v1 >= 1;
+    const int yu = u - (v1 + 1);
+    const bool g_out = top && !halo && v1 + 1 < dd.nz && yu >= 0 && yu < dd.ny;
     const i64 step_dir = a.rev ? -1 : 1;
-    // problem-local index of x = 0 of both rows (meaningful only if valid)
-    const i64 r1 = ((i64)v1 * dd.ny + y1) * nx, r0 = ((i64)v0 * dd.ny + y0) * nx;
+    // problem-local index of x = 0 of this row and of the row above
+    const i64 r1 = ((i64)v1 * dd.ny + y1) * nx, ru = ((i64)(v1 + 1) * dd.ny + yu) * nx;
     const i64 L1 = a.rev ? dd.n - 1 - r1 : r1;
-    const i64 L0 = a.rev ? dd.n - 1 - r0 : r0;
+    const i64 Lu = a.rev ? dd.n - 1 - ru : ru;
     const T* Qin = a.Qin + dd.off;
     const T* B = a.b + dd.off;
     T* Xo = a.x + dd.off;
     T* Qo = a.Qout ? a.Qout + dd.off : nullptr;
-    // this problem's mailbox (indexed by the problem-local point)
+    // this problem's mailboxes (indexed by the problem-local point)
     u64* const mbox = a.mbox + dd.off * (sizeof(T) == 8 ? 2 : 1);
+    u64* const mbg = a.mbg + dd.off * (sizeof(T) == 8 ? 2 : 1);
     // the fused r.z partial is used by the FP64 PCG only; compiling it out of
     // the FP32 sweep keeps float->double conversions off the FP64 pipe
     const bool want_rz = sizeof(T) == 8 && a.rz != nullptr;
 
-    // row state: slot 1 (computed or replayed) and slot 0 (warp 0 only)
+    // row state: the last two x values and the sums passed to the lane above
     T xm1 = 0, xm2 = 0, h1 = 0, h2 = 0, s21 = 0, s22 = 0;
-    T zm1 = 0, zm2 = 0, k1 = 0, k2 = 0, t21 = 0, t22 = 0, g0 = 0;
-    // prefetch ring: slot 1 (Q, b or mailbox bits), slot 0 (mailbox bits)
+    // prefetch ring: Q and b (computing lanes) or the mailbox bits of the
+    // replayed row (halo lanes); the mailbox bits of G (warp 0)
     T rq[D], rb[D], ra0[D], rb0[D];
 
     const int S = nx + 2 * 31 + 3;
-    // fetch the inputs of step s (x1 = s - 2 lane - 2, x0 = x1 + 2) into slot k
+    // fetch the inputs of step s (x1 = s - 2 lane - 2) into slot k
     auto fetch = [&](int k, int x1) {
         T q = 0, bv = 0, m0 = 0, m1 = 0;
         if (rv1 && (unsigned)x1 < (unsigned)nx) {
@@ -120,13 +127,11 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
             if (!halo) {
                 q = __ldg(Qin + p);
                 bv = __ldg(B + p);
+                if (g_in) tw_to_regs(mb_load<T>(mbg, p), &m0, &m1);
             } else {
                 tw_to_regs(mb_load<T>(mbox, p), &q, &bv);
             }
         }
-        const int x0 = x1 + 2;
-        if (rv0 && (unsigned)x0 < (unsigned)nx)
-            tw_to_regs(mb_load<T>(mbox, L0 + step_dir * x0), &m0, &m1);
         rq[k] = q;
         rb[k] = bv;
         ra0[k] = m0;
@@ -151,19 +156,18 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
     };
     auto step = [&](int s, int k) {
         const int x1 = s - 2 * lane - 2;
-        const int x0 = x1 + 2;
         const int tnow = s + tbase;
         const T q = rq[k], bv = rb[k], m0 = ra0[k], m1 = rb0[k];
         fetch(k, x1 + D);
         const bool in1 = rv1 && (unsigned)x1 < (unsigned)nx;
-        const bool in0 = rv0 && (unsigned)x0 < (unsigned)nx;
         const bool comp = in1 && !halo;
-        // replayed values: mailbox (slot 1 halo lanes, slot 0 of warp 0) and
-        // ring (plane sums of the plane below, warps above 0)
-        T X1 = 0, X0 = 0, gin = 0;
+        const bool in0 = comp && g_in;  // G of the plane below from the mailbox
+        // replayed values: mailbox (halo lanes: x of the row; warp 0: G of
+        // the plane below at this point) and ring (G, warps above 0)
+        T X1 = 0, gin = 0;
         bool good = true;
         if (in1 && halo) good = Tagged<T>::unpack(regs_to_tw(q, bv), tag, &X1);
-        if (in0) good = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &X0) && good;
+        if (in0) good = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &gin) && good;
         const TW* re = ring_in ? &sh.ring[w - 1][(tnow - 1) & (RING - 1)][lane] : nullptr;
         const unsigned gtag = (unsigned)(tnow - 1 + BIAS);
         if constexpr (sizeof(T) == 8) {
@@ -177,12 +181,12 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
             if (!__all_sync(FULL, okx && okg)) {
                 bool ok1 = !(in1 && halo), ok0 = !in0;
                 if (!ok1) ok1 = Tagged<T>::unpack(regs_to_tw(q, bv), tag, &X1);
-                if (!ok0) ok0 = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &X0);
+                if (!ok0) ok0 = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &gin);
                 unsigned long long t0 = 0;
                 for (int it = 1;; ++it) {
                     if (!okg) okg = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin);
                     if (!ok1) ok1 = Tagged<T>::unpack(mb_load<T>(mbox, L1 + step_dir * x1), tag, &X1);
-                    if (!ok0) ok0 = Tagged<T>::unpack(mb_load<T>(mbox, L0 + step_dir * x0), tag, &X0);
+                    if (!ok0) ok0 = Tagged<T>::unpack(mb_load<T>(mbg, L1 + step_dir * x1), tag, &gin);
                     if (__all_sync(FULL, ok1 && ok0 && okg)) break;
                     if ((it & 31) == 0) {
                         const unsigned long long now = global_ns();
@@ -206,7 +210,7 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
                     if (in1 && halo)
                         good = Tagged<T>::unpack(mb_load<T>(mbox, L1 + step_dir * x1), tag, &X1);
                     if (in0)
-                        good = Tagged<T>::unpack(mb_load<T>(mbox, L0 + step_dir * x0), tag, &X0) && good;
+                        good = Tagged<T>::unpack(mb_load<T>(mbg, L1 + step_dir * x1), tag, &gin) && good;
                     if (need_g) good = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin) && good;
                     if (__all_sync(FULL, good)) break;
                     if (fail()) { ok = false; return; }
@@ -217,9 +221,9 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
         // computed plane
         const T hu1 = __shfl_up_sync(FULL, h1, 1);
         const T hu2 = __shfl_up_sync(FULL, h2, 1);
-        const T su2 = ring_out ? __shfl_up_sync(FULL, s22, 1) : T(0);
+        const T su2 = __shfl_up_sync(FULL, s22, 1);
         if (comp) {
-            const T N = (xm1 + hu1) + (ring_in ? gin : g0);
+            const T N = (xm1 + hu1) + gin;
             X1 = (q + N) * inv26;
             const i64 p = L1 + step_dir * x1;
             Xo[p] = X1;
@@ -234,11 +238,11 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
         xm1 = X1;
         h2 = h1;
         h1 = H;
+        const T S2 = hu2 + H;
+        const T G = su2 + H;  // centred at x1 - 1
+        s22 = s21;
+        s21 = S2;
         if (ring_out) {
-            const T S2 = hu2 + H;
-            const T G = su2 + H;
-            s22 = s21;
-            s21 = S2;
             // back-pressure: the ring entry of step tnow - RING must have been
             // read by the warp above (first read: entry tbase + 1)
             const int old_entry = tnow - RING;
@@ -264,19 +268,9 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
             }
             sh.ring[w][tnow & (RING - 1)][lane] = Tagged<T>::pack(G, (unsigned)(tnow + BIAS));
         }
-        // replayed plane below (warp 0): its sums feed the computed plane
-        if (!ring_in) {
-            const T ku2 = __shfl_up_sync(FULL, k2, 1);
-            const T tu2 = __shfl_up_sync(FULL, t22, 1);
-            const T H0 = (zm2 + zm1) + X0;
-            zm2 = zm1;
-            zm1 = X0;
-            k2 = k1;
-            k1 = H0;
-            t22 = t21;
-            t21 = ku2 + H0;
-            g0 = tu2 + H0;
-        }
+        // the top warp publishes G for warp 0 of the unit above, at the point
+        // of the row above that consumes it
+        if (g_out && (unsigned)(x1 - 1) < (unsigned)nx) mb_store<T>(mbg, Lu + step_dir * (x1 - 1), G, tag);
         __syncwarp();
         if (lane == 0) sh.prog[w] = tnow;
     };
@@ -362,12 +356,36 @@ int cta_occupancy() {
 
 bool cta_warps_supported(int warps) { return warps == 4 || warps == 8; }
 
-// Default warps per unit (8: measured fastest at every level size from 32^3
-// to 256^3 on a GB300, in both precisions).
+// Default warps per unit, from sweep timings on a GB300 (m2s_autotune_sweeps
+// measures instead): FP64 levels of at most 64^3 points run faster with
+// 4-warp units (more, shorter units shorten the critical path: 0.41 vs
+// 0.46 ms at 64^3, 0.21 vs 0.23 ms at 32^3), larger FP64 levels and all FP32
+// levels with 8 (1.93 vs 2.81 ms at 256^3).
 int cta_default_warps(int dtype_is_f64, Dims d) {
-    (void)dtype_is_f64;
-    (void)d;
-    return 8;
+    return dtype_is_f64 && d.n <= (i64)64 * 64 * 64 ? 4 : 8;
+}
+
+// Ghost units: warp 0 of unit (U, V) reads the plane sums G of the top plane
+// of unit (U, V-1), published by that unit's top warp.  Where (U, V-1) has no
+// valid row, the sums over the rows u0-2, u0-1 (the halo rows of the unit)
+// can still be non-zero, so the unit is added: its rows compute nothing,
+// its halo lanes and sums run and its top warp publishes G.
+void add_ghost_units(int lanes, int planes, std::vector<int2>& org) {
+    int NU = 0, NV = 0;
+    for (const int2& o : org) {
+        NU = std::max(NU, o.x / lanes + 1);
+        NV = std::max(NV, o.y / planes + 1);
+    }
+    std::vector<char> has((size_t)NU * NV, 0);
+    for (const int2& o : org) has[(size_t)(o.y / planes) * NU + o.x / lanes] = 1;
+    const size_t n0 = org.size();
+    for (size_t k = 0; k < n0; ++k) {
+        const int U = org[k].x / lanes, V = org[k].y / planes;
+        if (V >= 1 && !has[(size_t)(V - 1) * NU + U]) {
+            has[(size_t)(V - 1) * NU + U] = 1;
+            org.push_back(make_int2(U * lanes, (V - 1) * planes));
+        }
+    }
 }
 
 int cta_rz_partials_max(const std::vector<Dims>& dims) {
@@ -378,6 +396,7 @@ int cta_rz_partials_max(const std::vector<Dims>& dims) {
             std::vector<int2> org;
             std::vector<int4> prod;
             build_units_host(30, 1, 1, W + 1, d, org, prod);
+            add_ghost_units(30, W, org);
             tot += (int)org.size() * W;
         }
         m = std::max(m, tot);
@@ -410,6 +429,7 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
         std::vector<int2> org;
         std::vector<int4> prod;
         build_units_host(lanes, 1, 1, planes + 1, dims[i], org, prod);
+        add_ghost_units(lanes, planes, org);
         std::vector<Item> mine;
         for (const int2& o : org)
             mine.push_back(Item{2LL * lanes * (o.x / lanes) + 2LL * planes * (o.y / planes), o.y,
@@ -446,7 +466,7 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
         (e = cudaMalloc(&u.d_dims, std::max<size_t>(dims.size(), 1) * sizeof(Dims))) != cudaSuccess ||
         (e = cudaMalloc(&u.d_rzpre, rzpre.size() * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&u.d_ctrl, 4 * sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&u.d_mbox, (size_t)std::max<i64>(words, 1) * sizeof(u64))) != cudaSuccess) {
+        (e = cudaMalloc(&u.d_mbox, 2 * (size_t)std::max<i64>(words, 1) * sizeof(u64))) != cudaSuccess) {
         free_wave_units(&u);
         return e;
     }
@@ -457,10 +477,11 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
         (e = cudaMemcpy(u.d_rzpre, rzpre.data(), rzpre.size() * sizeof(int),
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(u.d_ctrl, 0, 4 * sizeof(int))) != cudaSuccess ||
-        (e = cudaMemset(u.d_mbox, 0, (size_t)std::max<i64>(words, 1) * sizeof(u64))) != cudaSuccess) {
+        (e = cudaMemset(u.d_mbox, 0, 2 * (size_t)std::max<i64>(words, 1) * sizeof(u64))) != cudaSuccess) {
         free_wave_units(&u);
         return e;
     }
+    u.mb_words = std::max<i64>(words, 1);
     const int per_sm = W == 4 ? cta_occupancy<T, 4>() : cta_occupancy<T, 8>();
     u.grid = wave_grid(u.n_units, per_sm);
     *out = u;
@@ -487,6 +508,7 @@ cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, const T* Qin,
     a.rz = c.rz_partials;
     a.stall_unit = c.stall_unit;
     a.mbox = u.d_mbox;
+    a.mbg = u.d_mbox + u.mb_words;
     if (u.W == 4)
         gs27_cta_kernel<T, K, 4, D><<<u.grid, 4 * 32, cta_smem_bytes<T, 4>(), st>>>(a);
     else if (u.W == 8)

@@ -99,6 +99,7 @@ struct WaveUnits {
     int* d_rzpre = nullptr;
     int np = 0;
     int n_rz = 0;     // b.x partials of one launch (units x W)
+    i64 mb_words = 0; // 27-point: words of one mailbox (a second, for G, follows)
 };
 struct WaveCall {
     int rev;              // 0 forward, 1 backward (reflected index space)
