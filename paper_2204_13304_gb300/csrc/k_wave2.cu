@@ -330,21 +330,33 @@ __global__ void __launch_bounds__(W * 32, 1) gs27_cta_kernel(CtaArgs<T> a) {
 }  // namespace
 
 // Shapes of the CTA wavefront per element type: K register slots per lane
-// (one halo plane + K-1 computed planes) and D the depth of the input
-// prefetch ring in steps; the number W of compute warps per CTA is chosen at
-// run time (4 or 8).
+// (one halo plane + K-1 computed planes) and the depth D of the input
+// prefetch ring in steps, which is also the unrolling of the step loop.  The
+// number W of compute warps per CTA is chosen at run time (4 or 8), and so is
+// D for FP32.  Measured on a GB300: FP64 runs fastest with D = 2 at every
+// level size (a shorter unrolled loop, 1.79 vs 1.93 ms at 256^3); FP32 with
+// D = 8 on levels above 128^3 (1.25 vs 1.75 ms at 256^3: the loads of a
+// faster step need the longer lead) and D = 4 below (0.48 vs 0.56 ms at
+// 128^3: the shorter loop stays in the instruction cache).
 template <typename T> struct CtaShape;
-template <> struct CtaShape<double> { static constexpr int K = 2, D = 4; };
-template <> struct CtaShape<float> { static constexpr int K = 2, D = 8; };
+template <> struct CtaShape<double> { static constexpr int K = 2, D = 2, D2 = 2; };
+template <> struct CtaShape<float> { static constexpr int K = 2, D = 4, D2 = 8; };
+
+// Prefetch depth of a level: CtaShape::D, or CtaShape::D2 for FP32 levels of
+// more than 128^3 points.
+template <typename T>
+int cta_depth(Dims d) {
+    return (sizeof(T) == 4 && d.n > (i64)128 * 128 * 128) ? CtaShape<T>::D2 : CtaShape<T>::D;
+}
 
 template <typename T, int W>
 size_t cta_smem_bytes() {
     return sizeof(CtaShared<T, W>);
 }
 
-template <typename T, int W>
+template <typename T, int W, int D>
 int cta_occupancy() {
-    constexpr int K = CtaShape<T>::K, D = CtaShape<T>::D;
+    constexpr int K = CtaShape<T>::K;
     const size_t smem = cta_smem_bytes<T, W>();
     cudaFuncSetAttribute(gs27_cta_kernel<T, K, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
@@ -455,7 +467,6 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
     }
     WaveUnits u{};
     u.n_units = (int)units.size();
-    u.K = K;
     u.W = W;
     u.stencil = 27;
     u.np = (int)dims.size();
@@ -482,7 +493,15 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
         return e;
     }
     u.mb_words = std::max<i64>(words, 1);
-    const int per_sm = W == 4 ? cta_occupancy<T, 4>() : cta_occupancy<T, 8>();
+    // the prefetch depth follows the largest problem of the level
+    Dims big{};
+    for (const Dims& d : dims)
+        if (d.n > big.n) big = d;
+    u.K = K;
+    u.depth = cta_depth<T>(big);
+    constexpr int D1 = CtaShape<T>::D, D2 = CtaShape<T>::D2;
+    const int per_sm = W == 4 ? (u.depth == D1 ? cta_occupancy<T, 4, D1>() : cta_occupancy<T, 4, D2>())
+                              : (u.depth == D1 ? cta_occupancy<T, 8, D1>() : cta_occupancy<T, 8, D2>());
     u.grid = wave_grid(u.n_units, per_sm);
     *out = u;
     return cudaGetLastError();
@@ -491,7 +510,7 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
 template <typename T>
 cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, const T* Qin, T* Qout,
                             const T* b, T* x, cudaStream_t st) {
-    constexpr int K = CtaShape<T>::K, D = CtaShape<T>::D;
+    constexpr int K = CtaShape<T>::K, D1 = CtaShape<T>::D, D2 = CtaShape<T>::D2;
     if (u.n_units == 0) return cudaSuccess;
     CtaArgs<T> a;
     a.rev = c.rev;
@@ -509,10 +528,15 @@ cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, const T* Qin,
     a.stall_unit = c.stall_unit;
     a.mbox = u.d_mbox;
     a.mbg = u.d_mbox + u.mb_words;
-    if (u.W == 4)
-        gs27_cta_kernel<T, K, 4, D><<<u.grid, 4 * 32, cta_smem_bytes<T, 4>(), st>>>(a);
+    const bool d1 = u.depth == D1;
+    if (u.W == 4 && d1)
+        gs27_cta_kernel<T, K, 4, D1><<<u.grid, 4 * 32, cta_smem_bytes<T, 4>(), st>>>(a);
+    else if (u.W == 4)
+        gs27_cta_kernel<T, K, 4, D2><<<u.grid, 4 * 32, cta_smem_bytes<T, 4>(), st>>>(a);
+    else if (u.W == 8 && d1)
+        gs27_cta_kernel<T, K, 8, D1><<<u.grid, 8 * 32, cta_smem_bytes<T, 8>(), st>>>(a);
     else if (u.W == 8)
-        gs27_cta_kernel<T, K, 8, D><<<u.grid, 8 * 32, cta_smem_bytes<T, 8>(), st>>>(a);
+        gs27_cta_kernel<T, K, 8, D2><<<u.grid, 8 * 32, cta_smem_bytes<T, 8>(), st>>>(a);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -91,6 +91,7 @@ struct WaveUnits {
     int K;            // slots per lane (incl. the halo slot)
     int stencil;      // 27 or 7
     int W = 1;        // CTA kernel: compute warps (planes) per unit
+    int depth = 0;    // CTA kernel: prefetch depth (steps) of the launch
     // CTA kernels, all problems of a level in one launch: per unit (u0, v0,
     // problem, first b.x partial), per problem its dims and the prefix of
     // its b.x partials (np + 1 entries)
