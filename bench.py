@@ -199,16 +199,33 @@ def profile_case(args):
     import paper_2204_13304_gb300 as m
     n = args.n
     shape = (n, n, n)
+    if args.profile_case == "block_ssor":
+        import m2s_inputs as gen
+        D, L, U, rhs = gen.block_ssor_inputs(n)
+        dd, ld, ud = [torch.from_numpy(a_).cuda() for a_ in (D, L, U)]
+        g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.BLOCK7_5x5, mg_levels=1, D=dd, L=ld, U=ud)])
+        b = torch.from_numpy(rhs).cuda()
+        u = torch.zeros_like(b)
+        m.m2s_ssor_sweep(g.handle, b, u, 1.2, 3)
+        torch.cuda.synchronize()
+        g.close()
+        print("profile case block_ssor n=%d done" % n)
+        return 0
     f32 = args.profile_case.endswith("32")
     dt = torch.float32 if f32 else torch.float64
-    g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.HPCG27, mg_levels=1,
-                     precond_dtype=m.DType.F32 if f32 else m.DType.F64)])
+    if args.profile_case.startswith("kappa"):
+        import m2s_inputs as gen
+        kap = torch.from_numpy(gen.kappa_field(n)).cuda()
+        g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.DIFF7_KAPPA, mg_levels=1, kappa=kap)])
+    else:
+        g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.HPCG27, mg_levels=1,
+                         precond_dtype=m.DType.F32 if f32 else m.DType.F64)])
     ones = torch.ones(shape, dtype=dt, device="cuda")
     b = torch.empty_like(ones)
     m.m2s_spmv(g.handle, 0, ones, b)
     x = torch.zeros_like(ones)
     for _ in range(3):
-        if args.profile_case.startswith("sweep"):
+        if "sweep" in args.profile_case:
             m.m2s_symgs(g.handle, 0, b, x, 1)
         else:
             m.m2s_spmv(g.handle, 0, b, x)
@@ -427,7 +444,8 @@ def main():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workload configurations (32^3 SGS-PCG, block SSOR, "
                          "variable-kappa, batched adjoint)")
-    ap.add_argument("--profile-case", choices=["sweep64", "sweep32", "spmv64", "spmv32"],
+    ap.add_argument("--profile-case", choices=["sweep64", "sweep32", "spmv64", "spmv32",
+                                               "kappa_sweep64", "block_ssor"],
                     help="run a few launches of one kernel for an ncu capture and exit")
     args = ap.parse_args()
     if args.impl == "reference":
