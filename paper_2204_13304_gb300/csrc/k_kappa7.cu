@@ -84,7 +84,12 @@ __global__ void kappa_setup_kernel(Dims d, const double* __restrict__ kappa, Kap
     k.kr[1][p] = fyp;
     k.kr[2][p] = fzp;
     k.diag[p] = dg;
-    k.invdiag[p] = T(1) / dg;
+    const T id = T(1) / dg;
+    k.invdiag[p] = id;
+    T* f = k.pack[0] + 4 * p;
+    T* r = k.pack[1] + 4 * p;
+    f[0] = fxm, f[1] = fym, f[2] = fzm, f[3] = id;
+    r[0] = fxp, r[1] = fyp, r[2] = fzp, r[3] = id;
 }
 
 // (A x)_p at point i (local index) of level d.

@@ -44,10 +44,8 @@ struct Cta7Args {
     T* Qout;
     const T* b;
     T* x;
-    const T* k0;  // coefficient of the lower x / y / z neighbour in sweep
-    const T* k1;  // order, indexed like x (packed level arrays)
-    const T* k2;
-    const T* invd;
+    const T* kp;  // per point (k_x, k_y, k_z, 1/a_pp) of the lower
+                  // neighbours in sweep order (packed level array)
     const int4* units;  // (y0, z0, problem, first b.x partial), ticket order
     const Dims* dims;   // per problem: extent and packed offset
     int n_units;
@@ -57,6 +55,19 @@ struct Cta7Args {
     int stall_unit;
     u64* mbox;
 };
+
+// The four coefficients of a point: one 32-byte (FP64: two 16-byte loads)
+// or one 16-byte (FP32) read-only load, one sector per lane.
+__device__ __forceinline__ void ld_pack(const double* p, double* a, double* b, double* c,
+                                        double* d) {
+    const double2 u = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    *a = u.x, *b = u.y, *c = v.x, *d = v.y;
+}
+__device__ __forceinline__ void ld_pack(const float* p, float* a, float* b, float* c, float* d) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+    *a = u.x, *b = u.y, *c = u.z, *d = u.w;
+}
 
 template <typename T, int W>
 struct Cta7Shared {
@@ -87,10 +98,7 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
     const i64 szd = dir * (i64)nx * dm.ny;   // index step of the z - 1 neighbour
     const T* Q = a.Qin + dm.off;
     const T* B = a.b + dm.off;
-    const T* K0 = a.k0 + dm.off;
-    const T* K1 = a.k1 + dm.off;
-    const T* K2 = a.k2 + dm.off;
-    const T* ID = a.invd + dm.off;
+    const T* KP = a.kp + 4 * dm.off;
     T* Xo = a.x + dm.off;
     T* Qo = a.Qout ? a.Qout + dm.off : nullptr;
     // this problem's mailbox (indexed by the problem-local point)
@@ -111,10 +119,7 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
             if (!halo) {
                 q = __ldg(Q + p);
                 bv = __ldg(B + p);
-                c0 = __ldg(K0 + p);
-                c1 = __ldg(K1 + p);
-                c2 = __ldg(K2 + p);
-                dd = __ldg(ID + p);
+                ld_pack(KP + 4 * p, &c0, &c1, &c2, &dd);
                 if (zmb) tw_to_regs(mb_load<T>(mbox, p - szd), &m0, &m1);
             } else {
                 tw_to_regs(mb_load<T>(mbox, p), &q, &bv);
@@ -384,11 +389,9 @@ cudaError_t launch_gs7_cta(const WaveUnits& u, const WaveCall& c, const KappaLev
     a.b = b;
     a.x = x;
     // sweep order's lower faces: kf (forward) or the upper faces kr
-    // (backward sweep = forward sweep in reflected index space)
-    a.k0 = c.rev ? k.kr[0] : k.kf[0];
-    a.k1 = c.rev ? k.kr[1] : k.kf[1];
-    a.k2 = c.rev ? k.kr[2] : k.kf[2];
-    a.invd = k.invdiag;
+    // (backward sweep = forward sweep in reflected index space), packed
+    // with 1/a_pp
+    a.kp = k.pack[c.rev ? 1 : 0];
     a.units = u.d_units;
     a.dims = u.d_dims;
     a.n_units = u.n_units;

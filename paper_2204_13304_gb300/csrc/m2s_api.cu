@@ -599,6 +599,8 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
                     return fail(e);
             if ((e = galloc(g, &k.diag, g->ltot[l])) != cudaSuccess) return fail(e);
             if ((e = galloc(g, &k.invdiag, g->ltot[l])) != cudaSuccess) return fail(e);
+            for (int c = 0; c < 2; ++c)
+                if ((e = galloc(g, &k.pack[c], 4 * g->ltot[l])) != cudaSuccess) return fail(e);
             if (g->has32) {
                 KappaLevel<float>& k3 = g->k32[l];
                 for (int c = 0; c < 3; ++c)
@@ -607,6 +609,8 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
                         return fail(e);
                 if ((e = galloc(g, &k3.diag, g->ltot[l])) != cudaSuccess) return fail(e);
                 if ((e = galloc(g, &k3.invdiag, g->ltot[l])) != cudaSuccess) return fail(e);
+                for (int c = 0; c < 2; ++c)
+                    if ((e = galloc(g, &k3.pack[c], 4 * g->ltot[l])) != cudaSuccess) return fail(e);
             }
         }
         for (int i = 0; i < n_problems; ++i) {

@@ -124,6 +124,9 @@ struct KappaLevel {
     T* kr[3];  // kr[d][p]: face between p and p + e_d (0 on the boundary)
     T* diag;
     T* invdiag;
+    // the sweeps' coefficients packed per point, 4 values each: (kf x, y, z,
+    // 1/a_pp) for the forward sweep, (kr x, y, z, 1/a_pp) for the backward
+    T* pack[2];
 };
 // 7-point CTA wavefront sweep (k_wave7.cu): units of 31 rows x W planes.
 template <typename T>
