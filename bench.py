@@ -9,7 +9,7 @@ per-kernel timings of the dominant kernels (CUDA events on the launching
 stream), the roofline of the dominant kernel, an end-to-end time through the
 public API with host buffers, and the serial oracle on the host CPU.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 256] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--size 256] [--impl ours|reference]
 
 Multi-GPU: the solve does not shard (exact lexicographic Gauss-Seidel is
 sequential across z-slabs), so N GPUs run N independent replicas; value is
@@ -94,15 +94,19 @@ class Clocks:
                 "samples": len(s)}
 
 
-def dist_init(args):
+def dist_init(args, backend="nccl"):
+    """One process per GPU (torchrun environment).  The solve does not shard:
+    each rank runs a replica; ranks meet only at the barriers around the timed
+    region and in the max over ranks of the time."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -117,9 +121,16 @@ def max_over_ranks(ws, v):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(ws, t_rank):
+    """Whole-job time per solve: the slowest rank's time per solve divided by
+    the solves of all ranks (each rank solves one replica per step)."""
+    return max_over_ranks(ws, t_rank) / ws
 
 
 def cpu_baseline(n, budget_s=20.0):
@@ -437,7 +448,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--size", "--n", dest="n", type=int, default=256,
+                    help="grid points per dimension of the timed problem")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -593,7 +605,7 @@ def main():
 
     configs = None if args.no_configs else other_configs(m, torch, hbm)
 
-    value = max_over_ranks(ws, t64) / ws
+    value = job_value(ws, t64)
     launches = launches_per_solve(res64.iters)
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
