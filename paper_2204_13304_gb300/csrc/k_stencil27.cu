@@ -34,6 +34,8 @@ struct St27Args {
     const T* xc; // coarse correction (PROLONG_QUP)
     const T* b;  // right-hand side (Q modes) / p_in (PSPMV_DOT)
     T* y;        // output (A x, q, or Q)
+    T scale;     // Q modes: Q is written times this (1 or 1/26)
+    T* bs;       // Q modes: b * scale is also written here when not NULL
     T* pout;     // PSPMV_DOT: updated search direction
     const double* beta;  // PSPMV_DOT: device beta, NULL => p = z
     double* partials;    // PSPMV_DOT: one p.q partial per CTA
@@ -109,10 +111,12 @@ __global__ void __launch_bounds__(TX * TY) st27_kernel(St27Args<T> a) {
                     a.pout[p] = c_m1;
                     part = fma((double)c_m1, (double)yv, part);
                 }
-            } else if (MODE == ST27_QLO) {
-                a.y[p] = ((a.b[p] + s2_m2) + hdn_m1) + xl_m1;
-            } else {  // QUP, PROLONG_QUP
-                a.y[p] = ((a.b[p] + s2) + hup_m1) + xr_m1;
+            } else {
+                const T bp = a.b[p];
+                const T q = MODE == ST27_QLO ? ((bp + s2_m2) + hdn_m1) + xl_m1
+                                             : ((bp + s2) + hup_m1) + xr_m1;  // QUP, PROLONG_QUP
+                a.y[p] = q * a.scale;
+                if (a.bs) a.bs[p] = bp * a.scale;
             }
         }
         s2_m2 = s2_m1;
@@ -141,7 +145,8 @@ __global__ void __launch_bounds__(TX * TY) st27_kernel(St27Args<T> a) {
 
 template <typename T>
 __global__ void restrict27_kernel(Dims f, Dims c, const T* __restrict__ r,
-                                  const T* __restrict__ z, T* __restrict__ rc) {
+                                  const T* __restrict__ z, T* __restrict__ rc,
+                                  T* __restrict__ rcs) {
     const i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x;
     if (i >= c.n) return;
     const int cx = (int)(i % c.nx);
@@ -166,7 +171,15 @@ __global__ void restrict27_kernel(Dims f, Dims c, const T* __restrict__ r,
     }
     const i64 p = f.off + ((i64)fz * f.ny + fy) * f.nx + fx;
     const T az = fma(T(27), z[p], -box);
-    rc[c.off + i] = r[p] - az;
+    const T v = r[p] - az;
+    rc[c.off + i] = v;
+    if (rcs) rcs[c.off + i] = v * Lit<T>::inv26();
+}
+
+template <typename T>
+__global__ void scale_kernel(i64 n, const T* __restrict__ x, T* __restrict__ y) {
+    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+        y[i] = x[i] * Lit<T>::inv26();
 }
 
 template <typename T>
@@ -192,8 +205,8 @@ int st27_num_partials(Dims d) {
 }
 
 template <typename T>
-cudaError_t launch_st27(St27Mode mode, Dims d, Dims dc, const T* x, const T* xc, const T* b, T* y,
-                        cudaStream_t st) {
+cudaError_t st27_run(St27Mode mode, Dims d, Dims dc, const T* x, const T* xc, const T* b, T* y,
+                     T scale, T* bs, cudaStream_t st) {
     St27Args<T> a;
     a.d = d;
     a.dc = dc;
@@ -201,6 +214,8 @@ cudaError_t launch_st27(St27Mode mode, Dims d, Dims dc, const T* x, const T* xc,
     a.xc = xc;
     a.b = b;
     a.y = y;
+    a.scale = scale;
+    a.bs = bs;
     a.pout = nullptr;
     a.beta = nullptr;
     a.partials = nullptr;
@@ -216,6 +231,28 @@ cudaError_t launch_st27(St27Mode mode, Dims d, Dims dc, const T* x, const T* xc,
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_st27(St27Mode mode, Dims d, Dims dc, const T* x, const T* xc, const T* b, T* y,
+                        cudaStream_t st) {
+    return st27_run<T>(mode, d, dc, x, xc, b, y, T(1), nullptr, st);
+}
+
+template <typename T>
+cudaError_t launch_st27_q26(St27Mode mode, Dims d, Dims dc, const T* x, const T* xc, const T* b,
+                            T* Q, T* bs, cudaStream_t st) {
+    if (mode == ST27_SPMV || mode == ST27_PSPMV_DOT) return cudaErrorInvalidValue;
+    return st27_run<T>(mode, d, dc, x, xc, b, Q, T(1) / T(26), bs, st);
+}
+
+template <typename T>
+cudaError_t launch_scale26(i64 n, const T* x, T* y, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    i64 g = (n + 256 * 8 - 1) / (256 * 8);
+    g = g < 1 ? 1 : (g > 4096 ? 4096 : g);
+    scale_kernel<T><<<(unsigned)g, 256, 0, st>>>(n, x, y);
+    return cudaGetLastError();
+}
+
 // p-update + SpMV + dot: pout = z + beta*pin (beta NULL => pout = z),
 // q = A pout, partials[cta] = sum pout.q over the CTA.
 cudaError_t launch_pspmv_dot(Dims d, const double* z, const double* pin, double* pout,
@@ -228,6 +265,8 @@ cudaError_t launch_pspmv_dot(Dims d, const double* z, const double* pin, double*
     a.xc = nullptr;
     a.b = pin;
     a.y = q;
+    a.scale = 1.0;
+    a.bs = nullptr;
     a.pout = pout;
     a.beta = beta;
     a.partials = partials;
@@ -237,11 +276,11 @@ cudaError_t launch_pspmv_dot(Dims d, const double* z, const double* pin, double*
 }
 
 template <typename T>
-cudaError_t launch_restrict27(Dims f, Dims c, const T* r, const T* z, T* rc,
+cudaError_t launch_restrict27(Dims f, Dims c, const T* r, const T* z, T* rc, T* rcs,
                               cudaStream_t st) {
     if (c.n == 0) return cudaSuccess;
     const int bs = 256;
-    restrict27_kernel<T><<<(unsigned)((c.n + bs - 1) / bs), bs, 0, st>>>(f, c, r, z, rc);
+    restrict27_kernel<T><<<(unsigned)((c.n + bs - 1) / bs), bs, 0, st>>>(f, c, r, z, rc, rcs);
     return cudaGetLastError();
 }
 
@@ -257,10 +296,16 @@ template cudaError_t launch_st27<double>(St27Mode, Dims, Dims, const double*, co
                                          const double*, double*, cudaStream_t);
 template cudaError_t launch_st27<float>(St27Mode, Dims, Dims, const float*, const float*,
                                         const float*, float*, cudaStream_t);
+template cudaError_t launch_st27_q26<double>(St27Mode, Dims, Dims, const double*, const double*,
+                                             const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_st27_q26<float>(St27Mode, Dims, Dims, const float*, const float*,
+                                            const float*, float*, float*, cudaStream_t);
+template cudaError_t launch_scale26<double>(i64, const double*, double*, cudaStream_t);
+template cudaError_t launch_scale26<float>(i64, const float*, float*, cudaStream_t);
 template cudaError_t launch_restrict27<double>(Dims, Dims, const double*, const double*, double*,
-                                               cudaStream_t);
+                                               double*, cudaStream_t);
 template cudaError_t launch_restrict27<float>(Dims, Dims, const float*, const float*, float*,
-                                              cudaStream_t);
+                                              float*, cudaStream_t);
 template cudaError_t launch_prolong<double>(Dims, Dims, const double*, double*, cudaStream_t);
 template cudaError_t launch_prolong<float>(Dims, Dims, const float*, float*, cudaStream_t);
 

@@ -68,18 +68,25 @@ __global__ void __launch_bounds__(VB) cast_up_dots_b_kernel(Batch b, const float
     }
 }
 
+// r32 = float(r); r32s = r32 / 26 when not NULL
 __global__ void __launch_bounds__(VB) cast_down_kernel(i64 n, const double* __restrict__ r,
-                                                       float* __restrict__ r32) {
-    for (i64 i = blockIdx.x * (i64)VB + threadIdx.x; i < n; i += (i64)gridDim.x * VB)
-        r32[i] = (float)r[i];
+                                                       float* __restrict__ r32,
+                                                       float* __restrict__ r32s) {
+    for (i64 i = blockIdx.x * (i64)VB + threadIdx.x; i < n; i += (i64)gridDim.x * VB) {
+        const float v = (float)r[i];
+        r32[i] = v;
+        if (r32s) r32s[i] = v * Lit<float>::inv26();
+    }
 }
 
-// x += alpha p; r -= alpha q (alpha of the chunk's problem); partial r.r
+// x += alpha p; r -= alpha q (alpha of the chunk's problem); partial r.r;
+// rs = r / 26 when not NULL
 __global__ void __launch_bounds__(VB) update_b_kernel(Batch b, const PcgDev* __restrict__ s,
                                                       const double* __restrict__ p,
                                                       const double* __restrict__ q,
                                                       double* __restrict__ x,
-                                                      double* __restrict__ r, double* partials) {
+                                                      double* __restrict__ r,
+                                                      double* __restrict__ rs, double* partials) {
     __shared__ double sh[VB / 32];
     i64 lo, hi;
     const int pb = batch_locate(b, blockIdx.x, &lo, &hi);
@@ -89,6 +96,7 @@ __global__ void __launch_bounds__(VB) update_b_kernel(Batch b, const PcgDev* __r
         x[i] = fma(alpha, p[i], x[i]);
         const double ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
+        if (rs) rs[i] = ri * Lit<double>::inv26();
         acc = fma(ri, ri, acc);
     }
     acc = block_sum(acc, sh);
@@ -200,16 +208,16 @@ cudaError_t launch_cast_up_dots_b(const Batch& b, const float* z32, const double
     return cudaGetLastError();
 }
 
-cudaError_t launch_cast_down(i64 n, const double* r, float* r32, cudaStream_t st) {
+cudaError_t launch_cast_down(i64 n, const double* r, float* r32, float* r32s, cudaStream_t st) {
     i64 g = (n + (i64)VB * 8 - 1) / ((i64)VB * 8);
     g = g < 1 ? 1 : (g > 4096 ? 4096 : g);
-    cast_down_kernel<<<(unsigned)g, VB, 0, st>>>(n, r, r32);
+    cast_down_kernel<<<(unsigned)g, VB, 0, st>>>(n, r, r32, r32s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update_b(const Batch& b, const PcgDev* s, const double* p, const double* q,
-                            double* x, double* r, double* partials, cudaStream_t st) {
-    update_b_kernel<<<grid_of(b), VB, 0, st>>>(b, s, p, q, x, r, partials);
+                            double* x, double* r, double* rs, double* partials, cudaStream_t st) {
+    update_b_kernel<<<grid_of(b), VB, 0, st>>>(b, s, p, q, x, r, rs, partials);
     return cudaGetLastError();
 }
 

@@ -47,7 +47,12 @@ template <typename T>
 struct CtaArgs {
     int rev;
     long long spin_ns;
-    const T* Qin;  // packed level arrays of all problems
+    // packed level arrays of all problems.  Qin and Qout hold the
+    // old-neighbour sums pre-scaled by 1/26 (Q/26), so a point's update
+    // (Q + N)/26 is one FMA, N * (1/26) + Q/26.  b is b/26 when Qout is
+    // written (Qout = N * (1/26) + b/26) and b itself when rz is (b.x): a
+    // sweep never does both.
+    const T* Qin;
     T* Qout;
     const T* b;
     T* x;
@@ -224,10 +229,10 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
         const T su2 = __shfl_up_sync(FULL, s22, 1);
         if (comp) {
             const T N = (xm1 + hu1) + gin;
-            X1 = (q + N) * inv26;
+            X1 = fma(N, inv26, q);
             const i64 p = L1 + step_dir * x1;
             Xo[p] = X1;
-            if (Qo) Qo[p] = bv + N;
+            if (Qo) Qo[p] = fma(N, inv26, bv);
             if constexpr (sizeof(T) == 8) {
                 if (want_rz) rz = fma((double)bv, (double)X1, rz);
             }

@@ -23,6 +23,9 @@ constexpr int kMaxTimed = 16384;  // recorded sweep launches per level
 template <typename T>
 struct Work {
     std::vector<T*> Qa, Qb, rc, zc;  // per level, packed over problems
+    // 27-point operator: the level's right-hand side / 26 (its sweeps take
+    // pre-scaled sums); NULL for the other operators
+    std::vector<T*> rs;
 };
 
 }  // namespace
@@ -197,16 +200,18 @@ cudaError_t op_spmv(m2s_grid* g, int l, const T* x, T* y, cudaStream_t st) {
     return launch_spmv7_b<T>(g->batch[l], klev<T>(g, l), x, y, st);
 }
 
-// Q = b + sum of the upper (up) or lower neighbours of (x + P xc).
+// Q = b + sum of the upper (up) or lower neighbours of (x + P xc).  The
+// 27-point operator's Q is written as Q/26, and b/26 to bs when bs is not
+// NULL.
 template <typename T>
-cudaError_t op_qinit(m2s_grid* g, int l, int up, const T* x, const T* xc, const T* b, T* Q,
+cudaError_t op_qinit(m2s_grid* g, int l, int up, const T* x, const T* xc, const T* b, T* Q, T* bs,
                      cudaStream_t st) {
     if (g->op == M2S_OP_HPCG27) {
         for (int i = 0; i < g->np; ++i) {
             const Dims d = g->dims[i][l];
             cudaError_t e =
-                xc ? launch_st27<T>(ST27_PROLONG_QUP, d, coarse_of(g, i, l), x, xc, b, Q, st)
-                   : launch_st27<T>(up ? ST27_QUP : ST27_QLO, d, d, x, nullptr, b, Q, st);
+                xc ? launch_st27_q26<T>(ST27_PROLONG_QUP, d, coarse_of(g, i, l), x, xc, b, Q, bs, st)
+                   : launch_st27_q26<T>(up ? ST27_QUP : ST27_QLO, d, d, x, nullptr, b, Q, bs, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -251,11 +256,14 @@ cudaError_t op_sweep(m2s_grid* g, int l, int rev, const T* Qin, T* Qout, const T
     return e;
 }
 
+// rc = R (r - A z); the 27-point operator also writes rc/26 to rcs when not NULL
 template <typename T>
-cudaError_t op_restrict(m2s_grid* g, int l, const T* r, const T* z, T* rc, cudaStream_t st) {
+cudaError_t op_restrict(m2s_grid* g, int l, const T* r, const T* z, T* rc, T* rcs,
+                        cudaStream_t st) {
     if (g->op == M2S_OP_HPCG27) {
         for (int i = 0; i < g->np; ++i) {
-            cudaError_t e = launch_restrict27<T>(g->dims[i][l], g->dims[i][l + 1], r, z, rc, st);
+            cudaError_t e =
+                launch_restrict27<T>(g->dims[i][l], g->dims[i][l + 1], r, z, rc, rcs, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -264,35 +272,54 @@ cudaError_t op_restrict(m2s_grid* g, int l, const T* r, const T* z, T* rc, cudaS
 }
 
 // V-cycle from level l for all problems: z = M_l^-1 r (packed level-l
-// arrays).  rz (optional) receives the b.x partials of the last sweep of the
-// finest level, W per sweep unit.
+// arrays).  rs is r/26 for the 27-point operator (whose sweeps take Q/26 and
+// write Q/26 from b/26) and r itself otherwise.  rz (optional) receives the
+// b.x partials of the last sweep of the finest level, W per sweep unit.
 template <typename T>
-cudaError_t vcycle(m2s_grid* g, int l, const T* r, T* z, double* rz, cudaStream_t st) {
+cudaError_t vcycle(m2s_grid* g, int l, const T* r, const T* rs, T* z, double* rz,
+                   cudaStream_t st) {
     Work<T>& w = work<T>(g);
     T* Qa = w.Qa[l];
     T* Qb = w.Qb[l];
     cudaError_t e;
     // pre-smoothing from z = 0: the old-neighbour sum is r itself
-    if ((e = op_sweep<T>(g, l, 0, r, Qb, r, z, nullptr, st)) != cudaSuccess) return e;
+    if ((e = op_sweep<T>(g, l, 0, rs, Qb, rs, z, nullptr, st)) != cudaSuccess) return e;
     if (l == g->levels - 1) return op_sweep<T>(g, l, 1, Qb, nullptr, r, z, rz, st);
     if ((e = op_sweep<T>(g, l, 1, Qb, nullptr, r, z, nullptr, st)) != cudaSuccess) return e;
-    if ((e = op_restrict<T>(g, l, r, z, w.rc[l + 1], st)) != cudaSuccess) return e;
-    if ((e = vcycle<T>(g, l + 1, w.rc[l + 1], w.zc[l + 1], nullptr, st)) != cudaSuccess) return e;
+    T* rcs = w.rs.empty() ? nullptr : w.rs[l + 1];
+    if ((e = op_restrict<T>(g, l, r, z, w.rc[l + 1], rcs, st)) != cudaSuccess) return e;
+    if ((e = vcycle<T>(g, l + 1, w.rc[l + 1], rcs ? rcs : w.rc[l + 1], w.zc[l + 1], nullptr, st)) !=
+        cudaSuccess)
+        return e;
     // prolongation fused into the old-neighbour sum of the post-smoothing
-    if ((e = op_qinit<T>(g, l, 1, z, w.zc[l + 1], r, Qa, st)) != cudaSuccess) return e;
-    if ((e = op_sweep<T>(g, l, 0, Qa, Qb, r, z, nullptr, st)) != cudaSuccess) return e;
+    if ((e = op_qinit<T>(g, l, 1, z, w.zc[l + 1], r, Qa, nullptr, st)) != cudaSuccess) return e;
+    if ((e = op_sweep<T>(g, l, 0, Qa, Qb, rs, z, nullptr, st)) != cudaSuccess) return e;
     return op_sweep<T>(g, l, 1, Qb, nullptr, r, z, rz, st);
+}
+
+// V-cycle on a caller's r: the 27-point operator first forms r/26
+template <typename T>
+cudaError_t vcycle_from(m2s_grid* g, const T* r, T* z, cudaStream_t st) {
+    Work<T>& w = work<T>(g);
+    if (w.rs.empty()) return vcycle<T>(g, 0, r, r, z, nullptr, st);
+    cudaError_t e = launch_scale26<T>(g->ltot[0], r, w.rs[0], st);
+    if (e != cudaSuccess) return e;
+    return vcycle<T>(g, 0, r, w.rs[0], z, nullptr, st);
 }
 
 template <typename T>
 cudaError_t symgs(m2s_grid* g, int l, const T* b, T* x, int sweeps, cudaStream_t st) {
     Work<T>& w = work<T>(g);
+    // sweeps that write Q take b/26 for the 27-point operator (formed by the
+    // first Q kernel), b otherwise
+    T* bs = w.rs.empty() ? nullptr : w.rs[l];
+    const T* bq = bs ? bs : b;
     cudaError_t e;
-    if ((e = op_qinit<T>(g, l, 1, x, nullptr, b, w.Qa[l], st)) != cudaSuccess) return e;
+    if ((e = op_qinit<T>(g, l, 1, x, nullptr, b, w.Qa[l], bs, st)) != cudaSuccess) return e;
     for (int s = 0; s < sweeps; ++s) {
-        if ((e = op_sweep<T>(g, l, 0, w.Qa[l], w.Qb[l], b, x, nullptr, st)) != cudaSuccess) return e;
+        if ((e = op_sweep<T>(g, l, 0, w.Qa[l], w.Qb[l], bq, x, nullptr, st)) != cudaSuccess) return e;
         T* qn = (s + 1 < sweeps) ? w.Qa[l] : nullptr;
-        if ((e = op_sweep<T>(g, l, 1, w.Qb[l], qn, b, x, nullptr, st)) != cudaSuccess) return e;
+        if ((e = op_sweep<T>(g, l, 1, w.Qb[l], qn, bq, x, nullptr, st)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -301,7 +328,8 @@ template <typename T>
 cudaError_t gs_sweep(m2s_grid* g, int l, const T* b, T* x, int rev, cudaStream_t st) {
     Work<T>& w = work<T>(g);
     cudaError_t e;
-    if ((e = op_qinit<T>(g, l, rev ? 0 : 1, x, nullptr, b, w.Qa[l], st)) != cudaSuccess) return e;
+    if ((e = op_qinit<T>(g, l, rev ? 0 : 1, x, nullptr, b, w.Qa[l], nullptr, st)) != cudaSuccess)
+        return e;
     return op_sweep<T>(g, l, rev, w.Qa[l], nullptr, b, x, nullptr, st);
 }
 
@@ -328,8 +356,11 @@ cudaError_t pcg_iteration(m2s_grid* g, int k, cudaStream_t st) {
     cudaError_t e;
     // z = M^-1 r and rho = r.z
     if (g->pdtype == M2S_F32) {
-        if ((e = launch_cast_down(n, g->r, g->r32, st)) != cudaSuccess) return e;
-        if ((e = vcycle<float>(g, 0, g->r32, g->z32, nullptr, st)) != cudaSuccess) return e;
+        float* r32s = g->w32.rs.empty() ? nullptr : g->w32.rs[0];
+        if ((e = launch_cast_down(n, g->r, g->r32, r32s, st)) != cudaSuccess) return e;
+        if ((e = vcycle<float>(g, 0, g->r32, r32s ? r32s : g->r32, g->z32, nullptr, st)) !=
+            cudaSuccess)
+            return e;
         double* zo = (k > 1) ? g->zold : nullptr;
         if ((e = launch_cast_up_dots_b(b0, g->z32, g->r, zo, g->z, g->part, g->part2, st)) !=
             cudaSuccess)
@@ -338,7 +369,8 @@ cudaError_t pcg_iteration(m2s_grid* g, int k, cudaStream_t st) {
                                    b0.cstart, nullptr, stride, 0.0, 0, st)) != cudaSuccess)
             return e;
     } else {
-        if ((e = vcycle<double>(g, 0, g->r, g->z, g->part, st)) != cudaSuccess) return e;
+        const double* rs = g->w64.rs.empty() ? g->r : g->w64.rs[0];
+        if ((e = vcycle<double>(g, 0, g->r, rs, g->z, g->part, st)) != cudaSuccess) return e;
         if ((e = launch_finalize_b(FIN_RHO, g->dev, np, g->part, g->units[0].d_rzpre, nullptr,
                                    nullptr, nullptr, stride, 0.0, 0, st)) != cudaSuccess)
             return e;
@@ -364,7 +396,10 @@ cudaError_t pcg_iteration(m2s_grid* g, int k, cudaStream_t st) {
                                    nullptr, stride, 0.0, 0, st)) != cudaSuccess)
             return e;
     }
-    if ((e = launch_update_b(b0, g->dev, pout, g->q, g->x_cur, g->r, g->part, st)) != cudaSuccess)
+    // r/26 for the FP64 V-cycle of the 27-point operator
+    double* rs = (g->pdtype == M2S_F64 && !g->w64.rs.empty()) ? g->w64.rs[0] : nullptr;
+    if ((e = launch_update_b(b0, g->dev, pout, g->q, g->x_cur, g->r, rs, g->part, st)) !=
+        cudaSuccess)
         return e;
     if ((e = launch_finalize_b(FIN_RR, g->dev, np, g->part, b0.cstart, nullptr, nullptr, g->hist,
                                stride, 0.0, 0, st)) != cudaSuccess)
@@ -386,6 +421,8 @@ m2s_status pcg_batch(m2s_grid* g, const double* b, double* x, const m2s_pcg_opts
     g->zold = g->zold_base;
     M2S_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), st));
     M2S_TRY(cudaMemcpyAsync(g->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (g->pdtype == M2S_F64 && !g->w64.rs.empty())
+        M2S_TRY(launch_scale26<double>(n, g->r, g->w64.rs[0], st));
     M2S_TRY(launch_dot_b<double>(b0, g->r, g->r, g->part, st));
     M2S_TRY(launch_finalize_b(FIN_BB, g->dev, np, g->part, b0.cstart, nullptr, nullptr, g->hist,
                               stride, o.rtol * o.rtol, o.fixed_iters ? 1 : 0, st));
@@ -569,7 +606,15 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     g->w64.rc.assign(L, nullptr); g->w64.zc.assign(L, nullptr);
     g->w32.Qa.assign(L, nullptr); g->w32.Qb.assign(L, nullptr);
     g->w32.rc.assign(L, nullptr); g->w32.zc.assign(L, nullptr);
+    if (op == M2S_OP_HPCG27) {
+        g->w64.rs.assign(L, nullptr);
+        if (g->has32) g->w32.rs.assign(L, nullptr);
+    }
     for (int l = 0; l < L; ++l) {
+        if (!g->w64.rs.empty() && (e = galloc(g, &g->w64.rs[l], g->ltot[l])) != cudaSuccess)
+            return fail(e);
+        if (!g->w32.rs.empty() && (e = galloc(g, &g->w32.rs[l], g->ltot[l])) != cudaSuccess)
+            return fail(e);
         if ((e = galloc(g, &g->w64.Qa[l], g->ltot[l])) != cudaSuccess) return fail(e);
         if ((e = galloc(g, &g->w64.Qb[l], g->ltot[l])) != cudaSuccess) return fail(e);
         if (l > 0) {
@@ -891,10 +936,10 @@ m2s_status m2s_mg_restrict(m2s_grid* g, int level, m2s_dtype dtype, const void* 
     if (!g || level < 0 || level + 1 >= g->levels || !r || !z || !rc) return M2S_ERR_INVALID_ARG;
     if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
     if (dtype == M2S_F64)
-        M2S_TRY(op_restrict<double>(g, level, (const double*)r, (const double*)z, (double*)rc,
+        M2S_TRY(op_restrict<double>(g, level, (const double*)r, (const double*)z, (double*)rc, nullptr,
                                     S(stream)));
     else
-        M2S_TRY(op_restrict<float>(g, level, (const float*)r, (const float*)z, (float*)rc,
+        M2S_TRY(op_restrict<float>(g, level, (const float*)r, (const float*)z, (float*)rc, nullptr,
                                    S(stream)));
     return M2S_OK;
 }
@@ -915,9 +960,9 @@ m2s_status m2s_mg_vcycle(m2s_grid* g, m2s_dtype dtype, const void* r, void* z, v
     if (!g || !r || !z || r == z) return M2S_ERR_INVALID_ARG;
     if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
     if (dtype == M2S_F64)
-        M2S_TRY(vcycle<double>(g, 0, (const double*)r, (double*)z, nullptr, S(stream)));
+        M2S_TRY(vcycle_from<double>(g, (const double*)r, (double*)z, S(stream)));
     else
-        M2S_TRY(vcycle<float>(g, 0, (const float*)r, (float*)z, nullptr, S(stream)));
+        M2S_TRY(vcycle_from<float>(g, (const float*)r, (float*)z, S(stream)));
     return M2S_OK;
 }
 

@@ -71,10 +71,19 @@ enum St27Mode {
 template <typename T>
 cudaError_t launch_st27(St27Mode mode, Dims d, Dims dc, const T* x, const T* xc, const T* b, T* y,
                         cudaStream_t st);
+// The Q modes with Q written pre-scaled, Q/26 (the input of the CTA sweep
+// kernel), and b/26 also written to bs when bs is not NULL.
+template <typename T>
+cudaError_t launch_st27_q26(St27Mode mode, Dims d, Dims dc, const T* x, const T* xc, const T* b,
+                            T* Q, T* bs, cudaStream_t st);
+// y = x / 26 (as x * fl(1/26)), n elements
+template <typename T>
+cudaError_t launch_scale26(i64 n, const T* x, T* y, cudaStream_t st);
 int st27_num_partials(Dims d);
 
+// rc = injection of r - A z; rc/26 also written to rcs when rcs is not NULL
 template <typename T>
-cudaError_t launch_restrict27(Dims f, Dims c, const T* r, const T* z, T* rc,
+cudaError_t launch_restrict27(Dims f, Dims c, const T* r, const T* z, T* rc, T* rcs,
                               cudaStream_t st);
 template <typename T>
 cudaError_t launch_prolong(Dims f, Dims c, const T* zc, T* z, cudaStream_t st);
@@ -169,6 +178,8 @@ bool cta_warps_supported(int warps);
 int cta_default_warps(int dtype_is_f64, Dims d);
 // b.x partials of the largest schedule of these problems
 int cta_rz_partials_max(const std::vector<Dims>& dims);
+// Qin and Qout hold Q/26; b is b/26 when Qout is written, b when the b.x
+// partials are (c.rz_partials), and unused otherwise.
 template <typename T>
 cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, const T* Qin, T* Qout,
                             const T* b, T* x, cudaStream_t st);

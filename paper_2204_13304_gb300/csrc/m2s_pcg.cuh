@@ -60,9 +60,11 @@ cudaError_t launch_dot_b(const Batch& b, const T* x, const T* y, double* partial
 cudaError_t launch_cast_up_dots_b(const Batch& b, const float* z32, const double* r,
                                   const double* zold, double* z, double* part_rz,
                                   double* part_rzo, cudaStream_t st);
-cudaError_t launch_cast_down(i64 n, const double* r, float* r32, cudaStream_t st);
+// r32 = float(r), and r32s = r32 / 26 when r32s is not NULL
+cudaError_t launch_cast_down(i64 n, const double* r, float* r32, float* r32s, cudaStream_t st);
+// x += alpha p, r -= alpha q, partial r.r; rs = r / 26 when rs is not NULL
 cudaError_t launch_update_b(const Batch& b, const PcgDev* s, const double* p, const double* q,
-                            double* x, double* r, double* partials, cudaStream_t st);
+                            double* x, double* r, double* rs, double* partials, cudaStream_t st);
 cudaError_t launch_paxpy_b(const Batch& b, const PcgDev* s, int first, const double* z,
                            const double* pin, double* pout, cudaStream_t st);
 // One CTA per problem: sums the problem's partials (range pre[i]..pre[i+1],
