@@ -264,8 +264,8 @@ def other_configs(m, torch, hbm):
     """The other workload configurations of the hot path, measured in the same
     run (synthetic seeded inputs, m2s_inputs): 32^3 SGS-PCG, NPB-LU-shaped
     162^3 x 5 block SSOR, 256^3 variable-kappa MG-PCG in FP64 and with the
-    FP32 preconditioner, and 64 batched variable-kappa problems with the
-    adjoint."""
+    FP32 preconditioner, 64 batched variable-kappa problems with the
+    adjoint, and the 1536^3 FP64 symmetric Gauss-Seidel sweep."""
     import numpy as np
     import m2s_inputs as gen
     out = {}
@@ -395,6 +395,49 @@ def other_configs(m, torch, hbm):
                 "forward_s": tf, "adjoint_s": ta, "iters_max_forward": res[0].iters,
                 "iters_max_adjoint": res[1].iters}
 
+    def symgs_1536():
+        n = 1536
+        rows = n ** 3
+        torch.cuda.empty_cache()
+        free, _ = torch.cuda.mem_get_info()
+        # b, x (29 GB each) + the grid's Q/26, Q'/26, b/26 (87 GB) + mailboxes (22 GB)
+        need = 180 * 2 ** 30
+        if free < need:
+            return {"skipped": "needs ~170 GB of free device memory (%.0f GB free)"
+                               % (free / 2 ** 30)}
+        g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.HPCG27, mg_levels=1)])
+        t = {}
+        try:
+            t["x"] = torch.ones((n, n, n), dtype=torch.float64, device="cuda")
+            t["b"] = torch.empty_like(t["x"])
+            m.m2s_spmv(g.handle, 0, t["x"], t["b"])
+            t["x"].zero_()
+            m.m2s_sweep_timing(g.handle, True)
+            sec = time_cuda(torch, lambda: m.m2s_symgs(g.handle, 0, t["b"], t["x"], 1), 3, 1)
+            k, ms, _ = m.m2s_sweep_timing_read(g.handle, 0)
+            m.m2s_sweep_timing(g.handle, False)
+            used = torch.cuda.mem_get_info()
+        finally:
+            g.close()
+            t.clear()
+            torch.cuda.empty_cache()
+        sweep_s = ms / max(1, k) / 1e3
+        return {"workload": "HPCG 27-point 1536^3 (%d rows, FP64, 29 GB per vector), b = A*ones: "
+                            "symmetric Gauss-Seidel sweeps (forward + backward) from x = 0, the "
+                            "paper's SymGS micro-benchmark grid" % rows,
+                "ms_per_symgs": sec * 1e3, "ms_per_sweep": sweep_s * 1e3,
+                "sweeps_timed": k, "G_point_updates_per_s": 2 * rows / sec / 1e9,
+                "alg_GBs": 48.0 * rows / sec / 1e9, "hbm_frac": 48.0 * rows / sec / 1e9 / hbm,
+                "alg_bytes_note": "48 B/row per symmetric sweep (read b, x; write x; twice)",
+                # the kernel issues ~7.5 FP64 instructions per row and sweep
+                # (separable sums: 8 forward, 7 backward), fewer than the
+                # definition's 27 operations
+                "fp64_pipe_frac_est": 7.5 * rows / sweep_s / FP64_OPS_PEAK,
+                "device_GB_held": (used[1] - used[0]) / 2 ** 30,
+                "parity": "tests/test_gpu_fullsize.py::test_sweep_1536_f64 (sampled sweep "
+                          "identity at this size)"}
+
+    guarded("symgs_1536", symgs_1536)
     guarded("hpcg_32", cfg1)
     guarded("kappa_256", cfg4)
     guarded("block_ssor_162x5", cfg3)

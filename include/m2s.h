@@ -110,9 +110,16 @@ typedef struct {
 
 /* Create a grid of n_problems problems (n_problems >= 1; every desc must
  * use the same op).  Allocates the multigrid hierarchy, coefficient copies,
- * FP32 copies when requested, and all workspaces; copies coefficients with
+ * the FP64 sweep workspaces and schedules, and the FP32 copies of the
+ * variable-kappa operator when requested; copies coefficients with
  * stream-ordered copies on `stream` and synchronises it before returning.
- * On failure *out is NULL and nothing is leaked. */
+ * The Krylov vectors are allocated by the first m2s_pcg_solve or
+ * m2s_adjoint_solve, the 27-point operator's FP32 hierarchy by its first
+ * FP32 call (or PCG with precond_dtype = F32); those calls can therefore
+ * return M2S_ERR_OOM, after which the grid stays usable.  A grid that only
+ * runs FP64 sweeps holds three level-sized FP64 arrays per level plus its
+ * mailboxes (~1/10 of a level).  On failure *out is NULL and nothing is
+ * leaked. */
 m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems,
                            void* stream, m2s_grid** out);
 

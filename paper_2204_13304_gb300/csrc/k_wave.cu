@@ -276,6 +276,7 @@ void free_wave_units(WaveUnits* u) {
     if (u->d_units) cudaFree(u->d_units);
     if (u->d_dims) cudaFree(u->d_dims);
     if (u->d_rzpre) cudaFree(u->d_rzpre);
+    if (u->d_mboff) cudaFree(u->d_mboff);
     *u = WaveUnits{};
 }
 

@@ -65,7 +65,23 @@ struct CtaArgs {
     int stall_unit;
     unsigned long long* mbox;  // tagged x of the rows the unit to the right replays
     unsigned long long* mbg;   // tagged plane sums G the unit above reads
+    const long long* mboff;    // per problem: first value of its mbox and mbg slices
 };
+
+// Mailbox rows (units are 30 rows u x W planes v, origins (30 U, W V)).
+// mbox: the rows u = 30 U + 28, 30 U + 29 of each plane v, written by lanes
+// 30-31 of unit U and replayed by the halo lanes 0-1 of unit U + 1: row
+// slot (v, U, u mod 30 - 28).  mbg: the plane sums G at the rows of the
+// planes v = W m, written by the top warp of the unit below and read by warp
+// 0 of the unit starting at v: row slot (m, u).  Values of a row are
+// contiguous in the sweep's own x, so the mailboxes hold ~1/15 and ~1/W of a
+// level instead of a value per point.
+__host__ __device__ inline int mb_rows_u(int ny, int nz) { return ny + nz - 1; }
+__host__ __device__ inline int mb_cols(int ny, int nz) { return (mb_rows_u(ny, nz) - 1) / 30 + 1; }
+inline i64 mbox_values(const Dims& d) { return (i64)d.nz * mb_cols(d.ny, d.nz) * 2 * d.nx; }
+inline i64 mbg_values(const Dims& d, int W) {
+    return (i64)((d.nz - 1) / W + 1) * mb_rows_u(d.ny, d.nz) * d.nx;
+}
 
 // One compute warp of a CTA unit: lane = row u (lanes 0-1 replay the rows
 // of the unit to the left), plane v1 = org.y + w is computed, plane
@@ -102,17 +118,31 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
     const int yu = u - (v1 + 1);
     const bool g_out = top && !halo && v1 + 1 < dd.nz && yu >= 0 && yu < dd.ny;
     const i64 step_dir = a.rev ? -1 : 1;
-    // problem-local index of x = 0 of this row and of the row above
-    const i64 r1 = ((i64)v1 * dd.ny + y1) * nx, ru = ((i64)(v1 + 1) * dd.ny + yu) * nx;
+    // problem-local index of x = 0 of this row
+    const i64 r1 = ((i64)v1 * dd.ny + y1) * nx;
     const i64 L1 = a.rev ? dd.n - 1 - r1 : r1;
-    const i64 Lu = a.rev ? dd.n - 1 - ru : ru;
+    // mailbox rows of this lane, in the sweep's own coordinates
+    const int NU = mb_rows_u(dd.ny, dd.nz);
+    const i64 mrow = (u >= 0 && (halo || mb_out))
+                         ? (((i64)v1 * mb_cols(dd.ny, dd.nz) + u / 30) * 2 + (u % 30 - 28)) * nx
+                         : 0;
+    const i64 grow_in = g_in ? ((i64)(v1 / W) * NU + u) * nx : 0;
+    const i64 grow_out = g_out ? ((i64)((v1 + 1) / W) * NU + u) * nx : 0;
     const T* Qin = a.Qin + dd.off;
     const T* B = a.b + dd.off;
     T* Xo = a.x + dd.off;
     T* Qo = a.Qout ? a.Qout + dd.off : nullptr;
-    // this problem's mailboxes (indexed by the problem-local point)
-    u64* const mbox = a.mbox + dd.off * (sizeof(T) == 8 ? 2 : 1);
-    u64* const mbg = a.mbg + dd.off * (sizeof(T) == 8 ? 2 : 1);
+    // this problem's mailboxes.  Within a row, x1 is at row + x1 in a forward
+    // sweep and at row + nx - 1 - x1 in a backward one (the direction of the
+    // arrays), so a lane's mailbox index is its array index p plus a
+    // constant: the pointers below are offset by that constant once.
+    const i64 wpv = sizeof(T) == 8 ? 2 : 1;
+    const i64 rx = a.rev ? nx - 1 : 0;
+    u64* const mbox = a.mbox + a.mboff[2 * un.z] * wpv;
+    u64* const mbg = a.mbg + a.mboff[2 * un.z + 1] * wpv;
+    u64* const mbox_p = mbox + (mrow + rx - L1) * wpv;     // index p
+    u64* const mbg_p = mbg + (grow_in + rx - L1) * wpv;    // index p
+    const i64 Gu = grow_out + rx;                           // + step_dir * x
     // the fused r.z partial is used by the FP64 PCG only; compiling it out of
     // the FP32 sweep keeps float->double conversions off the FP64 pipe
     const bool want_rz = sizeof(T) == 8 && a.rz != nullptr;
@@ -132,9 +162,9 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
             if (!halo) {
                 q = __ldg(Qin + p);
                 bv = __ldg(B + p);
-                if (g_in) tw_to_regs(mb_load<T>(mbg, p), &m0, &m1);
+                if (g_in) tw_to_regs(mb_load<T>(mbg_p, p), &m0, &m1);
             } else {
-                tw_to_regs(mb_load<T>(mbox, p), &q, &bv);
+                tw_to_regs(mb_load<T>(mbox_p, p), &q, &bv);
             }
         }
         rq[k] = q;
@@ -190,8 +220,8 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
                 unsigned long long t0 = 0;
                 for (int it = 1;; ++it) {
                     if (!okg) okg = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin);
-                    if (!ok1) ok1 = Tagged<T>::unpack(mb_load<T>(mbox, L1 + step_dir * x1), tag, &X1);
-                    if (!ok0) ok0 = Tagged<T>::unpack(mb_load<T>(mbg, L1 + step_dir * x1), tag, &gin);
+                    if (!ok1) ok1 = Tagged<T>::unpack(mb_load<T>(mbox_p, L1 + step_dir * x1), tag, &X1);
+                    if (!ok0) ok0 = Tagged<T>::unpack(mb_load<T>(mbg_p, L1 + step_dir * x1), tag, &gin);
                     if (__all_sync(FULL, ok1 && ok0 && okg)) break;
                     if ((it & 31) == 0) {
                         const unsigned long long now = global_ns();
@@ -213,9 +243,9 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
                 for (;;) {
                     good = true;
                     if (in1 && halo)
-                        good = Tagged<T>::unpack(mb_load<T>(mbox, L1 + step_dir * x1), tag, &X1);
+                        good = Tagged<T>::unpack(mb_load<T>(mbox_p, L1 + step_dir * x1), tag, &X1);
                     if (in0)
-                        good = Tagged<T>::unpack(mb_load<T>(mbg, L1 + step_dir * x1), tag, &gin) && good;
+                        good = Tagged<T>::unpack(mb_load<T>(mbg_p, L1 + step_dir * x1), tag, &gin) && good;
                     if (need_g) good = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin) && good;
                     if (__all_sync(FULL, good)) break;
                     if (fail()) { ok = false; return; }
@@ -236,7 +266,7 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
             if constexpr (sizeof(T) == 8) {
                 if (want_rz) rz = fma((double)bv, (double)X1, rz);
             }
-            if (mb_out) mb_store<T>(mbox, p, X1, tag);
+            if (mb_out) mb_store<T>(mbox_p, p, X1, tag);
         }
         const T H = (xm2 + xm1) + X1;
         xm2 = xm1;
@@ -275,7 +305,7 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
         }
         // the top warp publishes G for warp 0 of the unit above, at the point
         // of the row above that consumes it
-        if (g_out && (unsigned)(x1 - 1) < (unsigned)nx) mb_store<T>(mbg, Lu + step_dir * (x1 - 1), G, tag);
+        if (g_out && (unsigned)(x1 - 1) < (unsigned)nx) mb_store<T>(mbg, Gu + step_dir * (x1 - 1), G, tag);
         __syncwarp();
         if (lane == 0) sh.prog[w] = tnow;
     };
@@ -441,7 +471,9 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
     };
     std::vector<Item> items;
     std::vector<int> rzpre(dims.size() + 1, 0);
-    i64 words = 0;
+    // per problem the first value of its slice of each mailbox
+    std::vector<long long> mboff(2 * std::max<size_t>(dims.size(), 1), 0);
+    i64 nbox = 0, ng = 0;
     for (size_t i = 0; i < dims.size(); ++i) {
         std::vector<int2> org;
         std::vector<int4> prod;
@@ -459,8 +491,14 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
             items.push_back(mine[k]);
         }
         rzpre[i + 1] = rzpre[i] + (int)mine.size() * W;
-        words += std::max<i64>(dims[i].n, 0) * (sizeof(T) == 8 ? 2 : 1);
+        mboff[2 * i] = nbox;
+        mboff[2 * i + 1] = ng;
+        nbox += mbox_values(dims[i]);
+        ng += mbg_values(dims[i], W);
     }
+    const i64 wpv = sizeof(T) == 8 ? 2 : 1;  // mailbox words per value
+    const i64 box_words = std::max<i64>(nbox, 1) * wpv;
+    const i64 words = box_words + std::max<i64>(ng, 1) * wpv;
     std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
         if (a.key != b.key) return a.key < b.key;
         return a.problem != b.problem ? a.problem < b.problem : a.v0 < b.v0;
@@ -482,7 +520,8 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
         (e = cudaMalloc(&u.d_dims, std::max<size_t>(dims.size(), 1) * sizeof(Dims))) != cudaSuccess ||
         (e = cudaMalloc(&u.d_rzpre, rzpre.size() * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&u.d_ctrl, 4 * sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&u.d_mbox, 2 * (size_t)std::max<i64>(words, 1) * sizeof(u64))) != cudaSuccess) {
+        (e = cudaMalloc(&u.d_mboff, mboff.size() * sizeof(long long))) != cudaSuccess ||
+        (e = cudaMalloc(&u.d_mbox, (size_t)words * sizeof(u64))) != cudaSuccess) {
         free_wave_units(&u);
         return e;
     }
@@ -492,12 +531,14 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
                                           cudaMemcpyHostToDevice)) != cudaSuccess) ||
         (e = cudaMemcpy(u.d_rzpre, rzpre.data(), rzpre.size() * sizeof(int),
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(u.d_mboff, mboff.data(), mboff.size() * sizeof(long long),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(u.d_ctrl, 0, 4 * sizeof(int))) != cudaSuccess ||
-        (e = cudaMemset(u.d_mbox, 0, 2 * (size_t)std::max<i64>(words, 1) * sizeof(u64))) != cudaSuccess) {
+        (e = cudaMemset(u.d_mbox, 0, (size_t)words * sizeof(u64))) != cudaSuccess) {
         free_wave_units(&u);
         return e;
     }
-    u.mb_words = std::max<i64>(words, 1);
+    u.mb_words = box_words;
     // the prefetch depth follows the largest problem of the level
     Dims big{};
     for (const Dims& d : dims)
@@ -533,6 +574,7 @@ cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, const T* Qin,
     a.stall_unit = c.stall_unit;
     a.mbox = u.d_mbox;
     a.mbg = u.d_mbox + u.mb_words;
+    a.mboff = u.d_mboff;
     const bool d1 = u.depth == D1;
     if (u.W == 4 && d1)
         gs27_cta_kernel<T, K, 4, D1><<<u.grid, 4 * 32, cta_smem_bytes<T, 4>(), st>>>(a);

@@ -86,6 +86,12 @@ struct m2s_grid {
     int graph_launches = 0;  // iterations replayed from a graph (statistics)
     std::vector<void*> allocs;
     cudaStream_t last_stream = nullptr;
+    // workspaces made at first use, so that a grid used only for FP64
+    // sweeps holds no Krylov vectors and no FP32 hierarchy (a 1536^3 FP64
+    // vector is 29 GB)
+    bool pcg_ready = false;  // r, z, zold, p0, p1, q
+    bool f32_ready = false;  // FP32 level arrays, sweep schedules, r32, z32
+    std::vector<int> w32_choice;  // 27-point FP32 warps per unit, per level
 };
 
 namespace {
@@ -155,7 +161,8 @@ std::vector<Dims> level_dims(m2s_grid* g, int l) {
     return v;
 }
 
-// (Re)build the 27-point sweep schedules of level l (both dtypes).
+// (Re)build the 27-point sweep schedules of level l: FP64 now, FP32 now if
+// the FP32 hierarchy exists, else when it is made (with w32 warps).
 cudaError_t build_level_units27(m2s_grid* g, int l, int w64, int w32) {
     WaveUnits a{}, b{};
     const std::vector<Dims> dl = level_dims(g, l);
@@ -164,15 +171,67 @@ cudaError_t build_level_units27(m2s_grid* g, int l, int w64, int w32) {
         free_wave_units(&a);
         return e;
     }
-    if ((e = build_cta_units<float>(dl, w32, &b)) != cudaSuccess) {
+    if (g->f32_ready && (e = build_cta_units<float>(dl, w32, &b)) != cudaSuccess) {
         free_wave_units(&a);
         free_wave_units(&b);
         return e;
     }
     free_wave_units(&g->units[l]);
-    free_wave_units(&g->units32[l]);
     g->units[l] = a;
-    g->units32[l] = b;
+    if (g->f32_ready) {
+        free_wave_units(&g->units32[l]);
+        g->units32[l] = b;
+    }
+    g->w32_choice[l] = w32;
+    return cudaSuccess;
+}
+
+// FP32 preconditioner workspaces of the 27-point operator (its level arrays
+// and sweep schedules) and the finest-level r32, z32 of any operator.
+cudaError_t ensure_f32(m2s_grid* g) {
+    if (g->f32_ready) return cudaSuccess;
+    if (!g->has32) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (g->op == M2S_OP_HPCG27) {
+        Work<float>& w = g->w32;
+        w.rs.assign(g->levels, nullptr);
+        for (int l = 0; l < g->levels; ++l) {
+            if ((e = galloc(g, &w.Qa[l], g->ltot[l])) != cudaSuccess ||
+                (e = galloc(g, &w.Qb[l], g->ltot[l])) != cudaSuccess ||
+                (e = galloc(g, &w.rs[l], g->ltot[l])) != cudaSuccess)
+                return e;
+            if (l > 0 && ((e = galloc(g, &w.rc[l], g->ltot[l])) != cudaSuccess ||
+                          (e = galloc(g, &w.zc[l], g->ltot[l])) != cudaSuccess))
+                return e;
+        }
+        for (int l = 0; l < g->levels; ++l) {
+            WaveUnits b{};
+            if ((e = build_cta_units<float>(level_dims(g, l), g->w32_choice[l], &b)) != cudaSuccess) {
+                free_wave_units(&b);
+                return e;
+            }
+            free_wave_units(&g->units32[l]);
+            g->units32[l] = b;
+        }
+    }
+    if ((e = galloc(g, &g->r32, g->ltot[0])) != cudaSuccess ||
+        (e = galloc(g, &g->z32, g->ltot[0])) != cudaSuccess)
+        return e;
+    g->f32_ready = true;
+    return cudaSuccess;
+}
+
+// Krylov vectors of the finest level (PCG and the adjoint solve).
+cudaError_t ensure_pcg(m2s_grid* g) {
+    cudaError_t e;
+    if (!g->pcg_ready) {
+        for (double** p : {&g->r, &g->z, &g->zold, &g->p0, &g->p1, &g->q})
+            if ((e = galloc(g, p, g->ltot[0])) != cudaSuccess) return e;
+        g->z_base = g->z;
+        g->zold_base = g->zold;
+        g->pcg_ready = true;
+    }
+    if (g->pdtype == M2S_F32 && (e = ensure_f32(g)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -335,10 +394,11 @@ cudaError_t gs_sweep(m2s_grid* g, int l, const T* b, T* x, int rev, cudaStream_t
 
 bool valid_level(m2s_grid* g, int level) { return g && level >= 0 && level < g->levels; }
 
+// FP64 always; FP32 where the grid has an FP32 hierarchy (made on first use)
 m2s_status check_dtype(m2s_grid* g, m2s_dtype dt) {
     if (dt == M2S_F64) return M2S_OK;
-    if (dt == M2S_F32 && g->has32) return M2S_OK;
-    return M2S_ERR_INVALID_ARG;
+    if (dt != M2S_F32 || !g->has32) return M2S_ERR_INVALID_ARG;
+    return cuda_status(ensure_f32(g));
 }
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
@@ -606,14 +666,10 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     g->w64.rc.assign(L, nullptr); g->w64.zc.assign(L, nullptr);
     g->w32.Qa.assign(L, nullptr); g->w32.Qb.assign(L, nullptr);
     g->w32.rc.assign(L, nullptr); g->w32.zc.assign(L, nullptr);
-    if (op == M2S_OP_HPCG27) {
-        g->w64.rs.assign(L, nullptr);
-        if (g->has32) g->w32.rs.assign(L, nullptr);
-    }
+    if (op == M2S_OP_HPCG27) g->w64.rs.assign(L, nullptr);
+    g->w32_choice.assign(L, 8);
     for (int l = 0; l < L; ++l) {
         if (!g->w64.rs.empty() && (e = galloc(g, &g->w64.rs[l], g->ltot[l])) != cudaSuccess)
-            return fail(e);
-        if (!g->w32.rs.empty() && (e = galloc(g, &g->w32.rs[l], g->ltot[l])) != cudaSuccess)
             return fail(e);
         if ((e = galloc(g, &g->w64.Qa[l], g->ltot[l])) != cudaSuccess) return fail(e);
         if ((e = galloc(g, &g->w64.Qb[l], g->ltot[l])) != cudaSuccess) return fail(e);
@@ -621,7 +677,8 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
             if ((e = galloc(g, &g->w64.rc[l], g->ltot[l])) != cudaSuccess) return fail(e);
             if ((e = galloc(g, &g->w64.zc[l], g->ltot[l])) != cudaSuccess) return fail(e);
         }
-        if (g->has32) {
+        // the 27-point operator's FP32 arrays are made at first FP32 use
+        if (g->has32 && op != M2S_OP_HPCG27) {
             if ((e = galloc(g, &g->w32.Qa[l], g->ltot[l])) != cudaSuccess) return fail(e);
             if ((e = galloc(g, &g->w32.Qb[l], g->ltot[l])) != cudaSuccess) return fail(e);
             if (l > 0) {
@@ -712,16 +769,8 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
                 return fail(e);
         }
     }
-    // PCG vectors
-    const i64 n0 = g->ltot[0];
-    for (double** p : {&g->r, &g->z, &g->zold, &g->p0, &g->p1, &g->q})
-        if ((e = galloc(g, p, n0)) != cudaSuccess) return fail(e);
-    if (g->has32) {
-        if ((e = galloc(g, &g->r32, n0)) != cudaSuccess) return fail(e);
-        if ((e = galloc(g, &g->z32, n0)) != cudaSuccess) return fail(e);
-    }
-    g->z_base = g->z;
-    g->zold_base = g->zold;
+    // the variable-kappa operator's FP32 hierarchy is made with its
+    // coefficients above; its r32, z32 and every PCG vector at first use
     // partial sums: chunks of the finest level, the 27-point fused SpMV's
     // tiles of every problem, or the b.x partials of any sweep schedule
     g->h_st27pre.assign(n_problems + 1, 0);
@@ -796,6 +845,7 @@ m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps) {
 
 m2s_status m2s_autotune_sweeps(m2s_grid* g, int reps, void* stream, int* chosen) {
     if (!g || g->op != M2S_OP_HPCG27 || reps < 1) return M2S_ERR_INVALID_ARG;
+    M2S_TRY(ensure_f32(g));
     cudaStream_t st = S(stream);
     cudaEvent_t e0, e1;
     M2S_TRY(cudaEventCreate(&e0));
@@ -806,14 +856,15 @@ m2s_status m2s_autotune_sweeps(m2s_grid* g, int reps, void* stream, int* chosen)
     }
     const bool timing = g->timing;
     g->timing = false;
-    // scratch: the grid's own work vectors (their contents are not kept
-    // between calls); b = 0 and x = 0, so the sweeps compute zeros
+    // scratch: the level's own work vectors (their contents are not kept
+    // between calls; on the finest level the r/26 and second Q buffers);
+    // b = 0 and x = 0, so the sweeps compute zeros
     auto time_sweeps = [&](int l, bool f64, float* ms) -> cudaError_t {
         const i64 n = g->ltot[l];
         cudaError_t er;
         if (f64) {
-            double* b = l == 0 ? g->r : g->w64.rc[l];
-            double* x = l == 0 ? g->z : g->w64.zc[l];
+            double* b = l == 0 ? g->w64.rs[0] : g->w64.rc[l];
+            double* x = l == 0 ? g->w64.Qb[0] : g->w64.zc[l];
             if ((er = cudaMemsetAsync(b, 0, n * sizeof(double), st)) != cudaSuccess ||
                 (er = cudaMemsetAsync(x, 0, n * sizeof(double), st)) != cudaSuccess ||
                 (er = gs_sweep<double>(g, l, b, x, 0, st)) != cudaSuccess ||
@@ -824,8 +875,8 @@ m2s_status m2s_autotune_sweeps(m2s_grid* g, int reps, void* stream, int* chosen)
                     cudaSuccess)
                     return er;
         } else {
-            float* b = l == 0 ? g->r32 : g->w32.rc[l];
-            float* x = l == 0 ? g->z32 : g->w32.zc[l];
+            float* b = l == 0 ? g->w32.rs[0] : g->w32.rc[l];
+            float* x = l == 0 ? g->w32.Qb[0] : g->w32.zc[l];
             if ((er = cudaMemsetAsync(b, 0, n * sizeof(float), st)) != cudaSuccess ||
                 (er = cudaMemsetAsync(x, 0, n * sizeof(float), st)) != cudaSuccess ||
                 (er = gs_sweep<float>(g, l, b, x, 0, st)) != cudaSuccess ||
@@ -900,7 +951,7 @@ m2s_status m2s_spmv(m2s_grid* g, int level, m2s_dtype dtype, const void* x, void
         if (dtype != M2S_F64) return M2S_ERR_INVALID_ARG;
         return cuda_status(block_apply(&g->blk, (const double*)x, (double*)y, S(stream)));
     }
-    if (check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    if (m2s_status cs = check_dtype(g, dtype)) return cs;
     if (dtype == M2S_F64) M2S_TRY(op_spmv<double>(g, level, (const double*)x, (double*)y, S(stream)));
     else M2S_TRY(op_spmv<float>(g, level, (const float*)x, (float*)y, S(stream)));
     return M2S_OK;
@@ -909,7 +960,8 @@ m2s_status m2s_spmv(m2s_grid* g, int level, m2s_dtype dtype, const void* x, void
 m2s_status m2s_symgs(m2s_grid* g, int level, m2s_dtype dtype, const void* b, void* x,
                      int n_sym_sweeps, void* stream) {
     if (!valid_level(g, level) || !b || !x || b == x || n_sym_sweeps < 0) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (m2s_status cs = check_dtype(g, dtype)) return cs;
     if (n_sym_sweeps == 0) return M2S_OK;
     if (dtype == M2S_F64)
         M2S_TRY(symgs<double>(g, level, (const double*)b, (double*)x, n_sym_sweeps, S(stream)));
@@ -922,7 +974,8 @@ m2s_status m2s_gs_sweep(m2s_grid* g, int level, m2s_dtype dtype, const void* b, 
                         m2s_direction direction, void* stream) {
     if (!valid_level(g, level) || !b || !x || b == x) return M2S_ERR_INVALID_ARG;
     if (direction != M2S_FORWARD && direction != M2S_BACKWARD) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (m2s_status cs = check_dtype(g, dtype)) return cs;
     const int rev = direction == M2S_BACKWARD;
     if (dtype == M2S_F64)
         M2S_TRY(gs_sweep<double>(g, level, (const double*)b, (double*)x, rev, S(stream)));
@@ -934,7 +987,8 @@ m2s_status m2s_gs_sweep(m2s_grid* g, int level, m2s_dtype dtype, const void* b, 
 m2s_status m2s_mg_restrict(m2s_grid* g, int level, m2s_dtype dtype, const void* r, const void* z,
                            void* rc, void* stream) {
     if (!g || level < 0 || level + 1 >= g->levels || !r || !z || !rc) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (m2s_status cs = check_dtype(g, dtype)) return cs;
     if (dtype == M2S_F64)
         M2S_TRY(op_restrict<double>(g, level, (const double*)r, (const double*)z, (double*)rc, nullptr,
                                     S(stream)));
@@ -947,7 +1001,8 @@ m2s_status m2s_mg_restrict(m2s_grid* g, int level, m2s_dtype dtype, const void* 
 m2s_status m2s_mg_prolong(m2s_grid* g, int level, m2s_dtype dtype, const void* zc, void* z,
                           void* stream) {
     if (!g || level < 0 || level + 1 >= g->levels || !zc || !z) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (m2s_status cs = check_dtype(g, dtype)) return cs;
     for (int i = 0; i < g->np; ++i) {
         const Dims f = g->dims[i][level], c = g->dims[i][level + 1];
         if (dtype == M2S_F64) M2S_TRY(launch_prolong<double>(f, c, (const double*)zc, (double*)z, S(stream)));
@@ -958,7 +1013,8 @@ m2s_status m2s_mg_prolong(m2s_grid* g, int level, m2s_dtype dtype, const void* z
 
 m2s_status m2s_mg_vcycle(m2s_grid* g, m2s_dtype dtype, const void* r, void* z, void* stream) {
     if (!g || !r || !z || r == z) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5 || check_dtype(g, dtype) != M2S_OK) return M2S_ERR_INVALID_ARG;
+    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (m2s_status cs = check_dtype(g, dtype)) return cs;
     if (dtype == M2S_F64)
         M2S_TRY(vcycle_from<double>(g, (const double*)r, (double*)z, S(stream)));
     else
@@ -973,6 +1029,7 @@ m2s_status m2s_pcg_solve(m2s_grid* g, const double* b, double* x, const m2s_pcg_
     m2s_pcg_opts o = *opts;
     if (o.max_iters < 1 || o.max_iters > g->hist_cap || !(o.rtol >= 0)) return M2S_ERR_INVALID_ARG;
     if (o.check_every < 1) o.check_every = 1;
+    M2S_TRY(ensure_pcg(g));
     return pcg_batch(g, b, x, o, out, S(stream));
 }
 

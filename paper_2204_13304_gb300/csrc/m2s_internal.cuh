@@ -109,7 +109,8 @@ struct WaveUnits {
     int* d_rzpre = nullptr;
     int np = 0;
     int n_rz = 0;     // b.x partials of one launch (units x W)
-    i64 mb_words = 0; // 27-point: words of one mailbox (a second, for G, follows)
+    i64 mb_words = 0; // 27-point: words of the row mailbox (the plane-sum mailbox follows)
+    long long* d_mboff = nullptr;  // 27-point: per problem its first mailbox values (2 each)
 };
 struct WaveCall {
     int rev;              // 0 forward, 1 backward (reflected index space)

@@ -1,0 +1,72 @@
+"""Full-size parity of the Gauss-Seidel sweeps, where the serial oracle
+cannot run: every sampled point of a sweep must satisfy the sweep identity of
+Sec. 4.3.3 (tests/sweep_defect.py, pinned against the oracle on the CPU in
+tests/test_sweep_defect.py).
+
+* 256^3 in the launch configuration of the benchmark's solve (FP64: 8-warp
+  units, prefetch depth 2; FP32: 8-warp units, depth 8), forward and
+  backward;
+* 1536^3 FP64, the paper's SymGS micro-benchmark grid (Sec. 7.2.1): 3.6 G
+  rows, 29 GB per vector; the test holds about 200 GB of device memory.
+
+Inputs: b = A*ones (the HPCG right-hand side) and a seeded uniform x0 drawn
+on the device, so both the new and the old neighbour values enter every
+identity.  Tolerances: FP64 1e-13 of the sum of the magnitudes (a sweep
+rounds ~30 terms; a wrong neighbour value shows at ~1e-2), FP32 1e-5.
+"""
+import numpy as np
+import pytest
+
+from sweep_defect import sample_points, sweep_defect_torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    from paper_2204_13304_gb300 import build
+    build.build()
+    import paper_2204_13304_gb300 as m
+    m.load()
+    return m
+
+
+def run_sweep(m, n, dtype, backward, seed, samples):
+    import torch
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.HPCG27, mg_levels=1)])
+    shape = (n, n, n)
+    t = {}
+    try:
+        t["x_new"] = torch.ones(shape, dtype=tdt, device="cuda")
+        t["b"] = torch.empty(shape, dtype=tdt, device="cuda")
+        m.m2s_spmv(g.handle, 0, t["x_new"], t["b"])
+        gen = torch.Generator(device="cuda").manual_seed(seed)
+        t["x_old"] = torch.rand(shape, dtype=tdt, device="cuda", generator=gen)
+        t["x_new"].copy_(t["x_old"])
+        m.m2s_gs_sweep(g.handle, 0, t["b"], t["x_new"],
+                       direction=m.BACKWARD if backward else m.FORWARD)
+        torch.cuda.synchronize()
+        pts = sample_points(shape, samples, seed)
+        return sweep_defect_torch(t["b"], t["x_old"], t["x_new"], pts, backward=backward)
+    finally:
+        g.close()
+        t.clear()
+        torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("backward", [False, True])
+def test_sweep_256_f64_bench_configuration(m, backward):
+    assert run_sweep(m, 256, "f64", backward, 31, 200000) <= 1e-13
+
+
+def test_sweep_256_f32_bench_configuration(m):
+    assert run_sweep(m, 256, "f32", False, 32, 200000) <= 1e-5
+
+
+def test_sweep_1536_f64(m):
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 230 * 2**30:
+        pytest.skip("needs ~200 GB of free device memory (%.0f GB free)" % (free / 2**30))
+    assert run_sweep(m, 1536, "f64", False, 33, 200000) <= 1e-13
