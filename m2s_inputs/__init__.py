@@ -20,6 +20,10 @@ Workload recipes (shapes of the paper's benchmarks, Sec. 7.1):
   * NPB-LU-shaped block SSOR: D_p = U(-1,1)^{5x5} + 10 I, L/U couplings
     U(-0.1, 0.1)^{5x5}, rhs U(-1,1), omega = 1.2.
   * batched problems: cube sides drawn from {32, 48, 64, 96, 128}.
+  * NPB-SP-shaped line solves: per point a pentadiagonal row (a, b, c, d, e)
+    with a, e ~ U(-0.25, 0.25), b, d ~ U(-1, 1), c ~ U(3, 4) (strictly
+    diagonally dominant, so elimination needs no pivoting) and k = 5
+    right-hand sides ~ U(-1, 1).
 """
 import numpy as np
 
@@ -37,6 +41,8 @@ STREAM_RHS = 5
 STREAM_TARGET = 6
 STREAM_VEC = 7
 STREAM_SIDES = 8
+STREAM_PENTA = 9
+STREAM_PENTA_RHS = 10
 
 BATCH_SIDES = (32, 48, 64, 96, 128)
 
@@ -131,3 +137,17 @@ def batch_sides(count=64, seed=BASE_SEED):
     """Cube sides of the batched problems, drawn from BATCH_SIDES."""
     u = uniform(seed, STREAM_SIDES, count)
     return [BATCH_SIDES[int(v * len(BATCH_SIDES))] for v in u]
+
+
+def line_penta_inputs(shape, k=5, seed=BASE_SEED):
+    """(coef, rhs) of the NPB-SP-shaped line solves on a grid of `shape`
+    (nz, ny, nx): coef (nz, ny, nx, 5) = (a, b, c, d, e) per point, rhs
+    (nz, ny, nx, k)."""
+    shape = tuple(shape)
+    npts = int(np.prod(shape))
+    u = uniform(seed, STREAM_PENTA, npts * 5).reshape(shape + (5,))
+    scale = np.array([0.5, 2.0, 1.0, 2.0, 0.5])
+    shift = np.array([-0.25, -1.0, 3.0, -1.0, -0.25])
+    coef = u * scale + shift
+    rhs = (2.0 * uniform(seed, STREAM_PENTA_RHS, npts * k) - 1.0).reshape(shape + (k,))
+    return coef, rhs

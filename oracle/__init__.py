@@ -57,6 +57,7 @@ def lib():
             "or_block_lower": [_i, _i, _i, _dp, _dp, _d, _dp, _dp],
             "or_block_upper": [_i, _i, _i, _dp, _dp, _d, _dp, _dp],
             "or_ssor": [_i, _i, _i, _dp, _dp, _dp, _d, _dp, _dp, _i],
+            "or_line_penta": [_i, _i, _i, _i, _dp, _dp, _i],
             "or_coarse_n": [_i],
             "or_abi_version": [],
         }
@@ -268,3 +269,17 @@ def ssor(D, L, U, omega, b, u, n_iters):
     lib().or_ssor(nx, ny, nz, _p(_f64(D)), _p(_f64(L)), _p(_f64(U)), float(omega),
                   _p(b), _p(u), int(n_iters))
     return u
+
+
+def line_penta(coef, rhs, axis):
+    """Solutions of the pentadiagonal systems along the lines of `axis`
+    (0 = x, 1 = y, 2 = z): coef (nz, ny, nx, 5) holds (a, b, c, d, e) of
+    a v_{i-2} + b v_{i-1} + c v_i + d v_{i+1} + e v_{i+2} = r_i at each point
+    (terms outside the line dropped), rhs (nz, ny, nx, k) the k right-hand
+    sides (NPB-SP's direct solves, Sec. 1, Sec. 7.2.2)."""
+    coef = _f64(coef)
+    v = _f64(rhs).copy()
+    nz, ny, nx, k = v.shape
+    assert coef.shape == (nz, ny, nx, 5)
+    lib().or_line_penta(nx, ny, nz, int(axis), _p(coef), _p(v), int(k))
+    return v

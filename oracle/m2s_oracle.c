@@ -699,4 +699,64 @@ void or_ssor(int nx, int ny, int nz, const double* D, const double* L,
 }
 
 /* Version tag so the tests can check which oracle build is loaded. */
+/* ------------------------------------------------------------------------ */
+/* Direct solves of multi-diagonal systems along grid lines (the "direct    */
+/* solving of multi-diagonal matrices" of NPB-SP, Sec. 1 and Sec. 7.2.2:    */
+/* along each axis in turn, every line is swept forward and backward).      */
+/* Point p at position i of its line carries the equation                   */
+/*   a v_{i-2} + b v_{i-1} + c v_i + d v_{i+1} + e v_{i+2} = r_i,           */
+/* coef[p][0..4] = (a, b, c, d, e); terms outside the line are dropped.     */
+/* rhs[p][0..k-1] holds k right-hand sides and is overwritten with the      */
+/* solutions.  The oracle is Gaussian elimination without pivoting on the   */
+/* band of each line, in the textbook order: for every pivot row i,        */
+/* subtract multiples of it from rows i+1 and i+2, then back-substitute.   */
+/* ------------------------------------------------------------------------ */
+void or_line_penta(int nx, int ny, int nz, int axis, const double* coef,
+                   double* rhs, int k) {
+    const int ext[3] = {nx, ny, nz};
+    const i64 stride[3] = {1, nx, (i64)nx * ny};
+    const int m = ext[axis];
+    /* the two coordinates across the lines */
+    const int o1 = axis == 0 ? 1 : 0, o2 = axis == 2 ? 1 : 2;
+    double* A = (double*)malloc(sizeof(double) * 5 * (size_t)(m > 0 ? m : 1));
+    double* R = (double*)malloc(sizeof(double) * (size_t)k * (size_t)(m > 0 ? m : 1));
+    for (int c2 = 0; c2 < ext[o2]; ++c2)
+        for (int c1 = 0; c1 < ext[o1]; ++c1) {
+            const i64 base = (i64)c1 * stride[o1] + (i64)c2 * stride[o2];
+            /* gather the band: A[i][j] multiplies v_{i+j-2} */
+            for (int i = 0; i < m; ++i) {
+                const i64 p = base + (i64)i * stride[axis];
+                for (int j = 0; j < 5; ++j) {
+                    const int col = i + j - 2;
+                    A[5 * i + j] = (col >= 0 && col < m) ? coef[5 * p + j] : 0.0;
+                }
+                for (int t = 0; t < k; ++t) R[(size_t)k * i + t] = rhs[(i64)k * p + t];
+            }
+            /* elimination below each pivot */
+            for (int i = 0; i < m; ++i) {
+                for (int r = i + 1; r <= i + 2 && r < m; ++r) {
+                    const int j = i - r + 2; /* column i in row r's band */
+                    const double f = A[5 * r + j] / A[5 * i + 2];
+                    for (int t = 0; t < 3 && j + t < 5; ++t)
+                        A[5 * r + j + t] -= f * A[5 * i + 2 + t];
+                    for (int t = 0; t < k; ++t) R[(size_t)k * r + t] -= f * R[(size_t)k * i + t];
+                }
+            }
+            /* back substitution */
+            for (int i = m - 1; i >= 0; --i)
+                for (int t = 0; t < k; ++t) {
+                    double s = R[(size_t)k * i + t];
+                    if (i + 1 < m) s -= A[5 * i + 3] * R[(size_t)k * (i + 1) + t];
+                    if (i + 2 < m) s -= A[5 * i + 4] * R[(size_t)k * (i + 2) + t];
+                    R[(size_t)k * i + t] = s / A[5 * i + 2];
+                }
+            for (int i = 0; i < m; ++i) {
+                const i64 p = base + (i64)i * stride[axis];
+                for (int t = 0; t < k; ++t) rhs[(i64)k * p + t] = R[(size_t)k * i + t];
+            }
+        }
+    free(A);
+    free(R);
+}
+
 int or_abi_version(void) { return 1; }

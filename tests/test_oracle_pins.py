@@ -574,3 +574,84 @@ def test_stored_pcg_histories_start_at_closed_form_norm_of_b(n):
              for k in range(4))
     assert abs(hist[0] - np.sqrt(bb)) <= 1e-12 * np.sqrt(bb)
     assert hist[-1] <= 1e-10 * hist[0] < hist[-2]
+
+
+# ---------------------------------------------------------------------------
+# NPB-SP-shaped line solves (Sec. 1, Sec. 7.2.2): pentadiagonal systems along
+# the lines of one axis, terms outside a line dropped.
+# ---------------------------------------------------------------------------
+LINE_SHAPES = [(3, 4, 5), (5, 3, 4), (4, 5, 3), (1, 2, 7), (6, 1, 2)]
+
+
+def _line_dense(coef, axis):
+    """Per line (in the order of the other two coordinates) the dense m x m
+    matrix assembled from the band, independently of the oracle."""
+    c = np.moveaxis(coef, 2 - axis, 2)  # line axis last among the grid axes
+    m = c.shape[2]
+    mats = {}
+    for i0 in range(c.shape[0]):
+        for i1 in range(c.shape[1]):
+            A = np.zeros((m, m))
+            for i in range(m):
+                for j, off in enumerate((-2, -1, 0, 1, 2)):
+                    if 0 <= i + off < m:
+                        A[i, i + off] = c[i0, i1, i, j]
+            mats[(i0, i1)] = A
+    return mats
+
+
+@pytest.mark.parametrize("shape", LINE_SHAPES)
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_line_penta_matches_dense_solves(shape, axis):
+    coef, rhs = gen.line_penta_inputs(shape, k=3, seed=gen.BASE_SEED + 31)
+    v = oracle.line_penta(coef, rhs, axis)
+    mats = _line_dense(coef, axis)
+    r = np.moveaxis(rhs, 2 - axis, 2)
+    vv = np.moveaxis(v, 2 - axis, 2)
+    for (i0, i1), A in mats.items():
+        ref = np.linalg.solve(A, r[i0, i1])
+        assert np.max(np.abs(vv[i0, i1] - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+        # residual of the band applied to the oracle's solution
+        assert np.max(np.abs(A @ vv[i0, i1] - r[i0, i1])) <= 1e-13
+
+
+def test_line_penta_tridiagonal_matches_solve_banded():
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    shape = (4, 3, 9)
+    coef, rhs = gen.line_penta_inputs(shape, k=2, seed=gen.BASE_SEED + 32)
+    coef[..., 0] = 0.0
+    coef[..., 4] = 0.0
+    v = oracle.line_penta(coef, rhs, 0)
+    for z in range(shape[0]):
+        for y in range(shape[1]):
+            ab = np.zeros((3, shape[2]))
+            ab[0, 1:] = coef[z, y, :-1, 3]   # super-diagonal: d of row i at column i+1
+            ab[1, :] = coef[z, y, :, 2]
+            ab[2, :-1] = coef[z, y, 1:, 1]   # sub-diagonal: b of row i at column i-1
+            ref = scipy_linalg.solve_banded((1, 1), ab, rhs[z, y])
+            assert np.max(np.abs(v[z, y] - ref)) <= 1e-13
+
+
+def test_line_penta_diagonal_is_exact_division():
+    shape = (3, 5, 4)
+    coef, rhs = gen.line_penta_inputs(shape, k=4, seed=gen.BASE_SEED + 33)
+    coef[..., [0, 1, 3, 4]] = 0.0
+    for axis in range(3):
+        v = oracle.line_penta(coef, rhs, axis)
+        assert np.array_equal(v, rhs / coef[..., 2:3])
+
+
+def test_line_penta_axis_permutation():
+    """Solving along x equals solving along z of the grid with x and z
+    exchanged (the same lines, the same arithmetic): pins the axis order."""
+    shape = (3, 4, 6)
+    coef, rhs = gen.line_penta_inputs(shape, k=2, seed=gen.BASE_SEED + 34)
+    vx = oracle.line_penta(coef, rhs, 0)
+    ct = np.ascontiguousarray(np.transpose(coef, (2, 1, 0, 3)))
+    rt = np.ascontiguousarray(np.transpose(rhs, (2, 1, 0, 3)))
+    vz = oracle.line_penta(ct, rt, 2)
+    assert np.array_equal(vx, np.transpose(vz, (2, 1, 0, 3)))
+    vy = oracle.line_penta(coef, rhs, 1)
+    ct = np.ascontiguousarray(np.transpose(coef, (0, 2, 1, 3)))
+    rt = np.ascontiguousarray(np.transpose(rhs, (0, 2, 1, 3)))
+    assert np.array_equal(vy, np.transpose(oracle.line_penta(ct, rt, 0), (0, 2, 1, 3)))
