@@ -222,6 +222,16 @@ def profile_case(args):
         g.close()
         print("profile case block_ssor n=%d done" % n)
         return 0
+    if args.profile_case == "line_penta":
+        import m2s_inputs as gen
+        coef, rhs = gen.line_penta_inputs(shape, k=5)
+        c = torch.from_numpy(coef).cuda()
+        r = torch.from_numpy(rhs).cuda()
+        for a in (0, 1, 2):
+            m.m2s_line_penta(c, r, a)
+        torch.cuda.synchronize()
+        print("profile case line_penta n=%d done" % n)
+        return 0
     f32 = args.profile_case.endswith("32")
     dt = torch.float32 if f32 else torch.float64
     if args.profile_case.startswith("kappa"):
@@ -437,6 +447,36 @@ def other_configs(m, torch, hbm):
                 "parity": "tests/test_gpu_fullsize.py::test_sweep_1536_f64 (sampled sweep "
                           "identity at this size)"}
 
+    def line_penta_162():
+        n, k = 162, 5
+        shape = (n, n, n)
+        pts = n ** 3
+        coefs = [torch.from_numpy(gen.line_penta_inputs(shape, k=k, seed=gen.BASE_SEED + a)[0])
+                 .cuda() for a in range(3)]
+        _, rhs = gen.line_penta_inputs(shape, k=k, seed=gen.BASE_SEED + 3)
+        r = torch.from_numpy(rhs).cuda()
+        work = torch.empty(m.m2s_line_penta_work_bytes(n, n, n) // 8, dtype=torch.float64,
+                           device="cuda")
+        ms = []
+        for a in range(3):
+            ms.append(time_cuda(torch, lambda: m.m2s_line_penta(coefs[a], r, a, work=work),
+                                10, 2) * 1e3)
+        t3 = time_cuda(torch, lambda: [m.m2s_line_penta(coefs[a], r, a, work=work)
+                                       for a in range(3)], 5, 1)
+        ops = (7 + 5 * k) * pts
+        return {"workload": "NPB-SP-shaped line solves 162^3 (class C), k = 5 right-hand sides: "
+                            "pentadiagonal systems along x, y and z lines (diagonally dominant "
+                            "a, e ~ U(-.25,.25), b, d ~ U(-1,1), c ~ U(3,4)), FP64",
+                "ms_x": ms[0], "ms_y": ms[1], "ms_z": ms[2], "ms_xyz": t3 * 1e3,
+                "alg_GBs_per_axis": [120.0 * pts / (t * 1e-3) / 1e9 for t in ms],
+                "alg_bytes_note": "120 B/point per axis solve (read coef, rhs; write v); the "
+                                  "kernel also writes and re-reads y and (1/u, u1, e)",
+                "fp64_op_frac_per_axis": [ops / (t * 1e-3) / FP64_OPS_PEAK for t in ms],
+                "fp64_ops_note": "7 + 5k FP64 operations per point (an FMA is one)",
+                "parity": "tests/test_gpu_lines.py (oracle on ragged shapes; sampled equations "
+                          "at 162^3)"}
+
+    guarded("line_penta_162x5", line_penta_162)
     guarded("symgs_1536", symgs_1536)
     guarded("hpcg_32", cfg1)
     guarded("kappa_256", cfg4)
@@ -498,9 +538,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workload configurations (32^3 SGS-PCG, block SSOR, "
-                         "variable-kappa, batched adjoint)")
+                         "variable-kappa, batched adjoint, line solves, 1536^3 SymGS)")
     ap.add_argument("--profile-case", choices=["sweep64", "sweep32", "spmv64", "spmv32",
-                                               "kappa_sweep64", "block_ssor"],
+                                               "kappa_sweep64", "block_ssor", "line_penta"],
                     help="run a few launches of one kernel for an ncu capture and exit")
     args = ap.parse_args()
     if args.impl == "reference":

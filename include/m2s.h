@@ -180,6 +180,31 @@ m2s_status m2s_pcg_solve(m2s_grid* grid, const double* b, double* x,
                          const m2s_pcg_opts* opts, m2s_pcg_result* out,
                          void* stream);
 
+/* Direct solves of pentadiagonal systems along the grid lines of one axis:
+ * the multi-diagonal direct solves of NPB-SP (paper Sec. 1; Sec. 7.2.2:
+ * along each axis every line is swept forward and backward, the two
+ * sweeps fused per line).  Grid nx, ny, nz, point p = (z*ny + y)*nx + x;
+ * axis 0 = lines along x, 1 = along y, 2 = along z.  Point p at position
+ * i of its line holds the equation
+ *     a v[i-2] + b v[i-1] + c v[i] + d v[i+1] + e v[i+2] = r[i]
+ * with coef[5p .. 5p+4] = (a, b, c, d, e) (device, FP64, [n][5]); terms
+ * outside the line are ignored.  rhs (device, FP64, [n][k], 1 <= k <= 8)
+ * holds k right-hand sides per point and is overwritten with the
+ * solutions.  work: caller-owned device scratch of at least
+ * m2s_line_penta_work_bytes(nx, ny, nz) bytes (3 FP64 values per point);
+ * its contents on return are unspecified.  coef, rhs and work must be
+ * 8-byte aligned and must not overlap.  No allocation, no host
+ * synchronisation: the solve is ordered on `stream`.  Elimination without
+ * pivoting: the caller supplies systems with nonzero pivots (e.g. strictly
+ * diagonally dominant); a zero pivot makes that line's solutions
+ * non-finite (not reported).  Errors: M2S_ERR_INVALID_ARG for bad sizes,
+ * axis, k, NULL, misaligned or overlapping pointers or a short work
+ * buffer; M2S_ERR_CUDA if the launch fails. */
+long long m2s_line_penta_work_bytes(int nx, int ny, int nz);
+m2s_status m2s_line_penta(int nx, int ny, int nz, int axis, const double* coef,
+                          double* rhs, int k, void* work, long long work_bytes,
+                          void* stream);
+
 /* Block SSOR on the BLOCK7_5x5 operator (NPB-LU shape, paper Sec. 1 and
  * Sec. 4.3.3): n_iters times
  *   r = b - A u; lower sweep (D + omega L) v = r; upper sweep

@@ -73,7 +73,7 @@ EXPORTS = (
     "m2s_pcg_solve", "m2s_ssor_sweep", "m2s_adjoint_solve", "m2s_kappa_grad",
     "m2s_set_spin_limit", "m2s_debug_stall_unit", "m2s_symgs_noalloc", "m2s_status_string",
     "m2s_sweep_timing", "m2s_sweep_timing_read", "m2s_set_sweep_warps", "m2s_set_graphs",
-    "m2s_autotune_sweeps",
+    "m2s_autotune_sweeps", "m2s_line_penta", "m2s_line_penta_work_bytes",
 )
 
 
@@ -118,6 +118,8 @@ def load():
         "m2s_autotune_sweeps": ([vp, i, vp, ctypes.POINTER(i)], i),
         "m2s_sweep_timing_read": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(d),
                                    ctypes.POINTER(i)], i),
+        "m2s_line_penta_work_bytes": ([i, i, i], ll),
+        "m2s_line_penta": ([i, i, i, i, vp, vp, i, vp, ll, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -305,6 +307,29 @@ def m2s_pcg_solve(grid, b, x, max_iters=50, rtol=0.0, fixed_iters=True, check_ev
     if raise_on_error and st not in (Status.OK, Status.NOT_CONVERGED):
         raise M2SError(st, "m2s_pcg_solve")
     return Status(st), res
+
+
+def m2s_line_penta_work_bytes(nx, ny, nz):
+    return int(load().m2s_line_penta_work_bytes(int(nx), int(ny), int(nz)))
+
+
+def m2s_line_penta(coef, rhs, axis, work=None, stream=None):
+    """Pentadiagonal solves along the lines of `axis` (0 = x, 1 = y, 2 = z):
+    coef (nz, ny, nx, 5) FP64 CUDA tensor of (a, b, c, d, e) per point, rhs
+    (nz, ny, nx, k) FP64 CUDA tensor, overwritten with the solutions.  work:
+    a CUDA tensor of at least m2s_line_penta_work_bytes bytes, or None (a
+    scratch tensor is made with torch)."""
+    nz, ny, nx, k = rhs.shape
+    if tuple(coef.shape) != (nz, ny, nx, 5):
+        raise M2SError(Status.INVALID_ARG, "m2s_line_penta: coef shape")
+    need = m2s_line_penta_work_bytes(nx, ny, nz)
+    if work is None:
+        import torch
+        work = torch.empty(need // 8, dtype=torch.float64, device=rhs.device)
+    nbytes = work.numel() * work.element_size()
+    return _check(load().m2s_line_penta(nx, ny, nz, int(axis), _ptr(coef, "coef"),
+                                        _ptr(rhs, "rhs"), int(k), _ptr(work, "work"), nbytes,
+                                        _stream(stream)), "m2s_line_penta")
 
 
 def m2s_ssor_sweep(grid, b, u, omega=1.2, n_iters=1, stream=None):

@@ -1056,6 +1056,32 @@ m2s_status m2s_adjoint_solve(m2s_grid* g, const double* u, const double* dLdu, d
     return s;
 }
 
+long long m2s_line_penta_work_bytes(int nx, int ny, int nz) {
+    if (nx < 1 || ny < 1 || nz < 1) return 0;
+    return line_penta_work_doubles(nx, ny, nz) * (long long)sizeof(double);
+}
+
+m2s_status m2s_line_penta(int nx, int ny, int nz, int axis, const double* coef, double* rhs,
+                          int k, void* work, long long work_bytes, void* stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || axis < 0 || axis > 2 || k < 1 || k > 8)
+        return M2S_ERR_INVALID_ARG;
+    if ((i64)nx * ny * nz > (1LL << 34)) return M2S_ERR_INVALID_ARG;
+    if (!coef || !rhs || !work || !aligned(coef, 8) || !aligned(rhs, 8) || !aligned(work, 8))
+        return M2S_ERR_INVALID_ARG;
+    if (work_bytes < m2s_line_penta_work_bytes(nx, ny, nz)) return M2S_ERR_INVALID_ARG;
+    const i64 n = (i64)nx * ny * nz;
+    // the three arrays must not overlap
+    auto disjoint = [](const void* a, i64 na, const void* b, i64 nb) {
+        const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+        return x + (uintptr_t)na <= y || y + (uintptr_t)nb <= x;
+    };
+    const i64 bc = 5 * n * 8, br = (i64)k * n * 8, bw = line_penta_work_doubles(nx, ny, nz) * 8;
+    if (!disjoint(coef, bc, rhs, br) || !disjoint(coef, bc, work, bw) || !disjoint(rhs, br, work, bw))
+        return M2S_ERR_INVALID_ARG;
+    M2S_TRY(launch_line_penta(nx, ny, nz, axis, coef, rhs, k, (double*)work, S(stream)));
+    return M2S_OK;
+}
+
 m2s_status m2s_ssor_sweep(m2s_grid* g, const double* b, double* u, double omega, int n_iters,
                           void* stream) {
     if (!g || !b || !u || b == u || g->op != M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;

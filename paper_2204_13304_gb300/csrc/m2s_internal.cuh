@@ -186,5 +186,10 @@ cudaError_t launch_gs27_cta(const WaveUnits& u, const WaveCall& c, const T* Qin,
                             const T* b, T* x, cudaStream_t st);
 void free_wave_units(WaveUnits* u);
 
+// Pentadiagonal line solves (k_line.cu): FP64 values of the work array.
+i64 line_penta_work_doubles(int nx, int ny, int nz);
+cudaError_t launch_line_penta(int nx, int ny, int nz, int axis, const double* coef, double* rhs,
+                              int k, double* work, cudaStream_t st);
+
 
 }  // namespace m2s

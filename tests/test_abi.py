@@ -74,3 +74,28 @@ def test_library_is_sm103a_only():
     from paper_2204_13304_gb300 import build as b
     assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
     assert "--use_fast_math" not in b.FLAGS
+
+
+def test_line_penta_rejects_invalid_arguments_without_gpu(lib):
+    """Every rejected call returns before any CUDA call, so fake (never
+    dereferenced) device addresses suffice."""
+    import paper_2204_13304_gb300 as m
+    nx, ny, nz, k = 4, 5, 6, 5
+    n = nx * ny * nz
+    need = lib.m2s_line_penta_work_bytes(nx, ny, nz)
+    assert need == 3 * n * 8
+    assert lib.m2s_line_penta_work_bytes(0, 5, 6) == 0
+    coef, rhs, work = 1 << 20, 1 << 24, 1 << 28  # disjoint, 8-byte aligned
+    bad = [
+        (0, ny, nz, 0, coef, rhs, k, work, need),        # empty grid
+        (nx, ny, nz, 3, coef, rhs, k, work, need),       # axis
+        (nx, ny, nz, 0, coef, rhs, 0, work, need),       # k too small
+        (nx, ny, nz, 0, coef, rhs, 9, work, need),       # k too large
+        (nx, ny, nz, 0, None, rhs, k, work, need),       # NULL
+        (nx, ny, nz, 0, coef + 4, rhs, k, work, need),   # misaligned
+        (nx, ny, nz, 0, coef, rhs, k, work, need - 8),   # short work buffer
+        (nx, ny, nz, 0, coef, coef + 8, k, work, need),  # rhs overlaps coef
+        (nx, ny, nz, 0, coef, rhs, k, rhs + 8 * n, need),  # work overlaps rhs
+    ]
+    for a in bad:
+        assert lib.m2s_line_penta(*a[:8], ctypes.c_longlong(a[8]), None) == m.Status.INVALID_ARG, a
