@@ -24,6 +24,9 @@ Workload recipes (shapes of the paper's benchmarks, Sec. 7.1):
     with a, e ~ U(-0.25, 0.25), b, d ~ U(-1, 1), c ~ U(3, 4) (strictly
     diagonally dominant, so elimination needs no pivoting) and k = 5
     right-hand sides ~ U(-1, 1).
+  * NPB-BT-shaped line solves: per point 5x5 blocks B = U(-1,1) + 10 I and
+    A, C ~ U(-0.25, 0.25) (row sums of the off-diagonal magnitudes <= 6.5 <
+    9 <= |B_jj|: strictly diagonally dominant), rhs ~ U(-1, 1).
 """
 import numpy as np
 
@@ -43,6 +46,8 @@ STREAM_VEC = 7
 STREAM_SIDES = 8
 STREAM_PENTA = 9
 STREAM_PENTA_RHS = 10
+STREAM_BTRI = 11
+STREAM_BTRI_RHS = 12
 
 BATCH_SIDES = (32, 48, 64, 96, 128)
 
@@ -151,3 +156,15 @@ def line_penta_inputs(shape, k=5, seed=BASE_SEED):
     coef = u * scale + shift
     rhs = (2.0 * uniform(seed, STREAM_PENTA_RHS, npts * k) - 1.0).reshape(shape + (k,))
     return coef, rhs
+
+
+def line_btri_inputs(shape, seed=BASE_SEED):
+    """(blk, rhs) of the NPB-BT-shaped line solves: blk (nz, ny, nx, 3, 5, 5)
+    = (A, B, C) per point, rhs (nz, ny, nx, 5)."""
+    shape = tuple(shape)
+    npts = int(np.prod(shape))
+    u = uniform(seed, STREAM_BTRI, npts * 75).reshape(shape + (3, 5, 5))
+    blk = 0.5 * u - 0.25
+    blk[..., 1, :, :] = 2.0 * u[..., 1, :, :] - 1.0 + 10.0 * np.eye(5)
+    rhs = (2.0 * uniform(seed, STREAM_BTRI_RHS, npts * 5) - 1.0).reshape(shape + (5,))
+    return blk, rhs

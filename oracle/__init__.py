@@ -58,6 +58,7 @@ def lib():
             "or_block_upper": [_i, _i, _i, _dp, _dp, _d, _dp, _dp],
             "or_ssor": [_i, _i, _i, _dp, _dp, _dp, _d, _dp, _dp, _i],
             "or_line_penta": [_i, _i, _i, _i, _dp, _dp, _i],
+            "or_line_btri": [_i, _i, _i, _i, _dp, _dp],
             "or_coarse_n": [_i],
             "or_abi_version": [],
         }
@@ -282,4 +283,18 @@ def line_penta(coef, rhs, axis):
     nz, ny, nx, k = v.shape
     assert coef.shape == (nz, ny, nx, 5)
     lib().or_line_penta(nx, ny, nz, int(axis), _p(coef), _p(v), int(k))
+    return v
+
+
+def line_btri(blk, rhs, axis):
+    """Solutions of the 5x5 block-tridiagonal systems along the lines of
+    `axis`: blk (nz, ny, nx, 3, 5, 5) = (A, B, C) of
+    A v_{i-1} + B v_i + C v_{i+1} = r_i at each point (A of a line's first
+    point and C of its last dropped), rhs (nz, ny, nx, 5) (NPB-BT's direct
+    solves)."""
+    blk = _f64(blk)
+    v = _f64(rhs).copy()
+    nz, ny, nx, _ = v.shape
+    assert blk.shape == (nz, ny, nx, 3, 5, 5) and v.shape[3] == 5
+    lib().or_line_btri(nx, ny, nz, int(axis), _p(blk), _p(v))
     return v

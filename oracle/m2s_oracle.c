@@ -759,4 +759,69 @@ void or_line_penta(int nx, int ny, int nz, int axis, const double* coef,
     free(R);
 }
 
+/* Block-tridiagonal systems along grid lines (NPB-BT's direct solves, the  */
+/* 5x5-block counterpart of the above): point p at position i of its line  */
+/* holds  A v_{i-1} + B v_i + C v_{i+1} = r_i  with 5x5 blocks             */
+/* blk[p][0] = A, blk[p][1] = B, blk[p][2] = C (row-major, entry (r, c) at */
+/* r*5 + c) and 5-vectors; A of the first and C of the last point of a     */
+/* line are dropped.  rhs[p][0..4] is overwritten with v.  The oracle is    */
+/* Gaussian elimination without pivoting on each line's dense 5m x 5m      */
+/* matrix restricted to its band: every pivot column eliminates the rows   */
+/* below it within the next block row, then back substitution.             */
+void or_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* rhs) {
+    const int ext[3] = {nx, ny, nz};
+    const i64 stride[3] = {1, nx, (i64)nx * ny};
+    const int m = ext[axis];
+    const int o1 = axis == 0 ? 1 : 0, o2 = axis == 2 ? 1 : 2;
+    const int N = 5 * m;
+    /* band storage: row R holds columns R-9 .. R+9 (the widest a block row
+       reaches), W[R][c - R + 9] */
+    const int BW = 19;
+    double* W = (double*)malloc(sizeof(double) * (size_t)BW * (size_t)(N > 0 ? N : 1));
+    double* R = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    for (int c2 = 0; c2 < ext[o2]; ++c2)
+        for (int c1 = 0; c1 < ext[o1]; ++c1) {
+            const i64 base = (i64)c1 * stride[o1] + (i64)c2 * stride[o2];
+            memset(W, 0, sizeof(double) * (size_t)BW * (size_t)N);
+            for (int i = 0; i < m; ++i) {
+                const i64 p = base + (i64)i * stride[axis];
+                for (int r = 0; r < 5; ++r) {
+                    const int row = 5 * i + r;
+                    for (int b = 0; b < 3; ++b) {
+                        const int bi = i + b - 1; /* block column */
+                        if (bi < 0 || bi >= m) continue;
+                        for (int c = 0; c < 5; ++c)
+                            W[(size_t)BW * row + (5 * bi + c) - row + 9] = blk[75 * p + 25 * b + 5 * r + c];
+                    }
+                    R[row] = rhs[5 * p + r];
+                }
+            }
+            /* elimination: pivot column k clears rows k+1 .. min(k+9, N-1) */
+            for (int k = 0; k < N; ++k) {
+                const double piv = W[(size_t)BW * k + 9];
+                for (int row = k + 1; row <= k + 9 && row < N; ++row) {
+                    const double f = W[(size_t)BW * row + k - row + 9] / piv;
+                    if (f == 0.0) continue;
+                    for (int c = k; c <= k + 9 && c < N; ++c) {
+                        const int jr = c - row + 9;
+                        if (jr < 0 || jr >= BW) continue;
+                        W[(size_t)BW * row + jr] -= f * W[(size_t)BW * k + c - k + 9];
+                    }
+                    R[row] -= f * R[k];
+                }
+            }
+            for (int k = N - 1; k >= 0; --k) {
+                double s = R[k];
+                for (int c = k + 1; c <= k + 9 && c < N; ++c) s -= W[(size_t)BW * k + c - k + 9] * R[c];
+                R[k] = s / W[(size_t)BW * k + 9];
+            }
+            for (int i = 0; i < m; ++i) {
+                const i64 p = base + (i64)i * stride[axis];
+                for (int r = 0; r < 5; ++r) rhs[5 * p + r] = R[5 * i + r];
+            }
+        }
+    free(W);
+    free(R);
+}
+
 int or_abi_version(void) { return 1; }

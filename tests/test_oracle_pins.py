@@ -655,3 +655,67 @@ def test_line_penta_axis_permutation():
     ct = np.ascontiguousarray(np.transpose(coef, (0, 2, 1, 3)))
     rt = np.ascontiguousarray(np.transpose(rhs, (0, 2, 1, 3)))
     assert np.array_equal(vy, np.transpose(oracle.line_penta(ct, rt, 0), (0, 2, 1, 3)))
+
+
+# ---------------------------------------------------------------------------
+# NPB-BT-shaped line solves: 5x5 block-tridiagonal systems along the lines
+# of one axis.
+# ---------------------------------------------------------------------------
+def _btri_dense(blk, axis):
+    b = np.moveaxis(blk, 2 - axis, 2)
+    m = b.shape[2]
+    mats = {}
+    for i0 in range(b.shape[0]):
+        for i1 in range(b.shape[1]):
+            A = np.zeros((5 * m, 5 * m))
+            for i in range(m):
+                for k, off in enumerate((-1, 0, 1)):
+                    j = i + off
+                    if 0 <= j < m:
+                        A[5 * i:5 * i + 5, 5 * j:5 * j + 5] = b[i0, i1, i, k]
+            mats[(i0, i1)] = A
+    return mats
+
+
+@pytest.mark.parametrize("shape", LINE_SHAPES)
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_line_btri_matches_dense_solves(shape, axis):
+    blk, rhs = gen.line_btri_inputs(shape, seed=gen.BASE_SEED + 35)
+    v = oracle.line_btri(blk, rhs, axis)
+    r = np.moveaxis(rhs, 2 - axis, 2)
+    vv = np.moveaxis(v, 2 - axis, 2)
+    for (i0, i1), A in _btri_dense(blk, axis).items():
+        ref = np.linalg.solve(A, r[i0, i1].ravel())
+        assert np.max(np.abs(vv[i0, i1].ravel() - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+        assert np.max(np.abs(A @ vv[i0, i1].ravel() - r[i0, i1].ravel())) <= 1e-13
+
+
+def test_line_btri_diagonal_blocks_reduce_to_tridiagonal():
+    """Blocks that are multiples of the identity decouple the 5 components
+    into 5 scalar tridiagonal systems (scipy's banded solver)."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    shape = (3, 2, 8)
+    rng = np.random.default_rng(5)
+    s = rng.uniform(-0.25, 0.25, size=shape + (3,))
+    s[..., 1] += 3.0
+    blk = s[..., :, None, None] * np.eye(5)
+    _, rhs = gen.line_btri_inputs(shape, seed=gen.BASE_SEED + 36)
+    v = oracle.line_btri(blk, rhs, 0)
+    for z in range(shape[0]):
+        for y in range(shape[1]):
+            ab = np.zeros((3, shape[2]))
+            ab[0, 1:] = s[z, y, :-1, 2]
+            ab[1, :] = s[z, y, :, 1]
+            ab[2, :-1] = s[z, y, 1:, 0]
+            for c in range(5):
+                ref = scipy_linalg.solve_banded((1, 1), ab, rhs[z, y, :, c])
+                assert np.max(np.abs(v[z, y, :, c] - ref)) <= 1e-13
+
+
+def test_line_btri_axis_permutation():
+    shape = (3, 4, 6)
+    blk, rhs = gen.line_btri_inputs(shape, seed=gen.BASE_SEED + 37)
+    vx = oracle.line_btri(blk, rhs, 0)
+    bt = np.ascontiguousarray(np.transpose(blk, (2, 1, 0, 3, 4, 5)))
+    rt = np.ascontiguousarray(np.transpose(rhs, (2, 1, 0, 3)))
+    assert np.array_equal(vx, np.transpose(oracle.line_btri(bt, rt, 2), (2, 1, 0, 3)))
