@@ -222,6 +222,16 @@ def profile_case(args):
         g.close()
         print("profile case block_ssor n=%d done" % n)
         return 0
+    if args.profile_case == "line_btri":
+        import m2s_inputs as gen
+        blk, rhs = gen.line_btri_inputs(shape)
+        b = torch.from_numpy(blk).cuda()
+        r = torch.from_numpy(rhs).cuda()
+        for a in (0, 1, 2):
+            m.m2s_line_btri(b, r, a)
+        torch.cuda.synchronize()
+        print("profile case line_btri n=%d done" % n)
+        return 0
     if args.profile_case == "line_penta":
         import m2s_inputs as gen
         coef, rhs = gen.line_penta_inputs(shape, k=5)
@@ -476,7 +486,40 @@ def other_configs(m, torch, hbm):
                 "parity": "tests/test_gpu_lines.py (oracle on ragged shapes; sampled equations "
                           "at 162^3)"}
 
+    def line_btri_162():
+        n = 162
+        shape = (n, n, n)
+        pts = n ** 3
+        blks = []
+        for a in range(3):
+            blk, rhs = gen.line_btri_inputs(shape, seed=gen.BASE_SEED + a)
+            blks.append(torch.from_numpy(blk).cuda())
+            del blk
+        r = torch.from_numpy(rhs).cuda()
+        work = torch.empty(m.m2s_line_btri_work_bytes(n, n, n) // 8, dtype=torch.float64,
+                           device="cuda")
+        ms = []
+        for a in range(3):
+            ms.append(time_cuda(torch, lambda: m.m2s_line_btri(blks[a], r, a, work=work), 5, 1)
+                      * 1e3)
+        ops = 375.0 * pts
+        out_ = {"workload": "NPB-BT-shaped line solves 162^3 (class C): 5x5 block-tridiagonal "
+                            "systems along x, y and z lines (B = U(-1,1) + 10 I, A, C ~ "
+                            "U(-.25,.25)), 5 unknowns per point, FP64",
+                "ms_x": ms[0], "ms_y": ms[1], "ms_z": ms[2],
+                "alg_GBs_per_axis": [680.0 * pts / (t * 1e-3) / 1e9 for t in ms],
+                "alg_bytes_note": "680 B/point per axis solve (read A, B, C, r; write v); the "
+                                  "kernel also writes and re-reads C^ and r^",
+                "fp64_op_frac_per_axis": [ops / (t * 1e-3) / FP64_OPS_PEAK for t in ms],
+                "fp64_ops_note": "~375 FP64 operations per point (an FMA is one)",
+                "parity": "tests/test_gpu_lines.py (oracle on ragged shapes; sampled equations "
+                          "at 162^3)"}
+        del blks, r, work
+        torch.cuda.empty_cache()
+        return out_
+
     guarded("line_penta_162x5", line_penta_162)
+    guarded("line_btri_162x5", line_btri_162)
     guarded("symgs_1536", symgs_1536)
     guarded("hpcg_32", cfg1)
     guarded("kappa_256", cfg4)
@@ -540,7 +583,8 @@ def main():
                     help="skip the other workload configurations (32^3 SGS-PCG, block SSOR, "
                          "variable-kappa, batched adjoint, line solves, 1536^3 SymGS)")
     ap.add_argument("--profile-case", choices=["sweep64", "sweep32", "spmv64", "spmv32",
-                                               "kappa_sweep64", "block_ssor", "line_penta"],
+                                               "kappa_sweep64", "block_ssor", "line_penta",
+                                               "line_btri"],
                     help="run a few launches of one kernel for an ncu capture and exit")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -205,6 +205,26 @@ m2s_status m2s_line_penta(int nx, int ny, int nz, int axis, const double* coef,
                           double* rhs, int k, void* work, long long work_bytes,
                           void* stream);
 
+/* Direct solves of 5x5 block-tridiagonal systems along the grid lines of
+ * one axis: the multi-diagonal direct solves of NPB-BT (paper Sec. 1, Sec.
+ * 7.2.2).  Point p at position i of its line holds
+ *     A v[i-1] + B v[i] + C v[i+1] = r[i]
+ * with blk[75p .. 75p+74] = (A, B, C), each 5x5 row-major (entry (r, c)
+ * at r*5 + c) (device, FP64, [n][3][5][5]); A of the first and C of the
+ * last point of a line are ignored.  rhs (device, FP64, [n][5]) is
+ * overwritten with v.  work: caller-owned device scratch of at least
+ * m2s_line_btri_work_bytes(nx, ny, nz) bytes (25 FP64 values per point;
+ * contents on return unspecified).  Block elimination without pivoting:
+ * the caller supplies systems whose pivots are nonzero (e.g. strictly
+ * block diagonally dominant); otherwise that line's solutions are
+ * non-finite (not reported).  Axis, layout, alignment, no-overlap,
+ * stream-ordering and error rules as m2s_line_penta; at most 2^32
+ * points. */
+long long m2s_line_btri_work_bytes(int nx, int ny, int nz);
+m2s_status m2s_line_btri(int nx, int ny, int nz, int axis, const double* blk,
+                         double* rhs, void* work, long long work_bytes,
+                         void* stream);
+
 /* Block SSOR on the BLOCK7_5x5 operator (NPB-LU shape, paper Sec. 1 and
  * Sec. 4.3.3): n_iters times
  *   r = b - A u; lower sweep (D + omega L) v = r; upper sweep

@@ -73,7 +73,8 @@ EXPORTS = (
     "m2s_pcg_solve", "m2s_ssor_sweep", "m2s_adjoint_solve", "m2s_kappa_grad",
     "m2s_set_spin_limit", "m2s_debug_stall_unit", "m2s_symgs_noalloc", "m2s_status_string",
     "m2s_sweep_timing", "m2s_sweep_timing_read", "m2s_set_sweep_warps", "m2s_set_graphs",
-    "m2s_autotune_sweeps", "m2s_line_penta", "m2s_line_penta_work_bytes",
+    "m2s_autotune_sweeps", "m2s_line_penta", "m2s_line_penta_work_bytes", "m2s_line_btri",
+    "m2s_line_btri_work_bytes",
 )
 
 
@@ -120,6 +121,8 @@ def load():
                                    ctypes.POINTER(i)], i),
         "m2s_line_penta_work_bytes": ([i, i, i], ll),
         "m2s_line_penta": ([i, i, i, i, vp, vp, i, vp, ll, vp], i),
+        "m2s_line_btri_work_bytes": ([i, i, i], ll),
+        "m2s_line_btri": ([i, i, i, i, vp, vp, vp, ll, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -330,6 +333,28 @@ def m2s_line_penta(coef, rhs, axis, work=None, stream=None):
     return _check(load().m2s_line_penta(nx, ny, nz, int(axis), _ptr(coef, "coef"),
                                         _ptr(rhs, "rhs"), int(k), _ptr(work, "work"), nbytes,
                                         _stream(stream)), "m2s_line_penta")
+
+
+def m2s_line_btri_work_bytes(nx, ny, nz):
+    return int(load().m2s_line_btri_work_bytes(int(nx), int(ny), int(nz)))
+
+
+def m2s_line_btri(blk, rhs, axis, work=None, stream=None):
+    """5x5 block-tridiagonal solves along the lines of `axis`: blk
+    (nz, ny, nx, 3, 5, 5) FP64 CUDA tensor of (A, B, C) per point, rhs
+    (nz, ny, nx, 5) FP64 CUDA tensor, overwritten with the solutions.  work:
+    a CUDA tensor of at least m2s_line_btri_work_bytes bytes, or None."""
+    nz, ny, nx, five = rhs.shape
+    if five != 5 or tuple(blk.shape) != (nz, ny, nx, 3, 5, 5):
+        raise M2SError(Status.INVALID_ARG, "m2s_line_btri: shapes")
+    need = m2s_line_btri_work_bytes(nx, ny, nz)
+    if work is None:
+        import torch
+        work = torch.empty(need // 8, dtype=torch.float64, device=rhs.device)
+    nbytes = work.numel() * work.element_size()
+    return _check(load().m2s_line_btri(nx, ny, nz, int(axis), _ptr(blk, "blk"), _ptr(rhs, "rhs"),
+                                       _ptr(work, "work"), nbytes, _stream(stream)),
+                  "m2s_line_btri")
 
 
 def m2s_ssor_sweep(grid, b, u, omega=1.2, n_iters=1, stream=None):

@@ -40,33 +40,40 @@ constexpr int LD = 4;    // points of a line in flight ahead of the one computed
 struct LineArgs {
     int nx, ny, nz, axis;
     i64 n;
-    const double* coef;  // [n][5]
+    const double* coef;  // pentadiagonal: [n][5]; block-tridiagonal: [n][3][25]
     double* rhs;         // [n][K]
-    double* work;        // [3][n]: 1/u, u1, e
+    double* work;        // pentadiagonal: [3][n] (1/u, u1, e); block: [n][25] (C^)
 };
+
+// Line t of the launch: its first point, the point stride along it and its
+// length.  Lines of the y and z axes are numbered with x fastest, so that
+// neighbouring threads hold neighbouring x.
+__device__ __forceinline__ bool line_of(const LineArgs& a, i64 t, i64* base, i64* stride, int* m) {
+    if (a.axis == 0) {  // lines along x: one per (y, z)
+        if (t >= (i64)a.ny * a.nz) return false;
+        *base = t * a.nx;
+        *stride = 1;
+        *m = a.nx;
+    } else if (a.axis == 1) {  // along y: one per (x, z)
+        if (t >= (i64)a.nx * a.nz) return false;
+        const i64 z = t / a.nx, x = t - z * a.nx;
+        *base = z * a.nx * a.ny + x;
+        *stride = a.nx;
+        *m = a.ny;
+    } else {  // along z: one per (x, y)
+        if (t >= (i64)a.nx * a.ny) return false;
+        *base = t;
+        *stride = (i64)a.nx * a.ny;
+        *m = a.nz;
+    }
+    return true;
+}
 
 template <int K>
 __global__ void __launch_bounds__(LB) line_penta_kernel(LineArgs a) {
-    const i64 t = blockIdx.x * (i64)LB + threadIdx.x;
     i64 base, stride;
     int m;
-    if (a.axis == 0) {  // lines along x: one per (y, z)
-        if (t >= (i64)a.ny * a.nz) return;
-        base = t * a.nx;
-        stride = 1;
-        m = a.nx;
-    } else if (a.axis == 1) {  // along y: one per (x, z)
-        if (t >= (i64)a.nx * a.nz) return;
-        const i64 z = t / a.nx, x = t - z * a.nx;
-        base = z * a.nx * a.ny + x;
-        stride = a.nx;
-        m = a.ny;
-    } else {  // along z: one per (x, y)
-        if (t >= (i64)a.nx * a.ny) return;
-        base = t;
-        stride = (i64)a.nx * a.ny;
-        m = a.nz;
-    }
+    if (!line_of(a, blockIdx.x * (i64)LB + threadIdx.x, &base, &stride, &m)) return;
     const double* __restrict__ coef = a.coef;
     double* __restrict__ rhs = a.rhs;
     double* __restrict__ w_inv = a.work;
@@ -176,6 +183,116 @@ __global__ void __launch_bounds__(LB) line_penta_kernel(LineArgs a) {
     }
 }
 
+// Block-tridiagonal lines (NPB-BT shape): A v_{i-1} + B v_i + C v_{i+1} = r_i
+// with 5x5 blocks.  One thread per line runs block elimination without
+// pivoting, forward
+//   B'_i = B_i - A_i C^_{i-1},  r'_i = r_i - A_i r^_{i-1},
+//   [C^_i | r^_i] = B'_i^{-1} [C_i | r'_i]   (Gaussian elimination of B'_i),
+// with C^_{i-1} and r^_{i-1} in registers, C^_i stored to the work array and
+// r^_i to rhs; backward v_i = r^_i - C^_i v_{i+1}.  About 375 FP64
+// operations per point against ~1.2 KB: FP64-bound on GB300.
+__global__ void __launch_bounds__(LB) line_btri_kernel(LineArgs a) {
+    i64 base, stride;
+    int m;
+    if (!line_of(a, blockIdx.x * (i64)LB + threadIdx.x, &base, &stride, &m)) return;
+    const double* __restrict__ blk = a.coef;
+    double* __restrict__ rhs = a.rhs;
+    double* __restrict__ ch = a.work;
+    double cp[25], rp[5];  // C^ and r^ of the previous point
+#pragma unroll
+    for (int j = 0; j < 25; ++j) cp[j] = 0.0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) rp[j] = 0.0;
+    i64 p = base;
+    for (int i = 0; i < m; ++i, p += stride) {
+        const double* bp = blk + 75 * p;
+        double B[25], r[5];
+#pragma unroll
+        for (int j = 0; j < 25; ++j) B[j] = __ldg(bp + 25 + j);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) r[j] = rhs[5 * p + j];
+        if (i > 0) {
+            double A[25];
+#pragma unroll
+            for (int j = 0; j < 25; ++j) A[j] = __ldg(bp + j);
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+#pragma unroll
+                for (int l = 0; l < 5; ++l) {
+                    const double ajl = A[5 * j + l];
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) B[5 * j + c] = fma(-ajl, cp[5 * l + c], B[5 * j + c]);
+                    r[j] = fma(-ajl, rp[l], r[j]);
+                }
+            }
+        }
+        // X = [C | r'], eliminated with B' below
+        double X[30];
+        const bool last = i + 1 == m;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) X[6 * j + c] = last ? 0.0 : __ldg(bp + 50 + 5 * j + c);
+            X[6 * j + 5] = r[j];
+        }
+        double piv[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            piv[k] = __drcp_rn(B[5 * k + k]);
+#pragma unroll
+            for (int j = k + 1; j < 5; ++j) {
+                const double f = B[5 * j + k] * piv[k];
+#pragma unroll
+                for (int c = k + 1; c < 5; ++c) B[5 * j + c] = fma(-f, B[5 * k + c], B[5 * j + c]);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) X[6 * j + c] = fma(-f, X[6 * k + c], X[6 * j + c]);
+            }
+        }
+#pragma unroll
+        for (int k = 4; k >= 0; --k) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                double sum = X[6 * k + c];
+#pragma unroll
+                for (int l = k + 1; l < 5; ++l) sum = fma(-B[5 * k + l], X[6 * l + c], sum);
+                X[6 * k + c] = sum * piv[k];
+            }
+        }
+        double* cw = ch + 25 * p;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                cp[5 * j + c] = X[6 * j + c];
+                cw[5 * j + c] = X[6 * j + c];
+            }
+            rp[j] = X[6 * j + 5];
+            rhs[5 * p + j] = rp[j];
+        }
+    }
+    // backward
+    double v[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) v[j] = 0.0;
+    p = base + (i64)(m - 1) * stride;
+    for (int i = m - 1; i >= 0; --i, p -= stride) {
+        const double* cw = ch + 25 * p;
+        double nv[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            double sum = rhs[5 * p + j];
+#pragma unroll
+            for (int l = 0; l < 5; ++l) sum = fma(-cw[5 * j + l], v[l], sum);
+            nv[j] = sum;
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            v[j] = nv[j];
+            rhs[5 * p + j] = nv[j];
+        }
+    }
+}
+
 template <int K>
 void launch_k(const LineArgs& a, i64 lines, cudaStream_t st) {
     const unsigned grid = (unsigned)((lines + LB - 1) / LB);
@@ -185,6 +302,24 @@ void launch_k(const LineArgs& a, i64 lines, cudaStream_t st) {
 }  // namespace
 
 i64 line_penta_work_doubles(int nx, int ny, int nz) { return 3LL * nx * ny * nz; }
+i64 line_btri_work_doubles(int nx, int ny, int nz) { return 25LL * nx * ny * nz; }
+
+cudaError_t launch_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* rhs,
+                             double* work, cudaStream_t st) {
+    LineArgs a;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.axis = axis;
+    a.n = (i64)nx * ny * nz;
+    a.coef = blk;
+    a.rhs = rhs;
+    a.work = work;
+    const i64 lines = axis == 0 ? (i64)ny * nz : axis == 1 ? (i64)nx * nz : (i64)nx * ny;
+    if (lines == 0) return cudaSuccess;
+    line_btri_kernel<<<(unsigned)((lines + LB - 1) / LB), LB, 0, st>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_line_penta(int nx, int ny, int nz, int axis, const double* coef, double* rhs,
                               int k, double* work, cudaStream_t st) {

@@ -1082,6 +1082,30 @@ m2s_status m2s_line_penta(int nx, int ny, int nz, int axis, const double* coef, 
     return M2S_OK;
 }
 
+long long m2s_line_btri_work_bytes(int nx, int ny, int nz) {
+    if (nx < 1 || ny < 1 || nz < 1) return 0;
+    return line_btri_work_doubles(nx, ny, nz) * (long long)sizeof(double);
+}
+
+m2s_status m2s_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* rhs,
+                         void* work, long long work_bytes, void* stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || axis < 0 || axis > 2) return M2S_ERR_INVALID_ARG;
+    if ((i64)nx * ny * nz > (1LL << 32)) return M2S_ERR_INVALID_ARG;
+    if (!blk || !rhs || !work || !aligned(blk, 8) || !aligned(rhs, 8) || !aligned(work, 8))
+        return M2S_ERR_INVALID_ARG;
+    if (work_bytes < m2s_line_btri_work_bytes(nx, ny, nz)) return M2S_ERR_INVALID_ARG;
+    const i64 n = (i64)nx * ny * nz;
+    auto disjoint = [](const void* a, i64 na, const void* b, i64 nb) {
+        const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+        return x + (uintptr_t)na <= y || y + (uintptr_t)nb <= x;
+    };
+    const i64 bb = 75 * n * 8, br = 5 * n * 8, bw = line_btri_work_doubles(nx, ny, nz) * 8;
+    if (!disjoint(blk, bb, rhs, br) || !disjoint(blk, bb, work, bw) || !disjoint(rhs, br, work, bw))
+        return M2S_ERR_INVALID_ARG;
+    M2S_TRY(launch_line_btri(nx, ny, nz, axis, blk, rhs, (double*)work, S(stream)));
+    return M2S_OK;
+}
+
 m2s_status m2s_ssor_sweep(m2s_grid* g, const double* b, double* u, double omega, int n_iters,
                           void* stream) {
     if (!g || !b || !u || b == u || g->op != M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;

@@ -190,6 +190,10 @@ void free_wave_units(WaveUnits* u);
 i64 line_penta_work_doubles(int nx, int ny, int nz);
 cudaError_t launch_line_penta(int nx, int ny, int nz, int axis, const double* coef, double* rhs,
                               int k, double* work, cudaStream_t st);
+// Block-tridiagonal (5x5) line solves (k_line.cu).
+i64 line_btri_work_doubles(int nx, int ny, int nz);
+cudaError_t launch_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* rhs,
+                             double* work, cudaStream_t st);
 
 
 }  // namespace m2s

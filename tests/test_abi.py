@@ -99,3 +99,22 @@ def test_line_penta_rejects_invalid_arguments_without_gpu(lib):
     ]
     for a in bad:
         assert lib.m2s_line_penta(*a[:8], ctypes.c_longlong(a[8]), None) == m.Status.INVALID_ARG, a
+
+
+def test_line_btri_rejects_invalid_arguments_without_gpu(lib):
+    import paper_2204_13304_gb300 as m
+    nx, ny, nz = 4, 5, 6
+    n = nx * ny * nz
+    need = lib.m2s_line_btri_work_bytes(nx, ny, nz)
+    assert need == 25 * n * 8
+    blk, rhs, work = 1 << 20, 1 << 24, 1 << 28
+    bad = [
+        (nx, 0, nz, 1, blk, rhs, work, need),
+        (nx, ny, nz, -1, blk, rhs, work, need),
+        (nx, ny, nz, 1, blk, None, work, need),
+        (nx, ny, nz, 1, blk, rhs + 2, work, need),
+        (nx, ny, nz, 1, blk, rhs, work, need - 1),
+        (nx, ny, nz, 1, blk, blk + 8, work, need),
+    ]
+    for a in bad:
+        assert lib.m2s_line_btri(*a[:7], ctypes.c_longlong(a[7]), None) == m.Status.INVALID_ARG, a

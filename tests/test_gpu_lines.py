@@ -105,3 +105,60 @@ def test_line_penta_162_sampled_equations(m, inputs_162, axis):
         res += term
         mag += term.abs()
     assert float((res.abs() / mag).max()) <= 1e-13
+
+
+# ---------------------------------------------------------------------------
+# NPB-BT-shaped 5x5 block-tridiagonal line solves.  The blocks are strictly
+# diagonally dominant (|B_jj| >= 9 > 6.5 >= the off-diagonal row sums), so
+# block elimination without pivoting is stable and the GPU (reciprocal
+# multiplications, fused multiply-adds, block order) and the oracle (scalar
+# banded elimination, divisions) agree to a few ulps: 1e-13 per entry
+# against max(|o_i|, 1e-2 |o|_inf).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_line_btri_matches_oracle(m, shape, axis):
+    import torch
+    blk, rhs = gen.line_btri_inputs(shape, seed=gen.BASE_SEED + 80)
+    want = oracle.line_btri(blk, rhs, axis)
+    b = torch.from_numpy(blk).cuda()
+    r = torch.from_numpy(rhs).cuda()
+    m.m2s_line_btri(b, r, axis)
+    torch.cuda.synchronize()
+    assert err(r.cpu().numpy(), want) <= 1e-13
+
+
+@pytest.fixture(scope="module")
+def btri_162():
+    import torch
+    blk, rhs = gen.line_btri_inputs((162, 162, 162), seed=gen.BASE_SEED + 81)
+    return torch.from_numpy(blk).cuda(), torch.from_numpy(rhs).cuda()
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_line_btri_162_sampled_equations(m, btri_162, axis):
+    """Every sampled point satisfies A v[i-1] + B v[i] + C v[i+1] = r[i]
+    (5 rows) to 1e-13 of the sum of the magnitudes of its terms."""
+    import torch
+    n = 162
+    b, r0 = btri_162
+    v = r0.clone()
+    m.m2s_line_btri(b, v, axis)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(82 + axis)
+    pts = rng.integers(0, n ** 3, size=50000)
+    z, y, x = pts // (n * n), (pts // n) % n, pts % n
+    pos = (x, y, z)[axis]
+    stride = (1, n, n * n)[axis]
+    vf = v.reshape(-1, 5)
+    bf = b.reshape(-1, 3, 5, 5)
+    P = torch.from_numpy(pts).cuda()
+    res = -r0.reshape(-1, 5)[P].clone()
+    mag = res.abs().clone()
+    for j, off in enumerate((-1, 0, 1)):
+        ok = torch.from_numpy((pos + off >= 0) & (pos + off < n)).cuda()
+        q = torch.where(ok, P + off * stride, P)
+        terms = bf[P, j] * vf[q].unsqueeze(1) * ok.view(-1, 1, 1)
+        res += terms.sum(-1)
+        mag += terms.abs().sum(-1)
+    assert float((res.abs() / mag).max()) <= 1e-13
