@@ -696,7 +696,7 @@ def main():
     t_launch = ms_l0 / 1e3 / max(1, n_l0)
     ach = 27 * rows / t_launch / 1e9
     traffic, traffic_src = sweep_traffic("gs27_cta_kernel_f64_%d" % n)
-    roof = {"kernel": "gs27_cta_kernel<double,2,8,2> (Gauss-Seidel sweep, %d^3 level)" % n,
+    roof = {"kernel": "gs27_cta_kernel<double,2,8,2,-1> (Gauss-Seidel sweep, %d^3 level)" % n,
             "bound": "alu", "achieved": ach, "peak": FP64_OPS_PEAK / 1e9,
             "unit": "G FP64 op/s", "frac": ach / (FP64_OPS_PEAK / 1e9), "traffic": traffic,
             "traffic_source": traffic_src,
