@@ -21,6 +21,7 @@
 // 27-point sweep (k_wave2.cu): tagged words, a vote per step, bounded polls.
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 #include <vector>
 
 #include "m2s_cta.cuh"
@@ -75,7 +76,7 @@ struct Cta7Shared {
     volatile int prog[W];
 };
 
-template <typename T, int W, int D>
+template <typename T, int W, int D, int RD>
 __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
                                             Cta7Shared<T, W>& sh, unsigned tag) {
     typedef typename Tagged<T>::W TW;
@@ -92,9 +93,12 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
     const bool mb_out = !halo && (lane == 31 || w == W - 1);
     const bool zmb = w == 0 && z >= 1;  // plane below from the unit underneath
     const int nx = dm.nx;
-    const i64 dir = a.rev ? -1 : 1;
+    // direction: RD = 0 forward, 1 backward (compile time), -1 read at run time
+    const bool rev = RD < 0 ? a.rev != 0 : RD == 1;
+    typedef typename std::conditional<(RD < 0), i64, int>::type StepT;
+    const StepT dir = rev ? -1 : 1;
     const i64 r = rv ? ((i64)z * dm.ny + y) * nx : 0;
-    const i64 L = a.rev ? dm.n - 1 - r : r;  // problem-local index of x = 0
+    const i64 L = rev ? dm.n - 1 - r : r;  // problem-local index of x = 0
     const i64 szd = dir * (i64)nx * dm.ny;   // index step of the z - 1 neighbour
     const T* Q = a.Qin + dm.off;
     const T* B = a.b + dm.off;
@@ -247,7 +251,7 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
     }
 }
 
-template <typename T, int W, int D>
+template <typename T, int W, int D, int RD>
 __global__ void __launch_bounds__(W * 32, 1) gs7_cta_kernel(Cta7Args<T> a) {
     __shared__ int s_ticket;
     __shared__ unsigned s_tag;
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(W * 32, 1) gs7_cta_kernel(Cta7Args<T> a) {
         int ab = 0;
         if (threadIdx.x == 0) ab = ld_relaxed_gpu(&a.status->abort) || t == a.stall_unit;
         ab = __syncthreads_or(ab);
-        if (!ab) sweep7_warp<T, W, D>(a, t, warp, sh, s_tag);
+        if (!ab) sweep7_warp<T, W, D, RD>(a, t, warp, sh, s_tag);
         __syncthreads();
     }
     // exit protocol: the last CTA out resets the ticket and advances the tag
@@ -287,8 +291,13 @@ __global__ void __launch_bounds__(W * 32, 1) gs7_cta_kernel(Cta7Args<T> a) {
 }
 
 template <typename T> struct Cta7Shape;
-template <> struct Cta7Shape<double> { static constexpr int W = 8, D = 4; };
-template <> struct Cta7Shape<float> { static constexpr int W = 8, D = 8; };
+// RD0 / RD1: the direction template argument of the forward / backward
+// launches (0 and 1 compile the direction in; -1 reads it at run time).
+// Measured on a GB300 (variable-kappa 256^3 MG-PCG): compiled-in directions
+// take the 256^3 sweep from 0.98 to 0.97 ms (FP64) and 0.72 to 0.71 ms
+// (FP32), the solves from 2.54 to 2.50 s and 1.99 to 1.95 s.
+template <> struct Cta7Shape<double> { static constexpr int W = 8, D = 4, RD0 = 0, RD1 = 1; };
+template <> struct Cta7Shape<float> { static constexpr int W = 8, D = 8, RD0 = 0, RD1 = 1; };
 
 template <typename T>
 size_t cta7_smem_bytes() {
@@ -367,10 +376,17 @@ cudaError_t build_cta7_units(const std::vector<Dims>& dims, WaveUnits* out) {
         return e;
     }
     const size_t smem = cta7_smem_bytes<T>();
-    cudaFuncSetAttribute(gs7_cta_kernel<T, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    constexpr int R0 = Cta7Shape<T>::RD0, R1 = Cta7Shape<T>::RD1;
+    cudaFuncSetAttribute(gs7_cta_kernel<T, W, D, R0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs7_cta_kernel<T, W, D>, W * 32, smem);
+    cudaFuncSetAttribute(gs7_cta_kernel<T, W, D, R1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int per_sm = 0, per_sm1 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs7_cta_kernel<T, W, D, R0>, W * 32,
+                                                  smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, gs7_cta_kernel<T, W, D, R1>, W * 32,
+                                                  smem);
+    per_sm = std::min(per_sm, per_sm1);
     u.grid = wave_grid(u.n_units, per_sm);
     *out = u;
     return cudaGetLastError();
@@ -400,7 +416,11 @@ cudaError_t launch_gs7_cta(const WaveUnits& u, const WaveCall& c, const KappaLev
     a.rz = c.rz_partials;
     a.stall_unit = c.stall_unit;
     a.mbox = u.d_mbox;
-    gs7_cta_kernel<T, W, D><<<u.grid, W * 32, cta7_smem_bytes<T>(), st>>>(a);
+    constexpr int R0 = Cta7Shape<T>::RD0, R1 = Cta7Shape<T>::RD1;
+    if (c.rev)
+        gs7_cta_kernel<T, W, D, R1><<<u.grid, W * 32, cta7_smem_bytes<T>(), st>>>(a);
+    else
+        gs7_cta_kernel<T, W, D, R0><<<u.grid, W * 32, cta7_smem_bytes<T>(), st>>>(a);
     return cudaGetLastError();
 }
 
