@@ -230,6 +230,65 @@ def test_sweep_timeout_is_reported_and_recoverable(m):
     assert err64(host(x), oracle.gs_forward(H27, b, x0)) <= TOL64
 
 
+def test_kappa_sweep_timeout_is_reported_and_recoverable(m):
+    """The same host-injected stall in the variable-kappa 7-point sweep."""
+    shape = (32, 32, 32)
+    kap = kappa_for(shape, 3)
+    g = make_grid(m, shape, op=K7, kappa=kap)
+    m.m2s_set_spin_limit(g.handle, 50_000_000)
+    b, x0 = rnd(shape, 20), rnd(shape, 21)
+    m.m2s_debug_stall_unit(g.handle, 0, 0)
+    x = dev(x0)
+    m.m2s_gs_sweep(g.handle, 0, dev(b), x, m.FORWARD)
+    with pytest.raises(m.M2SError) as ei:
+        m.m2s_grid_sync(g.handle)
+    assert ei.value.status == m.Status.TIMEOUT
+    x = dev(x0)
+    m.m2s_gs_sweep(g.handle, 0, dev(b), x, m.FORWARD)
+    m.m2s_grid_sync(g.handle)
+    assert err64(host(x), oracle.gs_forward(K7, b, x0, kap)) <= TOL64
+
+
+def test_f32_sweep_timeout_is_reported_and_recoverable(m):
+    """A stalled unit in the FP32 27-point sweep: TIMEOUT, then a correct
+    FP32 symmetric sweep."""
+    import torch
+    shape = (32, 32, 32)
+    g = make_grid(m, shape, pdt=1)
+    m.m2s_set_spin_limit(g.handle, 50_000_000)
+    b, x0 = rnd(shape, 22), rnd(shape, 23)
+    m.m2s_debug_stall_unit(g.handle, 0, 1)
+    x = dev(x0, torch.float32)
+    m.m2s_symgs(g.handle, 0, dev(b, torch.float32), x, 1)
+    with pytest.raises(m.M2SError) as ei:
+        m.m2s_grid_sync(g.handle)
+    assert ei.value.status == m.Status.TIMEOUT
+    x = dev(x0, torch.float32)
+    m.m2s_symgs(g.handle, 0, dev(b, torch.float32), x, 1)
+    m.m2s_grid_sync(g.handle)
+    want = oracle.symgs_f32(H27, b.astype(np.float32), x0.astype(np.float32), 1)
+    assert err32(host(x), want) <= TOL32
+
+
+def test_pcg_timeout_on_a_coarse_level_is_reported_and_the_next_solve_is_correct(m):
+    """A stall on level 1 inside the V-cycle of a solve: the solve returns
+    TIMEOUT (the kernels after the failed sweep run on and finish); the
+    next solve on the same grid matches the oracle."""
+    import torch
+    shape = (32, 32, 32)
+    g = make_grid(m, shape, levels=3)
+    m.m2s_set_spin_limit(g.handle, 50_000_000)
+    b = oracle.apply(H27, np.ones(shape))
+    x = torch.empty(shape, dtype=torch.float64, device="cuda")
+    m.m2s_debug_stall_unit(g.handle, 1, 0)
+    with pytest.raises(m.M2SError) as ei:
+        m.m2s_pcg_solve(g.handle, dev(b), x, max_iters=5, fixed_iters=True)
+    assert ei.value.status == m.Status.TIMEOUT
+    st, res = m.m2s_pcg_solve(g.handle, dev(b), x, max_iters=5, fixed_iters=True)
+    ox, _, _, _ = oracle.pcg(H27, b, 3, max_iters=5, fixed_iters=True)
+    assert st == m.Status.OK and err64(host(x), ox) <= TOL64
+
+
 @pytest.mark.parametrize("shape", [(5, 3, 4), (17, 33, 32), (33, 17, 35), (64, 64, 64),
                                    (40, 11, 3), (40, 7, 3), (70, 5, 2)])
 @pytest.mark.parametrize("f32", [False, True])
