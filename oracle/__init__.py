@@ -59,6 +59,8 @@ def lib():
             "or_ssor": [_i, _i, _i, _dp, _dp, _dp, _d, _dp, _dp, _i],
             "or_line_penta": [_i, _i, _i, _i, _dp, _dp, _i],
             "or_line_btri": [_i, _i, _i, _i, _dp, _dp],
+            "or_ilu0_factor": [_i, _i, _i, _dp],
+            "or_ilu0_apply": [_i, _i, _i, _dp, _dp, _dp],
             "or_coarse_n": [_i],
             "or_abi_version": [],
         }
@@ -298,3 +300,24 @@ def line_btri(blk, rhs, axis):
     assert blk.shape == (nz, ny, nx, 3, 5, 5) and v.shape[3] == 5
     lib().or_line_btri(nx, ny, nz, int(axis), _p(blk), _p(v))
     return v
+
+
+def ilu0_factor(shape):
+    """ILU(0) of the HPCG 27-point matrix on a grid of `shape` (nz, ny, nx):
+    (nz, ny, nx, 27) values per point over the 3x3x3 box offsets
+    o = (dz+1)*9 + (dy+1)*3 + (dx+1): o < 13 the unit-lower factor L, o = 13
+    the pivot, o > 13 the strict upper part of U; 0 off the domain."""
+    nz, ny, nx = shape
+    F = np.zeros((nz, ny, nx, 27))
+    lib().or_ilu0_factor(nx, ny, nz, _p(F))
+    return F
+
+
+def ilu0_apply(F, r):
+    """(LU)^{-1} r with the factors of ilu0_factor."""
+    F = _f64(F)
+    r = _f64(r)
+    z = np.empty_like(r)
+    nz, ny, nx = r.shape
+    lib().or_ilu0_apply(nx, ny, nz, _p(F), _p(r), _p(z))
+    return z

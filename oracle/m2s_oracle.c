@@ -824,4 +824,82 @@ void or_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* r
     free(R);
 }
 
+/* ------------------------------------------------------------------------ */
+/* ILU(0) of the HPCG 27-point matrix (the incomplete LU preconditioner of  */
+/* Sec. 1 and the ILU micro-benchmark of Sec. 7.2.1, on the 27-point       */
+/* stencil).  Factors on the matrix's own pattern: for every point p the   */
+/* 27 values F[p][o], o = (dz+1)*9 + (dy+1)*3 + (dx+1) over the offsets of  */
+/* the 3x3x3 box (o < 13: the strict lower part, L with a unit diagonal    */
+/* implied; o = 13: the pivot u_pp; o > 13: the strict upper part of U);   */
+/* entries of out-of-domain neighbours are 0.  Rows in lexicographic order,*/
+/* each by the IKJ elimination restricted to the pattern (Saad, Iterative  */
+/* Methods for Sparse Linear Systems, Sec. 10.3):                          */
+/*   for k in pattern(p), k < p, increasing:  a_pk /= a_kk;                 */
+/*     for j in pattern(p), j > k, j in pattern(k):  a_pj -= a_pk a_kj.     */
+/* ------------------------------------------------------------------------ */
+static int box_off(int dx, int dy, int dz) { return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1); }
+
+void or_ilu0_factor(int nx, int ny, int nz, double* F) {
+    const i64 n = (i64)nx * ny * nz;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const i64 p = pidx(nx, ny, x, y, z);
+                double* Fp = F + 27 * p;
+                /* the row of A on the pattern */
+                for (int o = 0; o < 27; ++o) {
+                    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+                    Fp[o] = inside(nx, ny, nz, x + dx, y + dy, z + dz) ? (o == 13 ? 26.0 : -1.0) : 0.0;
+                }
+                /* eliminate the lower entries in increasing column order */
+                for (int ok = 0; ok < 13; ++ok) {
+                    const int kx = ok % 3 - 1, ky = (ok / 3) % 3 - 1, kz = ok / 9 - 1;
+                    if (!inside(nx, ny, nz, x + kx, y + ky, z + kz)) continue;
+                    const double* Fk = F + 27 * pidx(nx, ny, x + kx, y + ky, z + kz);
+                    Fp[ok] /= Fk[13];
+                    for (int oj = ok + 1; oj < 27; ++oj) {
+                        const int jx = oj % 3 - 1, jy = (oj / 3) % 3 - 1, jz = oj / 9 - 1;
+                        if (!inside(nx, ny, nz, x + jx, y + jy, z + jz)) continue;
+                        /* column j relative to row k */
+                        const int rx = jx - kx, ry = jy - ky, rz = jz - kz;
+                        if (rx < -1 || rx > 1 || ry < -1 || ry > 1 || rz < -1 || rz > 1) continue;
+                        Fp[oj] -= Fp[ok] * Fk[box_off(rx, ry, rz)];
+                    }
+                }
+            }
+    (void)n;
+}
+
+/* z = (LU)^{-1} r: forward substitution with the unit lower factor in     */
+/* lexicographic order, then backward substitution with U in reverse.     */
+void or_ilu0_apply(int nx, int ny, int nz, const double* F, const double* r, double* zout) {
+    const i64 n = (i64)nx * ny * nz;
+    double* y = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int z = 0; z < nz; ++z)
+        for (int yy = 0; yy < ny; ++yy)
+            for (int x = 0; x < nx; ++x) {
+                const i64 p = pidx(nx, ny, x, yy, z);
+                double s = r[p];
+                for (int o = 0; o < 13; ++o) {
+                    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+                    if (inside(nx, ny, nz, x + dx, yy + dy, z + dz))
+                        s -= F[27 * p + o] * y[pidx(nx, ny, x + dx, yy + dy, z + dz)];
+                }
+                y[p] = s;
+            }
+    for (int z = nz - 1; z >= 0; --z)
+        for (int yy = ny - 1; yy >= 0; --yy)
+            for (int x = nx - 1; x >= 0; --x) {
+                const i64 p = pidx(nx, ny, x, yy, z);
+                double s = y[p];
+                for (int o = 14; o < 27; ++o) {
+                    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+                    if (inside(nx, ny, nz, x + dx, yy + dy, z + dz))
+                        s -= F[27 * p + o] * zout[pidx(nx, ny, x + dx, yy + dy, z + dz)];
+                }
+                zout[p] = s / F[27 * p + 13];
+            }
+    free(y);
+}
+
 int or_abi_version(void) { return 1; }

@@ -719,3 +719,88 @@ def test_line_btri_axis_permutation():
     bt = np.ascontiguousarray(np.transpose(blk, (2, 1, 0, 3, 4, 5)))
     rt = np.ascontiguousarray(np.transpose(rhs, (2, 1, 0, 3)))
     assert np.array_equal(vx, np.transpose(oracle.line_btri(bt, rt, 2), (2, 1, 0, 3)))
+
+
+# ---------------------------------------------------------------------------
+# ILU(0) of the HPCG 27-point matrix (Sec. 1; the ILU micro-benchmark of
+# Sec. 7.2.1 uses the 27-point stencil).
+# ---------------------------------------------------------------------------
+ILU_SHAPES = [(3, 4, 5), (5, 3, 4), (4, 4, 4), (2, 6, 3)]
+
+
+def _offsets27():
+    return [((o % 3) - 1, (o // 3) % 3 - 1, o // 9 - 1) for o in range(27)]
+
+
+def _dense_hpcg(shape):
+    nz, ny, nx = shape
+    n = nx * ny * nz
+    A = np.zeros((n, n))
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                p = (z * ny + y) * nx + x
+                for dz in (-1, 0, 1):
+                    for dy in (-1, 0, 1):
+                        for dx in (-1, 0, 1):
+                            qx, qy, qz = x + dx, y + dy, z + dz
+                            if 0 <= qx < nx and 0 <= qy < ny and 0 <= qz < nz:
+                                A[p, (qz * ny + qy) * nx + qx] = 26.0 if (dx, dy, dz) == (0, 0, 0) else -1.0
+    return A
+
+
+def _dense_factors(F):
+    nz, ny, nx, _ = F.shape
+    n = nx * ny * nz
+    L, U = np.eye(n), np.zeros((n, n))
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                p = (z * ny + y) * nx + x
+                for o, (dx, dy, dz) in enumerate(_offsets27()):
+                    qx, qy, qz = x + dx, y + dy, z + dz
+                    if 0 <= qx < nx and 0 <= qy < ny and 0 <= qz < nz:
+                        q = (qz * ny + qy) * nx + qx
+                        (L if o < 13 else U)[p, q] = F[z, y, x, o]
+    return L, U
+
+
+@pytest.mark.parametrize("shape", ILU_SHAPES)
+def test_ilu0_matches_a_on_its_pattern(shape):
+    """The defining property of ILU(0): (L U)_pq = a_pq wherever a_pq != 0."""
+    A = _dense_hpcg(shape)
+    L, U = _dense_factors(oracle.ilu0_factor(shape))
+    LU = L @ U
+    mask = A != 0
+    assert np.max(np.abs(LU[mask] - A[mask])) <= 1e-12
+    # and it is not the exact factorisation (fill-in outside the pattern)
+    if min(shape) >= 2:
+        assert np.max(np.abs(LU - A)) > 1e-3
+
+
+@pytest.mark.parametrize("shape", ILU_SHAPES)
+def test_ilu0_apply_solves_lu(shape):
+    F = oracle.ilu0_factor(shape)
+    L, U = _dense_factors(F)
+    r = gen.random_vector(shape, seed=gen.BASE_SEED + 90)
+    z = oracle.ilu0_apply(F, r)
+    assert np.max(np.abs(L @ (U @ z.ravel()) - r.ravel())) <= 1e-12
+
+
+def test_ilu0_of_a_symmetric_matrix_has_u_equal_d_lt():
+    """A is symmetric, so ILU(0) gives U = D L^T (D the pivots)."""
+    L, U = _dense_factors(oracle.ilu0_factor((3, 4, 5)))
+    D = np.diag(np.diag(U))
+    assert np.max(np.abs(U - D @ L.T)) <= 1e-12
+
+
+def test_ilu0_of_a_line_is_the_exact_lu():
+    """On a 1 x 1 x m grid the pattern is tridiagonal: no fill, so ILU(0) is
+    the exact LU and its application the exact solve."""
+    shape = (1, 1, 9)
+    A = _dense_hpcg(shape)
+    F = oracle.ilu0_factor(shape)
+    L, U = _dense_factors(F)
+    assert np.max(np.abs(L @ U - A)) <= 1e-13
+    r = gen.random_vector(shape, seed=gen.BASE_SEED + 91)
+    assert np.max(np.abs(oracle.ilu0_apply(F, r).ravel() - np.linalg.solve(A, r.ravel()))) <= 1e-13
