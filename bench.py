@@ -518,6 +518,33 @@ def other_configs(m, torch, hbm):
         torch.cuda.empty_cache()
         return out_
 
+    def ilu0_256():
+        n = 256
+        rows = n ** 3
+        g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.HPCG27, mg_levels=1)])
+        try:
+            t_fac = time_cuda(torch, lambda: m.m2s_ilu0_setup(g.handle), 1, 1)
+            gen_t = torch.Generator(device="cuda").manual_seed(5)
+            r = torch.rand((n, n, n), dtype=torch.float64, device="cuda", generator=gen_t)
+            z = torch.empty_like(r)
+            t_app = time_cuda(torch, lambda: m.m2s_ilu0_apply(g.handle, r, z), 5, 2)
+        finally:
+            g.close()
+        hp = (n - 1) * 7 + 1
+        return {"workload": "ILU(0) of the HPCG 27-point matrix at 256^3: factorisation and one "
+                            "application (forward L, backward U solve), FP64",
+                "factor_ms": t_fac * 1e3, "apply_ms": t_app * 1e3,
+                "hyperplanes": hp, "launches_per_apply": 2 * hp,
+                "apply_alg_GBs": 248.0 * rows / t_app / 1e9,
+                "apply_hbm_frac": 248.0 * rows / t_app / 1e9 / hbm,
+                "alg_bytes_note": "248 B/point per application: the 27 factors, r in, z out and "
+                                  "the intermediate y written and re-read",
+                "bound_note": "one launch per hyperplane x + 2y + 4z (CUDA graph): launch- and "
+                              "latency-bound",
+                "parity": "tests/test_gpu_ilu.py (oracle on ragged shapes; sampled (LU)_pq = "
+                          "a_pq and L U z = r at 256^3)"}
+
+    guarded("ilu0_256", ilu0_256)
     guarded("line_penta_162x5", line_penta_162)
     guarded("line_btri_162x5", line_btri_162)
     guarded("symgs_1536", symgs_1536)

@@ -180,6 +180,30 @@ m2s_status m2s_pcg_solve(m2s_grid* grid, const double* b, double* x,
                          const m2s_pcg_opts* opts, m2s_pcg_result* out,
                          void* stream);
 
+/* ILU(0) of the finest level's HPCG 27-point matrix (op HPCG27), the
+ * incomplete-LU preconditioner of paper Sec. 1 on the 27-point stencil of
+ * its ILU micro-benchmark (Sec. 7.2.1): factors L (unit lower) and U on the
+ * pattern of A, every problem of the grid.  m2s_ilu0_setup computes them
+ * (27 FP64 values per point, allocated by the first call, library-owned)
+ * in lexicographic elimination order, ordered on `stream`.  May return
+ * M2S_ERR_OOM. */
+m2s_status m2s_ilu0_setup(m2s_grid* grid, void* stream);
+
+/* Copy the factors of m2s_ilu0_setup to `out` (device, FP64,
+ * [n][27] per point of the packed finest level: offset o = (dz+1)*9 +
+ * (dy+1)*3 + (dx+1) of the 3x3x3 box; o < 13 L, o = 13 the pivot, o > 13
+ * U; 0 off the domain), ordered on `stream`. */
+m2s_status m2s_ilu0_factors(m2s_grid* grid, double* out, void* stream);
+
+/* z = (L U)^{-1} r with the factors of m2s_ilu0_setup: forward substitution
+ * with L, then backward substitution with U (packed FP64 finest-level
+ * vectors of all problems).  r and z are either the same array or do not
+ * overlap.  The launches for a given (r, z) are recorded once into a CUDA
+ * graph and replayed; ordered on `stream`.  M2S_ERR_INVALID_ARG before
+ * m2s_ilu0_setup or for another operator. */
+m2s_status m2s_ilu0_apply(m2s_grid* grid, const double* r, double* z,
+                          void* stream);
+
 /* Direct solves of pentadiagonal systems along the grid lines of one axis:
  * the multi-diagonal direct solves of NPB-SP (paper Sec. 1; Sec. 7.2.2:
  * along each axis every line is swept forward and backward, the two

@@ -74,7 +74,8 @@ EXPORTS = (
     "m2s_set_spin_limit", "m2s_debug_stall_unit", "m2s_symgs_noalloc", "m2s_status_string",
     "m2s_sweep_timing", "m2s_sweep_timing_read", "m2s_set_sweep_warps", "m2s_set_graphs",
     "m2s_autotune_sweeps", "m2s_line_penta", "m2s_line_penta_work_bytes", "m2s_line_btri",
-    "m2s_line_btri_work_bytes",
+    "m2s_line_btri_work_bytes", "m2s_ilu0_setup", "m2s_ilu0_apply",
+    "m2s_ilu0_factors",
 )
 
 
@@ -123,6 +124,9 @@ def load():
         "m2s_line_penta": ([i, i, i, i, vp, vp, i, vp, ll, vp], i),
         "m2s_line_btri_work_bytes": ([i, i, i], ll),
         "m2s_line_btri": ([i, i, i, i, vp, vp, vp, ll, vp], i),
+        "m2s_ilu0_setup": ([vp, vp], i),
+        "m2s_ilu0_apply": ([vp, vp, vp, vp], i),
+        "m2s_ilu0_factors": ([vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -333,6 +337,20 @@ def m2s_line_penta(coef, rhs, axis, work=None, stream=None):
     return _check(load().m2s_line_penta(nx, ny, nz, int(axis), _ptr(coef, "coef"),
                                         _ptr(rhs, "rhs"), int(k), _ptr(work, "work"), nbytes,
                                         _stream(stream)), "m2s_line_penta")
+
+
+def m2s_ilu0_setup(grid, stream=None):
+    return _check(load().m2s_ilu0_setup(grid, _stream(stream)), "m2s_ilu0_setup")
+
+
+def m2s_ilu0_factors(grid, out, stream=None):
+    return _check(load().m2s_ilu0_factors(grid, _ptr(out, "out"), _stream(stream)),
+                  "m2s_ilu0_factors")
+
+
+def m2s_ilu0_apply(grid, r, z, stream=None):
+    return _check(load().m2s_ilu0_apply(grid, _ptr(r, "r"), _ptr(z, "z"), _stream(stream)),
+                  "m2s_ilu0_apply")
 
 
 def m2s_line_btri_work_bytes(nx, ny, nz):

@@ -89,6 +89,12 @@ struct m2s_grid {
     // workspaces made at first use, so that a grid used only for FP64
     // sweeps holds no Krylov vectors and no FP32 hierarchy (a 1536^3 FP64
     // vector is 29 GB)
+    // ILU(0) factors of the finest level (m2s_ilu0_setup) and the CUDA graph
+    // of their application for the vectors (ilu_r, ilu_z)
+    double* ilu_F = nullptr;
+    cudaGraphExec_t ilu_graph = nullptr;
+    const double* ilu_r = nullptr;
+    double* ilu_z = nullptr;
     bool pcg_ready = false;  // r, z, zold, p0, p1, q
     bool f32_ready = false;  // FP32 level arrays, sweep schedules, r32, z32
     std::vector<int> w32_choice;  // 27-point FP32 warps per unit, per level
@@ -129,6 +135,7 @@ void destroy_grid(m2s_grid* g) {
         for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
     for (cudaGraphExec_t& ge : g->graph)
         if (ge) cudaGraphExecDestroy(ge);
+    if (g->ilu_graph) cudaGraphExecDestroy(g->ilu_graph);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
 }
@@ -1079,6 +1086,62 @@ m2s_status m2s_line_penta(int nx, int ny, int nz, int axis, const double* coef, 
     if (!disjoint(coef, bc, rhs, br) || !disjoint(coef, bc, work, bw) || !disjoint(rhs, br, work, bw))
         return M2S_ERR_INVALID_ARG;
     M2S_TRY(launch_line_penta(nx, ny, nz, axis, coef, rhs, k, (double*)work, S(stream)));
+    return M2S_OK;
+}
+
+m2s_status m2s_ilu0_setup(m2s_grid* g, void* stream) {
+    if (!g || g->op != M2S_OP_HPCG27) return M2S_ERR_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    if (!g->ilu_F) M2S_TRY(galloc(g, &g->ilu_F, 27 * g->ltot[0]));
+    for (int i = 0; i < g->np; ++i) M2S_TRY(launch_ilu_factor(g->dims[i][0], g->ilu_F, st));
+    g->last_stream = st;
+    return M2S_OK;
+}
+
+m2s_status m2s_ilu0_factors(m2s_grid* g, double* out, void* stream) {
+    if (!g || g->op != M2S_OP_HPCG27 || !g->ilu_F || !out) return M2S_ERR_INVALID_ARG;
+    M2S_TRY(cudaMemcpyAsync(out, g->ilu_F, 27 * g->ltot[0] * sizeof(double),
+                            cudaMemcpyDeviceToDevice, S(stream)));
+    return M2S_OK;
+}
+
+m2s_status m2s_ilu0_apply(m2s_grid* g, const double* r, double* z, void* stream) {
+    if (!g || g->op != M2S_OP_HPCG27 || !g->ilu_F || !r || !z) return M2S_ERR_INVALID_ARG;
+    if (!aligned(r, 8) || !aligned(z, 8)) return M2S_ERR_INVALID_ARG;
+    const i64 bytes = g->ltot[0] * 8;
+    const uintptr_t a = (uintptr_t)r, b = (uintptr_t)z;
+    if (a != b && a < b + (uintptr_t)bytes && b < a + (uintptr_t)bytes) return M2S_ERR_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    if (!g->ilu_graph || g->ilu_r != r || g->ilu_z != z) {
+        // record the 2 (T + 1) launches of every problem once on the grid's
+        // own stream, replay them on the caller's
+        if (g->ilu_graph) {
+            cudaGraphExecDestroy(g->ilu_graph);
+            g->ilu_graph = nullptr;
+        }
+        if (!g->cap_stream)
+            M2S_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t gr = nullptr;
+        M2S_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaSuccess;
+        for (int i = 0; i < g->np && ce == cudaSuccess; ++i)
+            ce = launch_ilu_apply(g->dims[i][0], g->ilu_F, r, z, g->cap_stream);
+        const cudaError_t ee = cudaStreamEndCapture(g->cap_stream, &gr);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            return cuda_status(ce != cudaSuccess ? ce : ee);
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&g->ilu_graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ie != cudaSuccess) {
+            g->ilu_graph = nullptr;
+            return cuda_status(ie);
+        }
+        g->ilu_r = r;
+        g->ilu_z = z;
+    }
+    M2S_TRY(cudaGraphLaunch(g->ilu_graph, st));
+    g->last_stream = st;
     return M2S_OK;
 }
 

@@ -190,6 +190,12 @@ void free_wave_units(WaveUnits* u);
 i64 line_penta_work_doubles(int nx, int ny, int nz);
 cudaError_t launch_line_penta(int nx, int ny, int nz, int axis, const double* coef, double* rhs,
                               int k, double* work, cudaStream_t st);
+// ILU(0) of the HPCG 27-point matrix (k_ilu.cu): factors F[n][27] over the
+// 3x3x3 box offsets; one launch per hyperplane x + 2y + 4z.
+int ilu_hyperplanes(const Dims& d);
+cudaError_t launch_ilu_factor(const Dims& d, double* F, cudaStream_t st);
+cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* r, double* z,
+                             cudaStream_t st);
 // Block-tridiagonal (5x5) line solves (k_line.cu).
 i64 line_btri_work_doubles(int nx, int ny, int nz);
 cudaError_t launch_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* rhs,

@@ -118,3 +118,10 @@ def test_line_btri_rejects_invalid_arguments_without_gpu(lib):
     ]
     for a in bad:
         assert lib.m2s_line_btri(*a[:7], ctypes.c_longlong(a[7]), None) == m.Status.INVALID_ARG, a
+
+
+def test_ilu0_rejects_invalid_arguments_without_gpu(lib):
+    import paper_2204_13304_gb300 as m
+    assert lib.m2s_ilu0_setup(None, None) == m.Status.INVALID_ARG
+    assert lib.m2s_ilu0_apply(None, None, None, None) == m.Status.INVALID_ARG
+    assert lib.m2s_ilu0_factors(None, None, None) == m.Status.INVALID_ARG

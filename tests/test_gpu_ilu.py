@@ -1,0 +1,160 @@
+"""GPU parity of ILU(0) of the HPCG 27-point matrix (the incomplete LU of
+Sec. 1 on the 27-point stencil of the ILU micro-benchmark, Sec. 7.2.1).
+
+Against the oracle, element by element: factors and the application
+z = (LU)^{-1} r.  The GPU fuses multiply-subtracts where the oracle rounds
+the product and the difference separately; A is diagonally dominant (26
+against 26 unit neighbours, strictly at the boundary), the pivots stay
+above 20, and the multipliers are below 0.05 in magnitude, so the
+differences stay at a few ulps: 1e-13 per entry against max(|o_i|,
+1e-2 |o|_inf).
+
+At 256^3 (the benchmark's size; 3.6 GB of factors) the oracle is not
+re-run: at sampled points p the factors must reproduce A on its pattern,
+(LU)_pq = a_pq, and the application must satisfy (L (U z))_p = r_p.
+"""
+import numpy as np
+import pytest
+
+import m2s_inputs as gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(1, 1, 1), (2, 3, 1), (3, 4, 5), (5, 3, 4), (7, 17, 5), (17, 33, 32)]
+
+
+@pytest.fixture(scope="module")
+def m():
+    from paper_2204_13304_gb300 import build
+    build.build()
+    import paper_2204_13304_gb300 as m
+    m.load()
+    return m
+
+
+def err(g, o, floor=1e-2):
+    scale = np.max(np.abs(o))
+    if scale == 0:
+        return float(np.max(np.abs(g)))
+    return float(np.max(np.abs(g - o) / np.maximum(np.abs(o), floor * scale)))
+
+
+def grid(m, shapes):
+    return m.Grid([dict(nx=s[2], ny=s[1], nz=s[0], op=m.Op.HPCG27, mg_levels=1) for s in shapes])
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_ilu0_factors_and_apply_match_oracle(m, shape):
+    import torch
+    g = grid(m, [shape])
+    m.m2s_ilu0_setup(g.handle)
+    n = int(np.prod(shape))
+    F = torch.empty(n * 27, dtype=torch.float64, device="cuda")
+    m.m2s_ilu0_factors(g.handle, F)
+    want = oracle.ilu0_factor(shape)
+    assert err(F.cpu().numpy().reshape(want.shape), want) <= 1e-13
+    r = gen.random_vector(shape, seed=gen.BASE_SEED + 95)
+    z = torch.empty(shape, dtype=torch.float64, device="cuda")
+    m.m2s_ilu0_apply(g.handle, torch.from_numpy(r).cuda(), z)
+    torch.cuda.synchronize()
+    assert err(z.cpu().numpy(), oracle.ilu0_apply(want, r)) <= 1e-13
+    g.close()
+
+
+def test_ilu0_two_problems_and_in_place(m):
+    """A grid of two problems (packed vectors) and an application with
+    r and z the same array; repeated applications replay the graph."""
+    import torch
+    shapes = [(9, 7, 13), (4, 12, 6)]
+    g = grid(m, shapes)
+    m.m2s_ilu0_setup(g.handle)
+    rs = [gen.random_vector(s, seed=gen.BASE_SEED + 96 + i) for i, s in enumerate(shapes)]
+    v = torch.from_numpy(np.concatenate([r.ravel() for r in rs])).cuda()
+    for _ in range(2):
+        w = v.clone()
+        m.m2s_ilu0_apply(g.handle, w, w)
+    torch.cuda.synchronize()
+    got = w.cpu().numpy()
+    off = 0
+    for s, r in zip(shapes, rs):
+        k = int(np.prod(s))
+        want = oracle.ilu0_apply(oracle.ilu0_factor(s), r)
+        assert err(got[off:off + k].reshape(s), want) <= 1e-13
+        off += k
+    g.close()
+
+
+def _offsets():
+    return [((o % 3) - 1, (o // 3) % 3 - 1, o // 9 - 1) for o in range(27)]
+
+
+def test_ilu0_256_sampled_identities(m):
+    import torch
+    n = 256
+    shape = (n, n, n)
+    g = grid(m, [shape])
+    m.m2s_ilu0_setup(g.handle)
+    F = torch.empty((n ** 3, 27), dtype=torch.float64, device="cuda")
+    m.m2s_ilu0_factors(g.handle, F)
+    gen_t = torch.Generator(device="cuda").manual_seed(97)
+    r = torch.rand(shape, dtype=torch.float64, device="cuda", generator=gen_t) - 0.5
+    z = torch.empty_like(r)
+    m.m2s_ilu0_apply(g.handle, r, z)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(98)
+    pts = rng.integers(0, n ** 3, size=20000)
+    offs = _offsets()
+
+    def coords(p):
+        return p // (n * n), (p // n) % n, p % n
+
+    def nb(p, o):
+        z_, y_, x_ = coords(p)
+        dx, dy, dz = offs[o]
+        ok = (x_ + dx >= 0) & (x_ + dx < n) & (y_ + dy >= 0) & (y_ + dy < n) & \
+             (z_ + dz >= 0) & (z_ + dz < n)
+        return np.where(ok, p + (dz * n + dy) * n + dx, p), ok
+
+    zf = z.reshape(-1)
+    P = torch.from_numpy(pts).cuda()
+
+    def uz(p):  # (U z)_p for an array of points
+        pt = torch.from_numpy(p).cuda()
+        s = torch.zeros(len(p), dtype=torch.float64, device="cuda")
+        for o in range(13, 27):
+            q, ok = nb(p, o)
+            s += F[pt, o] * zf[torch.from_numpy(q).cuda()] * torch.from_numpy(ok).cuda()
+        return s
+
+    # (L (U z))_p = (U z)_p + sum_{o < 13} L_po (U z)_q
+    lhs = uz(pts)
+    mag = lhs.abs().clone()
+    for o in range(13):
+        q, ok = nb(pts, o)
+        t = F[P, o] * uz(q) * torch.from_numpy(ok).cuda()
+        lhs += t
+        mag += t.abs()
+    rp = r.reshape(-1)[P]
+    assert float(((lhs - rp).abs() / (mag + rp.abs())).max()) <= 1e-12
+    # (L U)_pq = a_pq on the pattern at the sampled points
+    worst = 0.0
+    for oq in range(27):
+        q, okq = nb(pts, oq)
+        acc = torch.zeros(len(pts), dtype=torch.float64, device="cuda")
+        for ok_ in range(14):  # k = p + offset ok_, ok_ <= 13 (L_pp = 1 at 13)
+            dxk, dyk, dzk = offs[ok_]
+            rx, ry, rz = offs[oq][0] - dxk, offs[oq][1] - dyk, offs[oq][2] - dzk
+            if max(abs(rx), abs(ry), abs(rz)) > 1:
+                continue
+            ou = (rz + 1) * 9 + (ry + 1) * 3 + (rx + 1)
+            if ou < 13:
+                continue  # U has no entry below the diagonal
+            k, okk = nb(pts, ok_)
+            lpk = torch.ones(len(pts), dtype=torch.float64, device="cuda") if ok_ == 13 \
+                else F[P, ok_]
+            acc += lpk * F[torch.from_numpy(k).cuda(), ou] * torch.from_numpy(okk).cuda()
+        want = np.where(okq, 26.0 if oq == 13 else -1.0, 0.0)
+        worst = max(worst, float((acc - torch.from_numpy(want).cuda()).abs().max()))
+    assert worst <= 1e-12
+    g.close()
