@@ -13,13 +13,15 @@
 // thread per point), and stream order between the launches carries every
 // dependence: no kernel waits on another, nothing can hang.  The
 // application replays its 2 (T + 1) launches from a CUDA graph.
+#include <algorithm>
+
 #include "m2s_internal.cuh"
 
 namespace m2s {
 
 namespace {
 
-constexpr int IB = 128;  // threads per CTA
+constexpr int IB = 256;  // largest CTA of a hyperplane launch
 
 __host__ __device__ constexpr int odx(int o) { return o % 3 - 1; }
 __host__ __device__ constexpr int ody(int o) { return (o / 3) % 3 - 1; }
@@ -31,16 +33,17 @@ __host__ __device__ constexpr bool in_box(int dx, int dy, int dz) {
     return dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
 }
 
-// The point of hyperplane t handled by this thread: y from the thread index
-// within the window of y whose x = t - 2y - 4z lies in [0, nx), z from
-// blockIdx.y.
-__device__ __forceinline__ bool hyperplane_point(const Dims& d, int t, int* x, int* y, int* z) {
-    *z = blockIdx.y;
+// The point of hyperplane t handled by this thread: z = z0 + blockIdx.y
+// (the launch covers the z that meet the hyperplane), y from the thread
+// index within the window of y whose x = t - 2y - 4z lies in [0, nx).
+__device__ __forceinline__ bool hyperplane_point(const Dims& d, int t, int z0, int* x, int* y,
+                                                 int* z) {
+    *z = z0 + (int)blockIdx.y;
     const int rem = t - 4 * *z;  // x + 2y
     if (rem < 0) return false;
     // smallest y with x = rem - 2y <= nx - 1
     int ylo = rem - (d.nx - 1) > 0 ? (rem - (d.nx - 1) + 1) / 2 : 0;
-    *y = ylo + (int)(blockIdx.x * IB + threadIdx.x);
+    *y = ylo + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     *x = rem - 2 * *y;
     return *y < d.ny && *x >= 0 && *x < d.nx;
 }
@@ -62,9 +65,10 @@ __device__ __forceinline__ i64 nbr(const Dims& d, i64 p, int dx, int dy, int dz)
     return p + ((i64)dz * d.ny + dy) * d.nx + dx;
 }
 
-__global__ void __launch_bounds__(IB) ilu_factor_kernel(Dims d, int t, double* __restrict__ F) {
+__global__ void __launch_bounds__(IB) ilu_factor_kernel(Dims d, int t, int z0,
+                                                        double* __restrict__ F) {
     int x, y, z;
-    if (!hyperplane_point(d, t, &x, &y, &z)) return;
+    if (!hyperplane_point(d, t, z0, &x, &y, &z)) return;
     const Inside in = inside_of(d, x, y, z);
     const i64 p = ((i64)z * d.ny + y) * d.nx + x;  // problem-local
     double* Fb = F + 27 * d.off;
@@ -90,42 +94,66 @@ __global__ void __launch_bounds__(IB) ilu_factor_kernel(Dims d, int t, double* _
     for (int o = 0; o < 27; ++o) Fp[o] = f[o];
 }
 
-// forward: y_p = r_p - sum_{o < 13} F[p][o] y_q, y kept in z
-__global__ void __launch_bounds__(IB) ilu_lower_kernel(Dims d, int t, const double* __restrict__ F,
+// forward: y_p = r_p - sum_{o < 13} F[p][o] y_q, y kept in z (two partial
+// sums halve the chain of dependent FMAs)
+__global__ void __launch_bounds__(IB) ilu_lower_kernel(Dims d, int t, int z0,
+                                                       const double* __restrict__ F,
                                                        const double* r, double* z) {
     int x, y, zz;
-    if (!hyperplane_point(d, t, &x, &y, &zz)) return;
+    if (!hyperplane_point(d, t, z0, &x, &y, &zz)) return;
     const Inside in = inside_of(d, x, y, zz);
     const i64 p = ((i64)zz * d.ny + y) * d.nx + x;
     const double* Fp = F + 27 * (d.off + p);
     const double* zb = z + d.off;
-    double s = r[d.off + p];
+    double s0 = r[d.off + p], s1 = 0.0;
 #pragma unroll
     for (int o = 0; o < 13; ++o)
-        if (in(odx(o), ody(o), odz(o))) s = fma(-__ldg(Fp + o), zb[nbr(d, p, odx(o), ody(o), odz(o))], s);
-    z[d.off + p] = s;
+        if (in(odx(o), ody(o), odz(o))) {
+            const double v = zb[nbr(d, p, odx(o), ody(o), odz(o))];
+            if (o & 1) s1 = fma(-__ldg(Fp + o), v, s1);
+            else s0 = fma(-__ldg(Fp + o), v, s0);
+        }
+    z[d.off + p] = s0 + s1;
 }
 
 // backward: z_p = (y_p - sum_{o > 13} F[p][o] z_q) / F[p][13]
-__global__ void __launch_bounds__(IB) ilu_upper_kernel(Dims d, int t, const double* __restrict__ F,
-                                                       double* z) {
+__global__ void __launch_bounds__(IB) ilu_upper_kernel(Dims d, int t, int z0,
+                                                       const double* __restrict__ F, double* z) {
     int x, y, zz;
-    if (!hyperplane_point(d, t, &x, &y, &zz)) return;
+    if (!hyperplane_point(d, t, z0, &x, &y, &zz)) return;
     const Inside in = inside_of(d, x, y, zz);
     const i64 p = ((i64)zz * d.ny + y) * d.nx + x;
     const double* Fp = F + 27 * (d.off + p);
     const double* zb = z + d.off;
-    double s = zb[p];
+    double s0 = zb[p], s1 = 0.0;
 #pragma unroll
     for (int o = 14; o < 27; ++o)
-        if (in(odx(o), ody(o), odz(o))) s = fma(-__ldg(Fp + o), zb[nbr(d, p, odx(o), ody(o), odz(o))], s);
-    z[d.off + p] = s / __ldg(Fp + 13);
+        if (in(odx(o), ody(o), odz(o))) {
+            const double v = zb[nbr(d, p, odx(o), ody(o), odz(o))];
+            if (o & 1) s1 = fma(-__ldg(Fp + o), v, s1);
+            else s0 = fma(-__ldg(Fp + o), v, s0);
+        }
+    z[d.off + p] = (s0 + s1) / __ldg(Fp + 13);
 }
 
-dim3 hyperplane_grid(const Dims& d) {
-    // at most ceil(nx / 2) + 1 values of y per z on one hyperplane
+// Launch shape of hyperplane t: the z that meet it (0 <= t - 4z <= (nx-1) +
+// 2(ny-1)), one CTA row each; the window of at most nx/2 + 2 values of y
+// per z in CTAs of up to IB threads (a warp multiple).
+struct HpLaunch {
+    dim3 grid, block;
+    int z0;
+};
+HpLaunch hyperplane_launch(const Dims& d, int t) {
+    const int reach = (d.nx - 1) + 2 * (d.ny - 1);
+    const int zlo = std::max(0, (t - reach + 3) / 4);
+    const int zhi = std::min(d.nz - 1, t / 4);
     const int win = d.nx / 2 + 2;
-    return dim3((unsigned)((win + IB - 1) / IB), (unsigned)d.nz);
+    const int bs = std::min(IB, (win + 31) / 32 * 32);
+    HpLaunch h;
+    h.z0 = zlo;
+    h.block = dim3((unsigned)bs);
+    h.grid = dim3((unsigned)((win + bs - 1) / bs), (unsigned)std::max(0, zhi - zlo + 1));
+    return h;
 }
 
 }  // namespace
@@ -134,10 +162,11 @@ int ilu_hyperplanes(const Dims& d) { return (d.nx - 1) + 2 * (d.ny - 1) + 4 * (d
 
 cudaError_t launch_ilu_factor(const Dims& d, double* F, cudaStream_t st) {
     if (d.n == 0) return cudaSuccess;
-    const dim3 g = hyperplane_grid(d);
     const int T = ilu_hyperplanes(d);
     for (int t = 0; t < T; ++t) {
-        ilu_factor_kernel<<<g, IB, 0, st>>>(d, t, F);
+        const HpLaunch h = hyperplane_launch(d, t);
+        if (h.grid.y == 0) continue;
+        ilu_factor_kernel<<<h.grid, h.block, 0, st>>>(d, t, h.z0, F);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -147,15 +176,18 @@ cudaError_t launch_ilu_factor(const Dims& d, double* F, cudaStream_t st) {
 cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* r, double* z,
                              cudaStream_t st) {
     if (d.n == 0) return cudaSuccess;
-    const dim3 g = hyperplane_grid(d);
     const int T = ilu_hyperplanes(d);
     for (int t = 0; t < T; ++t) {
-        ilu_lower_kernel<<<g, IB, 0, st>>>(d, t, F, r, z);
+        const HpLaunch h = hyperplane_launch(d, t);
+        if (h.grid.y == 0) continue;
+        ilu_lower_kernel<<<h.grid, h.block, 0, st>>>(d, t, h.z0, F, r, z);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     for (int t = T - 1; t >= 0; --t) {
-        ilu_upper_kernel<<<g, IB, 0, st>>>(d, t, F, z);
+        const HpLaunch h = hyperplane_launch(d, t);
+        if (h.grid.y == 0) continue;
+        ilu_upper_kernel<<<h.grid, h.block, 0, st>>>(d, t, h.z0, F, z);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
