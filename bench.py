@@ -800,12 +800,12 @@ def main():
 
 
 def launches_per_solve(iters, levels=4):
-    """Kernels of one FP64 MG-PCG solve: setup (dot + finalize) then per
+    """Kernels of one FP64 MG-PCG solve: setup (r/26, dot, finalize) then per
     iteration the V-cycle (per non-coarsest level 2 + 2 sweeps, restriction,
     fused prolongation; coarsest 2 sweeps), finalize(rho), p-update+SpMV+dot,
     finalize(pq), update+|r|, finalize(rr)."""
     per_v = (levels - 1) * 6 + 2
-    return 2 + iters * (per_v + 5)
+    return 3 + iters * (per_v + 5)
 
 
 if __name__ == "__main__":
