@@ -104,7 +104,12 @@ namespace {
 
 m2s_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return M2S_OK;
-    if (e == cudaErrorMemoryAllocation) return M2S_ERR_OOM;
+    if (e == cudaErrorMemoryAllocation) {
+        // a failed allocation leaves the context usable but is also kept as
+        // the runtime's last error, which the next launch check would report
+        cudaGetLastError();
+        return M2S_ERR_OOM;
+    }
     return M2S_ERR_CUDA;
 }
 
@@ -118,7 +123,10 @@ template <typename T>
 cudaError_t galloc(m2s_grid* g, T** p, i64 count) {
     void* v = nullptr;
     cudaError_t e = cudaMalloc(&v, (size_t)std::max<i64>(count, 1) * sizeof(T));
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // not left behind for the next launch check
+        return e;
+    }
     g->allocs.push_back(v);
     *p = (T*)v;
     return cudaSuccess;

@@ -70,3 +70,4 @@ def test_sweep_1536_f64(m):
     if free < 230 * 2**30:
         pytest.skip("needs ~200 GB of free device memory (%.0f GB free)" % (free / 2**30))
     assert run_sweep(m, 1536, "f64", False, 33, 200000) <= 1e-13
+
