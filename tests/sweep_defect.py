@@ -83,3 +83,58 @@ def sweep_defect_torch(b, x_old, x_new, samples, backward=False):
     fb, fo, fn = b.reshape(-1), x_old.reshape(-1), x_new.reshape(-1)
     got = [t.double().cpu().numpy() for t in (fb[ps], fn[ps], fn[qs], fo[qs])]
     return defect(got[0], got[1], got[2].reshape(q.shape), got[3].reshape(q.shape), valid, backward)
+
+
+# ---------------------------------------------------------------------------
+# The variable-kappa 7-point operator (face coefficient k_f = (kappa_p +
+# kappa_q) / 2, a boundary face at kappa_p with a zero ghost value; Sec. 4.1
+# averaging): after a forward sweep every point satisfies
+#   a_pp x'_p = b_p + sum_{lower faces} k_f x'_q + sum_{upper faces} k_f x_q,
+# a_pp the sum of its six face coefficients; a backward sweep mirrors it.
+# ---------------------------------------------------------------------------
+FACES = [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]  # (dx, dy, dz)
+
+
+def face_neighbours(shape, p):
+    nz, ny, nx = shape
+    p = np.asarray(p, dtype=np.int64)
+    z, y, x = p // (ny * nx), (p // nx) % ny, p % nx
+    qs, oks = [], []
+    for dx, dy, dz in FACES:
+        ok = (x + dx >= 0) & (x + dx < nx) & (y + dy >= 0) & (y + dy < ny) & \
+             (z + dz >= 0) & (z + dz < nz)
+        qs.append(np.where(ok, p + (dz * ny + dy) * nx + dx, p))
+        oks.append(ok)
+    return np.stack(qs, 1), np.stack(oks, 1)
+
+
+def kappa_defect(b_p, kap_p, kap_q, xnew_p, xnew_q, xold_q, valid, backward=False):
+    """Largest residual of the 7-point sweep identity relative to the sum of
+    the magnitudes of its terms (arrays gathered at the sampled points)."""
+    lower = np.array([d[0] + d[1] + d[2] < 0 for d in FACES])
+    new = lower != backward
+    kface = np.where(valid, 0.5 * (kap_p[:, None] + kap_q), kap_p[:, None])
+    app = kface.sum(axis=1)
+    terms = np.where(valid, kface * np.where(new[None, :], xnew_q, xold_q), 0.0)
+    lhs = app * xnew_p
+    res = lhs - b_p - terms.sum(axis=1)
+    mag = np.abs(lhs) + np.abs(b_p) + np.abs(terms).sum(axis=1)
+    return float(np.max(np.abs(res) / np.maximum(mag, np.finfo(np.float64).tiny)))
+
+
+def kappa_defect_numpy(kappa, b, x_old, x_new, samples, backward=False):
+    q, valid = face_neighbours(b.shape, samples)
+    k, bf, xo, xn = kappa.reshape(-1), b.reshape(-1), x_old.reshape(-1), x_new.reshape(-1)
+    return kappa_defect(bf[samples], k[samples], k[q], xn[samples], xn[q], xo[q], valid, backward)
+
+
+def kappa_defect_torch(kappa, b, x_old, x_new, samples, backward=False):
+    import torch
+    q, valid = face_neighbours(tuple(b.shape), samples)
+    dev = b.device
+    ps = torch.from_numpy(samples).to(dev)
+    qs = torch.from_numpy(q.reshape(-1)).to(dev)
+    k, bf, xo, xn = kappa.reshape(-1), b.reshape(-1), x_old.reshape(-1), x_new.reshape(-1)
+    g = [t.double().cpu().numpy() for t in (bf[ps], k[ps], k[qs], xn[ps], xn[qs], xo[qs])]
+    return kappa_defect(g[0], g[1], g[2].reshape(q.shape), g[3], g[4].reshape(q.shape),
+                        g[5].reshape(q.shape), valid, backward)

@@ -71,3 +71,32 @@ def test_sweep_1536_f64(m):
         pytest.skip("needs ~200 GB of free device memory (%.0f GB free)" % (free / 2**30))
     assert run_sweep(m, 1536, "f64", False, 33, 200000) <= 1e-13
 
+
+
+@pytest.mark.parametrize("backward", [False, True])
+def test_kappa_sweep_256_sampled_identity(m, backward):
+    """The variable-kappa 7-point sweep at 256^3 in the benchmark's launch
+    configuration (the finest level of the kappa solve), on the benchmark's
+    kappa field: every sampled point satisfies the sweep identity
+      a_pp x'_p = b_p + sum_{lower faces} k_f x'_q + sum_{upper faces} k_f x_q
+    (tests/sweep_defect.py, pinned against the oracle in
+    tests/test_sweep_defect.py; mirrored for the backward sweep), 1e-13 of
+    the sum of the magnitudes of its terms."""
+    import torch
+    import m2s_inputs as gen
+    from sweep_defect import kappa_defect_torch
+    n = 256
+    shape = (n, n, n)
+    kap = torch.from_numpy(gen.kappa_field(n)).cuda()
+    g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.DIFF7_KAPPA, mg_levels=1, kappa=kap)])
+    try:
+        gt = torch.Generator(device="cuda").manual_seed(40 + backward)
+        b = torch.rand(shape, dtype=torch.float64, device="cuda", generator=gt) - 0.5
+        x0 = torch.rand(shape, dtype=torch.float64, device="cuda", generator=gt)
+        x = x0.clone()
+        m.m2s_gs_sweep(g.handle, 0, b, x, direction=m.BACKWARD if backward else m.FORWARD)
+        torch.cuda.synchronize()
+        pts = sample_points(shape, 200000, 41 + backward)
+        assert kappa_defect_torch(kap, b, x0, x, pts, backward=backward) <= 1e-13
+    finally:
+        g.close()

@@ -56,3 +56,37 @@ def test_sampling_includes_corners_and_is_seeded():
     n = 9 * 8 * 7
     assert 0 in a and n - 1 in a and (8 * 8 + 7) * 7 + 0 in a
     assert a.min() >= 0 and a.max() < n
+
+
+def test_kappa_oracle_sweeps_satisfy_the_identity():
+    from sweep_defect import kappa_defect_numpy
+    K7 = oracle.KAPPA7
+    for shape in [(3, 4, 5), (7, 9, 6)]:
+        kap = np.exp(gen.random_vector(shape, seed=gen.BASE_SEED + 760))
+        b, x0 = inputs(shape, 2)
+        pts = every_point(shape)
+        assert kappa_defect_numpy(kap, b, x0, oracle.gs_forward(K7, b, x0, kap), pts) <= 1e-14
+        assert kappa_defect_numpy(kap, b, x0, oracle.gs_backward(K7, b, x0, kap), pts,
+                                  backward=True) <= 1e-14
+        # a Jacobi update, the wrong direction and the 27-point sweep fail it
+        xj = x0 + (b - oracle.apply(K7, x0, kap)) / kap_diag(kap)
+        assert kappa_defect_numpy(kap, b, x0, xj, pts) > 1e-3
+        assert kappa_defect_numpy(kap, b, x0, oracle.gs_forward(K7, b, x0, kap), pts,
+                                  backward=True) > 1e-3
+        assert kappa_defect_numpy(kap, b, x0, oracle.gs_forward(H27, b, x0), pts) > 1e-3
+
+
+def kap_diag(kap):
+    """a_pp of the 7-point operator by its definition (sum of the six face
+    coefficients, boundary faces at kappa_p), independently of the oracle."""
+    nz, ny, nx = kap.shape
+    d = np.zeros_like(kap)
+    for axis in range(3):
+        for s in (-1, 1):
+            nb = np.roll(kap, -s, axis=axis)
+            face = 0.5 * (kap + nb)
+            idx = [slice(None)] * 3
+            idx[axis] = -1 if s == 1 else 0
+            face[tuple(idx)] = kap[tuple(idx)]
+            d += face
+    return d
