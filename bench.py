@@ -670,6 +670,9 @@ def main():
     m.m2s_sweep_timing(g64.handle, False)
     clk = clocks.stop()
     x64 = x.clone()
+    # the fixed-iteration form of the same workload: 50 MG-PCG iterations
+    t50 = time_cuda(torch, lambda: m.m2s_pcg_solve(g64.handle, b, x, max_iters=50,
+                                                   fixed_iters=True), 1, 1)
 
     # FP32-preconditioned form on the same problem
     for _ in range(max(1, args.warmup // 2)):
@@ -769,6 +772,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (HPCG operator, b = A*ones)", "config": workload_config(n),
         "iters_fp64": res64.iters, "rel_resid_fp64": res64.rel_resid,
+        "fp64_50_iterations_s": t50,
         "max_err_vs_ones_fp64": err64_ones,
         "fp32_precond": {"value": t32, "unit": "s", "iters": res32.iters,
                          "rel_resid": res32.rel_resid, "rel_err_vs_fp64_solution": err32,

@@ -538,9 +538,12 @@ def test_kappa_grad_and_adjoint(m):
     assert err(host(gg), go) <= 1e-9
 
 
-def test_autograd_matches_finite_differences(m):
+@pytest.mark.parametrize("n", [12, 16])
+def test_autograd_matches_finite_differences(m, n):
+    """dL/dkappa from the hand-written adjoint behind torch.autograd against
+    central differences of the loss (oracle solves), on 12^3 and on the 16^3
+    instance of the batched-adjoint workload's check."""
     import torch
-    n = 12
     kap = torch.from_numpy(gen.kappa_field(n, seed=25)).cuda().requires_grad_(True)
     b = torch.ones((n, n, n), dtype=torch.float64, device="cuda")
     ut = torch.from_numpy(gen.target((n, n, n), seed=26)).cuda()
