@@ -223,6 +223,18 @@ def profile_case(args):
         g.close()
         print("profile case block_ssor n=%d done" % n)
         return 0
+    if args.profile_case == "ilu0":
+        # one ILU(0) factorisation (one launch per hyperplane) then one
+        # application (two launches per hyperplane), every launch recorded
+        g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.HPCG27, mg_levels=1)])
+        m.m2s_ilu0_setup(g.handle)
+        r = torch.ones(shape, dtype=torch.float64, device="cuda")
+        z = torch.empty_like(r)
+        m.m2s_ilu0_apply(g.handle, r, z)
+        torch.cuda.synchronize()
+        g.close()
+        print("profile case ilu0 n=%d done (%d hyperplanes)" % (n, 7 * (n - 1) + 1))
+        return 0
     if args.profile_case == "line_btri":
         import m2s_inputs as gen
         blk, rhs = gen.line_btri_inputs(shape)
@@ -612,7 +624,7 @@ def main():
                          "variable-kappa, batched adjoint, line solves, 1536^3 SymGS)")
     ap.add_argument("--profile-case", choices=["sweep64", "sweep32", "spmv64", "spmv32",
                                                "kappa_sweep64", "block_ssor", "line_penta",
-                                               "line_btri"],
+                                               "line_btri", "ilu0"],
                     help="run a few launches of one kernel for an ncu capture and exit")
     args = ap.parse_args()
     if args.impl == "reference":
