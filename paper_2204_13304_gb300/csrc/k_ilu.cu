@@ -94,6 +94,13 @@ __global__ void __launch_bounds__(IB) ilu_factor_kernel(Dims d, int t, int z0,
     for (int o = 0; o < 27; ++o) Fp[o] = f[o];
 }
 
+// Ask L2 for the 216 bytes of factors (and, forward, the right-hand side)
+// of this row's point on the next hyperplane, x + 1 forward and x - 1
+// backward: that launch then reads them from L2 instead of HBM.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // forward: y_p = r_p - sum_{o < 13} F[p][o] y_q, y kept in z (two partial
 // sums halve the chain of dependent FMAs)
 __global__ void __launch_bounds__(IB) ilu_lower_kernel(Dims d, int t, int z0,
@@ -105,6 +112,11 @@ __global__ void __launch_bounds__(IB) ilu_lower_kernel(Dims d, int t, int z0,
     const i64 p = ((i64)zz * d.ny + y) * d.nx + x;
     const double* Fp = F + 27 * (d.off + p);
     const double* zb = z + d.off;
+    if (x + 1 < d.nx) {
+        prefetch_l2(Fp + 27);
+        prefetch_l2(Fp + 27 + 16);
+        prefetch_l2(r + d.off + p + 1);
+    }
     double s0 = r[d.off + p], s1 = 0.0;
 #pragma unroll
     for (int o = 0; o < 13; ++o)
@@ -125,6 +137,10 @@ __global__ void __launch_bounds__(IB) ilu_upper_kernel(Dims d, int t, int z0,
     const i64 p = ((i64)zz * d.ny + y) * d.nx + x;
     const double* Fp = F + 27 * (d.off + p);
     const double* zb = z + d.off;
+    if (x > 0) {
+        prefetch_l2(Fp - 27);
+        prefetch_l2(Fp - 27 + 16);
+    }
     double s0 = zb[p], s1 = 0.0;
 #pragma unroll
     for (int o = 14; o < 27; ++o)
