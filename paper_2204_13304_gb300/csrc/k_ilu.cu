@@ -66,20 +66,23 @@ __device__ __forceinline__ i64 nbr(const Dims& d, i64 p, int dx, int dy, int dz)
 }
 
 __global__ void __launch_bounds__(IB) ilu_factor_kernel(Dims d, int t, int z0,
-                                                        double* __restrict__ F) {
+                                                        double* __restrict__ F,
+                                                        double* __restrict__ Finv) {
     int x, y, z;
     if (!hyperplane_point(d, t, z0, &x, &y, &z)) return;
     const Inside in = inside_of(d, x, y, z);
     const i64 p = ((i64)z * d.ny + y) * d.nx + x;  // problem-local
     double* Fb = F + 27 * d.off;
+    double* Ib = Finv + d.off;
     double f[27];
 #pragma unroll
     for (int o = 0; o < 27; ++o) f[o] = in(odx(o), ody(o), odz(o)) ? (o == 13 ? 26.0 : -1.0) : 0.0;
 #pragma unroll
     for (int ok = 0; ok < 13; ++ok) {
         if (!in(odx(ok), ody(ok), odz(ok))) continue;
-        const double* Fk = Fb + 27 * nbr(d, p, odx(ok), ody(ok), odz(ok));
-        const double l = f[ok] / Fk[13];
+        const i64 k = nbr(d, p, odx(ok), ody(ok), odz(ok));
+        const double* Fk = Fb + 27 * k;
+        const double l = f[ok] * Ib[k];  // the pivot's rounded reciprocal
         f[ok] = l;
 #pragma unroll
         for (int oj = ok + 1; oj < 27; ++oj) {
@@ -92,6 +95,7 @@ __global__ void __launch_bounds__(IB) ilu_factor_kernel(Dims d, int t, int z0,
     double* Fp = Fb + 27 * p;
 #pragma unroll
     for (int o = 0; o < 27; ++o) Fp[o] = f[o];
+    Ib[p] = 1.0 / f[13];
 }
 
 // Ask L2 for the 216 bytes of factors (and, forward, the right-hand side)
@@ -128,9 +132,11 @@ __global__ void __launch_bounds__(IB) ilu_lower_kernel(Dims d, int t, int z0,
     z[d.off + p] = s0 + s1;
 }
 
-// backward: z_p = (y_p - sum_{o > 13} F[p][o] z_q) / F[p][13]
+// backward: z_p = (y_p - sum_{o > 13} F[p][o] z_q) / F[p][13], the division
+// as a product with the pivot's rounded reciprocal
 __global__ void __launch_bounds__(IB) ilu_upper_kernel(Dims d, int t, int z0,
-                                                       const double* __restrict__ F, double* z) {
+                                                       const double* __restrict__ F,
+                                                       const double* __restrict__ Finv, double* z) {
     int x, y, zz;
     if (!hyperplane_point(d, t, z0, &x, &y, &zz)) return;
     const Inside in = inside_of(d, x, y, zz);
@@ -140,6 +146,7 @@ __global__ void __launch_bounds__(IB) ilu_upper_kernel(Dims d, int t, int z0,
     if (x > 0) {
         prefetch_l2(Fp - 27);
         prefetch_l2(Fp - 27 + 16);
+        prefetch_l2(Finv + d.off + p - 1);
     }
     double s0 = zb[p], s1 = 0.0;
 #pragma unroll
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(IB) ilu_upper_kernel(Dims d, int t, int z0,
             if (o & 1) s1 = fma(-__ldg(Fp + o), v, s1);
             else s0 = fma(-__ldg(Fp + o), v, s0);
         }
-    z[d.off + p] = (s0 + s1) / __ldg(Fp + 13);
+    z[d.off + p] = (s0 + s1) * __ldg(Finv + d.off + p);
 }
 
 // Launch shape of hyperplane t: the z that meet it (0 <= t - 4z <= (nx-1) +
@@ -176,21 +183,21 @@ HpLaunch hyperplane_launch(const Dims& d, int t) {
 
 int ilu_hyperplanes(const Dims& d) { return (d.nx - 1) + 2 * (d.ny - 1) + 4 * (d.nz - 1) + 1; }
 
-cudaError_t launch_ilu_factor(const Dims& d, double* F, cudaStream_t st) {
+cudaError_t launch_ilu_factor(const Dims& d, double* F, double* Finv, cudaStream_t st) {
     if (d.n == 0) return cudaSuccess;
     const int T = ilu_hyperplanes(d);
     for (int t = 0; t < T; ++t) {
         const HpLaunch h = hyperplane_launch(d, t);
         if (h.grid.y == 0) continue;
-        ilu_factor_kernel<<<h.grid, h.block, 0, st>>>(d, t, h.z0, F);
+        ilu_factor_kernel<<<h.grid, h.block, 0, st>>>(d, t, h.z0, F, Finv);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* r, double* z,
-                             cudaStream_t st) {
+cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* Finv, const double* r,
+                             double* z, cudaStream_t st) {
     if (d.n == 0) return cudaSuccess;
     const int T = ilu_hyperplanes(d);
     for (int t = 0; t < T; ++t) {
@@ -203,7 +210,7 @@ cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* r, do
     for (int t = T - 1; t >= 0; --t) {
         const HpLaunch h = hyperplane_launch(d, t);
         if (h.grid.y == 0) continue;
-        ilu_upper_kernel<<<h.grid, h.block, 0, st>>>(d, t, h.z0, F, z);
+        ilu_upper_kernel<<<h.grid, h.block, 0, st>>>(d, t, h.z0, F, Finv, z);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -92,6 +92,7 @@ struct m2s_grid {
     // ILU(0) factors of the finest level (m2s_ilu0_setup) and the CUDA graph
     // of their application for the vectors (ilu_r, ilu_z)
     double* ilu_F = nullptr;
+    double* ilu_inv = nullptr;  // 1 / pivot per point
     cudaGraphExec_t ilu_graph = nullptr;
     const double* ilu_r = nullptr;
     double* ilu_z = nullptr;
@@ -1101,7 +1102,9 @@ m2s_status m2s_ilu0_setup(m2s_grid* g, void* stream) {
     if (!g || g->op != M2S_OP_HPCG27) return M2S_ERR_INVALID_ARG;
     cudaStream_t st = S(stream);
     if (!g->ilu_F) M2S_TRY(galloc(g, &g->ilu_F, 27 * g->ltot[0]));
-    for (int i = 0; i < g->np; ++i) M2S_TRY(launch_ilu_factor(g->dims[i][0], g->ilu_F, st));
+    if (!g->ilu_inv) M2S_TRY(galloc(g, &g->ilu_inv, g->ltot[0]));
+    for (int i = 0; i < g->np; ++i)
+        M2S_TRY(launch_ilu_factor(g->dims[i][0], g->ilu_F, g->ilu_inv, st));
     g->last_stream = st;
     return M2S_OK;
 }
@@ -1133,7 +1136,7 @@ m2s_status m2s_ilu0_apply(m2s_grid* g, const double* r, double* z, void* stream)
         M2S_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t ce = cudaSuccess;
         for (int i = 0; i < g->np && ce == cudaSuccess; ++i)
-            ce = launch_ilu_apply(g->dims[i][0], g->ilu_F, r, z, g->cap_stream);
+            ce = launch_ilu_apply(g->dims[i][0], g->ilu_F, g->ilu_inv, r, z, g->cap_stream);
         const cudaError_t ee = cudaStreamEndCapture(g->cap_stream, &gr);
         if (ce != cudaSuccess || ee != cudaSuccess) {
             if (gr) cudaGraphDestroy(gr);

@@ -193,9 +193,11 @@ cudaError_t launch_line_penta(int nx, int ny, int nz, int axis, const double* co
 // ILU(0) of the HPCG 27-point matrix (k_ilu.cu): factors F[n][27] over the
 // 3x3x3 box offsets; one launch per hyperplane x + 2y + 4z.
 int ilu_hyperplanes(const Dims& d);
-cudaError_t launch_ilu_factor(const Dims& d, double* F, cudaStream_t st);
-cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* r, double* z,
-                             cudaStream_t st);
+// Finv[n]: the pivots' rounded reciprocals 1/F[p][13], written by the
+// factorisation and used in place of divisions
+cudaError_t launch_ilu_factor(const Dims& d, double* F, double* Finv, cudaStream_t st);
+cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* Finv, const double* r,
+                             double* z, cudaStream_t st);
 // Block-tridiagonal (5x5) line solves (k_line.cu).
 i64 line_btri_work_doubles(int nx, int ny, int nz);
 cudaError_t launch_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* rhs,
