@@ -48,6 +48,9 @@ STREAM_PENTA = 9
 STREAM_PENTA_RHS = 10
 STREAM_BTRI = 11
 STREAM_BTRI_RHS = 12
+STREAM_JAC = 13
+STREAM_JAC_RHS = 14
+STREAM_JAC_U0 = 15
 
 BATCH_SIDES = (32, 48, 64, 96, 128)
 
@@ -126,6 +129,29 @@ def block_ssor_inputs(n, seed=BASE_SEED, shape=None):
     rhs = (2.0 * uniform(seed, STREAM_RHS, npts * 5) - 1.0).reshape(shape + (5,))
     return D, L, U, rhs
 
+
+
+def block_jac_inputs(shape, seed=BASE_SEED, sigma=10.0, nu=0.5):
+    """(P, rhs, u0) for the SSOR step whose 5x5 blocks are formed from the
+    state: P holds sigma, nu and, for k = 0..3 (point term, x, y, z), the
+    flux parameters C_k ~ U(-0.1, 0.1) (5x5), E_k ~ U(-0.05, 0.05) (5x5),
+    g_k ~ U(-0.2, 0.2) (5); rhs ~ U(-1, 1) and u0 ~ U(0, 1), (nz, ny, nx, 5).
+    With |u| <= 1.5 every entry of a Jacobian is below 0.25 in magnitude, so
+    each block row of A(u) is diagonally dominant (9.75 against < 8)."""
+    shape = tuple(shape)
+    npts = int(np.prod(shape))
+    w = uniform(seed, STREAM_JAC, 4 * 55)
+    P = np.empty(2 + 4 * 55)
+    P[0], P[1] = sigma, nu
+    for k in range(4):
+        a = w[55 * k:55 * (k + 1)]
+        base = 2 + 55 * k
+        P[base:base + 25] = 0.2 * a[:25] - 0.1
+        P[base + 25:base + 50] = 0.1 * a[25:50] - 0.05
+        P[base + 50:base + 55] = 0.4 * a[50:55] - 0.2
+    rhs = (2.0 * uniform(seed, STREAM_JAC_RHS, npts * 5) - 1.0).reshape(shape + (5,))
+    u0 = uniform(seed, STREAM_JAC_U0, npts * 5).reshape(shape + (5,))
+    return P, rhs, u0
 
 def target(shape, seed=BASE_SEED):
     """u_target ~ U(0, 1)."""

@@ -57,6 +57,8 @@ def lib():
             "or_block_lower": [_i, _i, _i, _dp, _dp, _d, _dp, _dp],
             "or_block_upper": [_i, _i, _i, _dp, _dp, _d, _dp, _dp],
             "or_ssor": [_i, _i, _i, _dp, _dp, _dp, _d, _dp, _dp, _i],
+            "or_block_jac": [_i, _i, _i, _dp, _dp, _dp, _dp, _dp],
+            "or_ssor_jac": [_i, _i, _i, _dp, _d, _dp, _dp, _i],
             "or_line_penta": [_i, _i, _i, _i, _dp, _dp, _i],
             "or_line_btri": [_i, _i, _i, _i, _dp, _dp],
             "or_ilu0_factor": [_i, _i, _i, _dp],
@@ -273,6 +275,37 @@ def ssor(D, L, U, omega, b, u, n_iters):
                   _p(b), _p(u), int(n_iters))
     return u
 
+
+JAC_PARAMS = 2 + 4 * 55
+
+
+def block_jac(P, u):
+    """(D, L, U) formed from the state u (nz, ny, nx, 5) with the parameters
+    P (222 doubles: sigma, nu, then C_k, E_k, g_k for k = 0..3):
+    D_p = sigma I + J_0(u_p), L_{p,d} = -nu I - J_{d+1}(u_{p-e_d}) / 2,
+    U_{p,d} = -nu I + J_{d+1}(u_{p+e_d}) / 2, J_k the Jacobian of the flux
+    F_k(q) = C_k q + (g_k . q) E_k q; couplings off the domain 0."""
+    P = _f64(P)
+    assert P.shape == (JAC_PARAMS,)
+    u = _f64(u)
+    nz, ny, nx, _ = u.shape
+    D = np.empty((nz, ny, nx, 5, 5))
+    L = np.empty((nz, ny, nx, 3, 5, 5))
+    U = np.empty((nz, ny, nx, 3, 5, 5))
+    lib().or_block_jac(nx, ny, nz, _p(P), _p(u), _p(D), _p(L), _p(U))
+    return D, L, U
+
+
+def ssor_jac(P, omega, b, u, n_iters):
+    """n_iters SSOR steps, each with the blocks formed from the u it starts
+    from (the NPB-LU situation: Jacobian blocks formed every step)."""
+    P = _f64(P)
+    assert P.shape == (JAC_PARAMS,)
+    b = _f64(b)
+    u = _f64(u).copy()
+    nz, ny, nx, _ = u.shape
+    lib().or_ssor_jac(nx, ny, nz, _p(P), float(omega), _p(b), _p(u), int(n_iters))
+    return u
 
 def line_penta(coef, rhs, axis):
     """Solutions of the pentadiagonal systems along the lines of `axis`

@@ -698,6 +698,89 @@ void or_ssor(int nx, int ny, int nz, const double* D, const double* L,
     free(r); free(v); free(w);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Blocks formed from the state (the NPB-LU situation of Sec. 1 and Sec.    */
+/* 4.2.3: the 5x5 blocks of the SSOR step are Jacobians evaluated at the    */
+/* current u, formed again every step instead of stored).  NPB's own flux   */
+/* formulas are not part of the paper, so the flux here is a synthetic      */
+/* quadratic one with the same data dependence: each block is a nonlinear   */
+/* function of ONE point's 5-vector.                                        */
+/*                                                                          */
+/* Parameters P, 2 + 4 * 55 doubles: sigma = P[0], nu = P[1]; for           */
+/* k = 0..3 at P + 2 + 55 k: C_k (5x5 row-major), E_k (5x5), g_k (5).       */
+/* k = 0 is the point term, k = 1, 2, 3 the x, y, z directions.             */
+/*   flux      F_k(q) = C_k q + (g_k . q) E_k q                             */
+/*   Jacobian  J_k(q) = C_k + (g_k . q) E_k + (E_k q) g_k^T                 */
+/*   D_p       = sigma I + J_0(u_p)                                         */
+/*   L_{p,d}   = -nu I - J_{d+1}(u_{p-e_d}) / 2   (p - e_d in the domain)   */
+/*   U_{p,d}   = -nu I + J_{d+1}(u_{p+e_d}) / 2   (p + e_d in the domain)   */
+/* i.e. a central difference of the flux plus a diffusion of weight nu;     */
+/* couplings that leave the domain are 0.                                   */
+/* ------------------------------------------------------------------------ */
+static void jac_block(const double* Pk, const double* q, double* J) {
+    const double* C = Pk;
+    const double* E = Pk + 25;
+    const double* g = Pk + 50;
+    double gq = 0.0, Eq[5];
+    for (int j = 0; j < 5; ++j) gq += g[j] * q[j];
+    for (int i = 0; i < 5; ++i) {
+        Eq[i] = 0.0;
+        for (int j = 0; j < 5; ++j) Eq[i] += E[i * 5 + j] * q[j];
+    }
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) J[i * 5 + j] = C[i * 5 + j] + gq * E[i * 5 + j] + Eq[i] * g[j];
+}
+
+void or_block_jac(int nx, int ny, int nz, const double* P, const double* u,
+                  double* D, double* L, double* U) {
+    const double sigma = P[0], nu = P[1];
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                i64 p = pidx(nx, ny, x, y, z);
+                double J[25];
+                jac_block(P + 2, u + p * 5, J);
+                for (int i = 0; i < 25; ++i) D[p * 25 + i] = J[i] + (i % 6 == 0 ? sigma : 0.0);
+                for (int d = 0; d < 3; ++d) {
+                    const int c[3] = {x, y, z};
+                    const int ext[3] = {nx, ny, nz};
+                    int lo[3] = {x, y, z}, hi[3] = {x, y, z};
+                    lo[d] -= 1;
+                    hi[d] += 1;
+                    double* Lb = L + (p * 3 + d) * 25;
+                    double* Ub = U + (p * 3 + d) * 25;
+                    if (c[d] > 0) {
+                        jac_block(P + 2 + 55 * (d + 1), u + pidx(nx, ny, lo[0], lo[1], lo[2]) * 5, J);
+                        for (int i = 0; i < 25; ++i) Lb[i] = -0.5 * J[i] - (i % 6 == 0 ? nu : 0.0);
+                    } else {
+                        for (int i = 0; i < 25; ++i) Lb[i] = 0.0;
+                    }
+                    if (c[d] < ext[d] - 1) {
+                        jac_block(P + 2 + 55 * (d + 1), u + pidx(nx, ny, hi[0], hi[1], hi[2]) * 5, J);
+                        for (int i = 0; i < 25; ++i) Ub[i] = 0.5 * J[i] - (i % 6 == 0 ? nu : 0.0);
+                    } else {
+                        for (int i = 0; i < 25; ++i) Ub[i] = 0.0;
+                    }
+                }
+            }
+}
+
+/* n_iters SSOR steps on u (in place), each with the blocks formed from the
+ * u it starts from: u <- u + w(2-w) M(u)^-1 (b - A(u) u). */
+void or_ssor_jac(int nx, int ny, int nz, const double* P, double omega,
+                 const double* b, double* u, int n_iters) {
+    i64 n = (i64)nx * ny * nz;
+    size_t m = (size_t)(n > 0 ? n : 1);
+    double* D = (double*)malloc(sizeof(double) * m * 25);
+    double* L = (double*)malloc(sizeof(double) * m * 75);
+    double* U = (double*)malloc(sizeof(double) * m * 75);
+    for (int it = 0; it < n_iters; ++it) {
+        or_block_jac(nx, ny, nz, P, u, D, L, U);
+        or_ssor(nx, ny, nz, D, L, U, omega, b, u, 1);
+    }
+    free(D); free(L); free(U);
+}
+
 /* Version tag so the tests can check which oracle build is loaded. */
 /* ------------------------------------------------------------------------ */
 /* Direct solves of multi-diagonal systems along grid lines (the "direct    */

@@ -533,6 +533,164 @@ def test_ssor_converges_to_dense_solution():
     assert np.max(np.abs(u.ravel() - ud)) <= 1e-12 * np.max(np.abs(ud))
 
 
+
+# --------------------------------------------------------------------------
+# Blocks formed from the state (NPB-LU's Jacobians, synthetic quadratic flux)
+# --------------------------------------------------------------------------
+def jac_parts(P, k):
+    base = 2 + 55 * k
+    return (P[base:base + 25].reshape(5, 5), P[base + 25:base + 50].reshape(5, 5),
+            P[base + 50:base + 55])
+
+
+def flux(P, k, q):
+    """F_k(q) = C_k q + (g_k . q) E_k q for q of shape (..., 5)."""
+    C, E, g = jac_parts(P, k)
+    return q @ C.T + (q @ g)[..., None] * (q @ E.T)
+
+
+def fd_jacobian(P, k, q, h=1e-3):
+    """Central-difference Jacobian of F_k at q: exact for a quadratic flux up
+    to rounding."""
+    J = np.empty((5, 5))
+    for j in range(5):
+        e = np.zeros(5)
+        e[j] = h
+        J[:, j] = (flux(P, k, q + e) - flux(P, k, q - e)) / (2 * h)
+    return J
+
+
+def test_block_jac_blocks_are_flux_jacobians():
+    """D_p - sigma I = dF_0/du at u_p; -2 (L_{p,d} + nu I) = dF_{d+1}/du at
+    u_{p-e_d}; 2 (U_{p,d} + nu I) = dF_{d+1}/du at u_{p+e_d}; couplings that
+    leave the grid are 0."""
+    shape = (3, 4, 5)
+    P, _, u = gen.block_jac_inputs(shape, seed=61)
+    D, L, U = oracle.block_jac(P, u)
+    sigma, nu = P[0], P[1]
+    nz, ny, nx = shape
+    I5 = np.eye(5)
+    for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+        assert np.max(np.abs(D[z, y, x] - sigma * I5 - fd_jacobian(P, 0, u[z, y, x]))) <= 1e-10
+        for d, (dx, dy, dz) in enumerate(((1, 0, 0), (0, 1, 0), (0, 0, 1))):
+            lo = (z - dz, y - dy, x - dx)
+            hi = (z + dz, y + dy, x + dx)
+            if min(lo) >= 0:
+                J = fd_jacobian(P, d + 1, u[lo])
+                assert np.max(np.abs(-2 * (L[z, y, x, d] + nu * I5) - J)) <= 1e-10
+            else:
+                assert not L[z, y, x, d].any()
+            if hi[0] < nz and hi[1] < ny and hi[2] < nx:
+                J = fd_jacobian(P, d + 1, u[hi])
+                assert np.max(np.abs(2 * (U[z, y, x, d] + nu * I5) - J)) <= 1e-10
+            else:
+                assert not U[z, y, x, d].any()
+
+
+def test_block_jac_depends_on_one_point_per_block():
+    """Changing u at one point q changes exactly D_q, L_{q+e_d,d} and
+    U_{q-e_d,d}, and nothing else."""
+    shape = (4, 3, 5)
+    P, _, u = gen.block_jac_inputs(shape, seed=62)
+    D0, L0, U0 = oracle.block_jac(P, u)
+    q = (2, 1, 3)
+    u2 = u.copy()
+    u2[q] += 0.25
+    D1, L1, U1 = oracle.block_jac(P, u2)
+    changed = set()
+    nz, ny, nx = shape
+    for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+        if np.any(D1[z, y, x] != D0[z, y, x]):
+            changed.add(("D", z, y, x))
+        for d in range(3):
+            if np.any(L1[z, y, x, d] != L0[z, y, x, d]):
+                changed.add(("L", z, y, x, d))
+            if np.any(U1[z, y, x, d] != U0[z, y, x, d]):
+                changed.add(("U", z, y, x, d))
+    z, y, x = q
+    want = {("D", z, y, x),
+            ("L", z, y, x + 1, 0), ("L", z, y + 1, x, 1), ("L", z + 1, y, x, 2),
+            ("U", z, y, x - 1, 0), ("U", z, y - 1, x, 1), ("U", z - 1, y, x, 2)}
+    assert changed == want
+
+
+def jac_operator_closed_form(P, u):
+    """A(u) u from the flux alone (independent of the block assembly).  With
+    J_k(q) q = 2 F_k(q) - C_k q (Euler's identity for the quadratic part) and
+    zero padding (F_k(0) = 0 drops the couplings that leave the grid):
+      (A(u) u)_p = sigma u_p + 2 F_0(u_p) - C_0 u_p - nu sum_{6 nbrs} u_q
+                   + sum_d [G_d(u_{p+e_d}) - G_d(u_{p-e_d})] / 2,
+    G_d(q) = 2 F_{d+1}(q) - C_{d+1} q."""
+    sigma, nu = P[0], P[1]
+    up = np.pad(u, ((1, 1), (1, 1), (1, 1), (0, 0)))
+    c = up[1:-1, 1:-1, 1:-1]
+    C0 = jac_parts(P, 0)[0]
+    out = sigma * c + 2 * flux(P, 0, c) - c @ C0.T
+    for d, ax in enumerate((2, 1, 0)):  # x, y, z are array axes 2, 1, 0
+        hi = np.roll(up, -1, axis=ax)[1:-1, 1:-1, 1:-1]
+        lo = np.roll(up, 1, axis=ax)[1:-1, 1:-1, 1:-1]
+        Cd = jac_parts(P, d + 1)[0]
+        G = lambda q: 2 * flux(P, d + 1, q) - q @ Cd.T  # noqa: E731
+        out = out - nu * (hi + lo) + 0.5 * (G(hi) - G(lo))
+    return out
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (1, 2, 6), (5, 1, 1)])
+def test_block_jac_operator_matches_flux_closed_form(shape):
+    P, _, u = gen.block_jac_inputs(shape, seed=63)
+    D, L, U = oracle.block_jac(P, u)
+    got = oracle.block_apply(D, L, U, u)
+    want = jac_operator_closed_form(P, u)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_ssor_jac_linear_flux_is_block_ssor_with_constant_blocks():
+    """E_k = 0, g_k = 0: the blocks no longer depend on u (D = sigma I + C_0,
+    L = -nu I - C_{d+1}/2, U = -nu I + C_{d+1}/2 inside the grid), and the
+    steps are plain block SSOR steps with those blocks."""
+    shape = (3, 4, 2)
+    P, b, u0 = gen.block_jac_inputs(shape, seed=64)
+    for k in range(4):
+        P[2 + 55 * k + 25:2 + 55 * k + 55] = 0.0
+    nz, ny, nx = shape
+    D = np.broadcast_to(P[0] * np.eye(5) + jac_parts(P, 0)[0], shape + (5, 5)).copy()
+    L = np.zeros(shape + (3, 5, 5))
+    U = np.zeros(shape + (3, 5, 5))
+    for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+        for d, c in enumerate((x, y, z)):
+            Cd = jac_parts(P, d + 1)[0]
+            n = (nx, ny, nz)[d]
+            if c > 0:
+                L[z, y, x, d] = -P[1] * np.eye(5) - 0.5 * Cd
+            if c < n - 1:
+                U[z, y, x, d] = -P[1] * np.eye(5) + 0.5 * Cd
+    got = oracle.ssor_jac(P, 1.2, b, u0, 3)
+    want = oracle.ssor(D, L, U, 1.2, b, u0, 3)
+    assert np.max(np.abs(got - want)) <= 1e-14 * np.max(np.abs(want))
+
+
+def test_ssor_jac_step_uses_blocks_of_its_start_state():
+    shape = (2, 3, 4)
+    P, b, u0 = gen.block_jac_inputs(shape, seed=65)
+    u1 = oracle.ssor_jac(P, 1.2, b, u0, 1)
+    D, L, U = oracle.block_jac(P, u0)
+    want = oracle.ssor(D, L, U, 1.2, b, u0, 1)
+    assert np.array_equal(u1, want)
+    u2 = oracle.ssor_jac(P, 1.2, b, u0, 2)
+    D, L, U = oracle.block_jac(P, u1)
+    assert np.array_equal(u2, oracle.ssor(D, L, U, 1.2, b, u1, 1))
+
+
+def test_ssor_jac_converges_to_the_nonlinear_solution():
+    """The fixed point of the steps solves A(u) u = b, checked with the
+    closed form of A(u) u (not with the oracle's blocks)."""
+    shape = (4, 3, 5)
+    P, b, u0 = gen.block_jac_inputs(shape, seed=66)
+    u = oracle.ssor_jac(P, 1.2, b, u0, 40)
+    res = b - jac_operator_closed_form(P, u)
+    assert np.max(np.abs(res)) <= 1e-12 * np.max(np.abs(b))
+    assert np.max(np.abs(b - jac_operator_closed_form(P, u0))) > 1.0
+
 # --------------------------------------------------------------------------
 # c9 / c11: inputs
 # --------------------------------------------------------------------------
