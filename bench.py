@@ -223,6 +223,17 @@ def profile_case(args):
         g.close()
         print("profile case block_ssor n=%d done" % n)
         return 0
+    if args.profile_case == "block_jac":
+        import m2s_inputs as gen
+        P, rhs, u0 = gen.block_jac_inputs(shape)
+        g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.BLOCK7_JAC, mg_levels=1, jac=P)])
+        b = torch.from_numpy(rhs).cuda()
+        u = torch.from_numpy(u0).cuda()
+        m.m2s_ssor_sweep(g.handle, b, u, 1.2, 2)
+        torch.cuda.synchronize()
+        g.close()
+        print("profile case block_jac n=%d done" % n)
+        return 0
     if args.profile_case == "ilu0":
         # one ILU(0) factorisation (one launch per hyperplane) then one
         # application (two launches per hyperplane), every launch recorded
@@ -394,6 +405,50 @@ def other_configs(m, torch, hbm):
                                   "lower sweep, update into the upper)",
                 "rel_resid_after_50": rel}
 
+    def block_jac_162():
+        # NPB-LU-style step: the blocks are formed from u at every step (fused
+        # with the residual into one pass that writes w D^-1 L, w D^-1 U and
+        # D^-1 r), then the two block sweeps
+        n = 162
+        shape = (n, n, n)
+        P, rhs, u0 = gen.block_jac_inputs(shape)
+        g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.BLOCK7_JAC, mg_levels=1, jac=P)])
+        b = torch.from_numpy(rhs).cuda()
+        u0d = torch.from_numpy(u0).cuda()
+        u = u0d.clone()
+        m.m2s_ssor_sweep(g.handle, b, u, 1.2, 1)
+        u.copy_(u0d)
+        steps = 20
+        t = time_cuda(torch, lambda: m.m2s_ssor_sweep(g.handle, b, u, 1.2, steps), 1, 0)
+        y = torch.empty_like(b)
+        m.m2s_spmv(g.handle, 0, u, y)
+        rel = float((b - y).norm() / b.norm())
+        ta = time_cuda(torch, lambda: m.m2s_spmv(g.handle, 0, u, y), 5, 1)
+        g.close()
+        pts = n ** 3
+        it = t / steps
+        ops_step = 1870 + 150  # FP64 operations per point: forming pass + two sweeps
+        ops_apply = 710 + 175
+        return {"workload": "NPB-LU-style block SSOR 162^3 x 5 unknowns with the 5x5 blocks "
+                            "formed from u every step (synthetic quadratic-flux Jacobians), "
+                            "omega 1.2, %d steps from u0 ~ U(0, 1) (FP64)" % steps,
+                "ms_per_step": it * 1e3, "steps": steps,
+                "rel_nonlinear_resid_after": rel,
+                "apply_ms": ta * 1e3,
+                "fp64_ops_per_point": {"step": ops_step, "apply": ops_apply},
+                "fp64_op_frac": {"step": ops_step * pts / it / FP64_OPS_PEAK,
+                                 "apply": ops_apply * pts / ta / FP64_OPS_PEAK},
+                "fp64_ops_note": "per interior point, an FMA one operation: forming the 7 "
+                                 "blocks 710, A(u) u 175, the inverse of D ~175, the six "
+                                 "products w D^-1 L, w D^-1 U 750, the residual 35; each "
+                                 "sweep 75 FMAs",
+                "bytes_per_point_step": 1200 + 80 + 40 + 2 * (600 + 80),
+                "bytes_note": "the forming pass reads u (40 B, neighbours from cache) and b, "
+                              "writes w D^-1 L, w D^-1 U (1200 B) and s; each sweep reads "
+                              "its 600 B of couplings; no block is stored between steps",
+                "parity": "tests/test_gpu_block_jac.py (oracle on ragged and degenerate "
+                          "shapes, batches, and one full 162^3 step entry by entry)"}
+
     def cfg5():
         sides = gen.batch_sides(64)
         kaps = [torch.from_numpy(gen.kappa_field(s_, seed=gen.BASE_SEED + i)).cuda()
@@ -564,6 +619,7 @@ def other_configs(m, torch, hbm):
     guarded("hpcg_32", cfg1)
     guarded("kappa_256", cfg4)
     guarded("block_ssor_162x5", cfg3)
+    guarded("block_jac_162x5", block_jac_162)
     guarded("batched_adjoint_64", cfg5)
     return out
 
@@ -623,7 +679,7 @@ def main():
                     help="skip the other workload configurations (32^3 SGS-PCG, block SSOR, "
                          "variable-kappa, batched adjoint, line solves, 1536^3 SymGS)")
     ap.add_argument("--profile-case", choices=["sweep64", "sweep32", "spmv64", "spmv32",
-                                               "kappa_sweep64", "block_ssor", "line_penta",
+                                               "kappa_sweep64", "block_ssor", "block_jac", "line_penta",
                                                "line_btri", "ilu0"],
                     help="run a few launches of one kernel for an ncu capture and exit")
     args = ap.parse_args()

@@ -56,7 +56,8 @@ typedef enum {
 typedef enum {
     M2S_OP_HPCG27 = 0,      /* 27-point: a_pp = 26, a_pq = -1 (HPCG) */
     M2S_OP_DIFF7_KAPPA = 1, /* 7-point variable-coefficient diffusion */
-    M2S_OP_BLOCK7_5x5 = 2   /* 7-point 5x5-block operator (NPB-LU shape) */
+    M2S_OP_BLOCK7_5x5 = 2,  /* 7-point 5x5-block operator (NPB-LU shape) */
+    M2S_OP_BLOCK7_JAC = 3   /* the same, blocks formed from the state u */
 } m2s_op;
 
 typedef enum { M2S_F64 = 0, M2S_F32 = 1 } m2s_dtype;
@@ -78,7 +79,20 @@ typedef enum { M2S_FORWARD = 0, M2S_BACKWARD = 1 } m2s_direction;
  *                  blocks: D[n][5][5] diagonal blocks, L[n][3][5][5]
  *                  couplings to p-e_x, p-e_y, p-e_z, U[n][3][5][5] to
  *                  p+e_x, p+e_y, p+e_z (ignored where they leave the grid);
- *                  copied at creation. */
+ *                  copied at creation.
+ *   jac            op = BLOCK7_JAC: HOST FP64 array of 222 parameters,
+ *                  copied at creation: sigma, nu, then for k = 0..3 (point
+ *                  term, x, y, z) C_k (5x5 row-major), E_k (5x5), g_k (5).
+ *                  The blocks are NPB-LU-style Jacobians of the synthetic
+ *                  flux F_k(q) = C_k q + (g_k . q) E_k q evaluated at the
+ *                  state, J_k(q) = C_k + (g_k . q) E_k + (E_k q) g_k^T:
+ *                    D_p     = sigma I + J_0(u_p)
+ *                    L_{p,d} = -nu I - J_{d+1}(u_{p-e_d}) / 2
+ *                    U_{p,d} = -nu I + J_{d+1}(u_{p+e_d}) / 2
+ *                  (couplings that leave the grid dropped).  They are
+ *                  formed again from u at every use and never stored.  The
+ *                  5x5 eliminations do not pivot: the caller keeps every
+ *                  block row diagonally dominant along the iteration. */
 typedef struct {
     int nx, ny, nz;
     m2s_op op;
@@ -88,6 +102,7 @@ typedef struct {
     const double* D;
     const double* L;
     const double* U;
+    const double* jac;
 } m2s_grid_desc;
 
 /* PCG options.  max_iters >= 1; rtol >= 0 (stop when |r|/|b| <= rtol);
@@ -134,7 +149,9 @@ m2s_status m2s_grid_sync(m2s_grid* grid, void* stream);
 long long m2s_grid_points(const m2s_grid* grid, int problem, int level);
 
 /* Sec. 4.3.1 SpMV on level `level`: y = A_level x (all problems of the
- * grid).  x and y must not overlap.  Op HPCG27 or DIFF7_KAPPA. */
+ * grid).  x and y must not overlap.  Op HPCG27 or DIFF7_KAPPA; for the
+ * block operators level 0, FP64, [n][5] vectors: y = A x (BLOCK7_5x5) or
+ * y = A(x) x with the blocks formed from x itself (BLOCK7_JAC). */
 m2s_status m2s_spmv(m2s_grid* grid, int level, m2s_dtype dtype,
                     const void* x, void* y, void* stream);
 
@@ -254,6 +271,9 @@ m2s_status m2s_line_btri(int nx, int ny, int nz, int axis, const double* blk,
  *   r = b - A u; lower sweep (D + omega L) v = r; upper sweep
  *   (D + omega U) w = D v; u += omega (2 - omega) w,
  * i.e. one forward and one backward block-SOR sweep per iteration.
+ * On the BLOCK7_JAC operator every iteration first forms its blocks from
+ * the u it starts from (A = A(u), the NPB-LU step with Jacobians formed
+ * every step), fused with the residual into one pass.
  * 0 < omega < 2.  u is in/out ([n][5] FP64). */
 m2s_status m2s_ssor_sweep(m2s_grid* grid, const double* b, double* u,
                           double omega, int n_iters, void* stream);

@@ -33,6 +33,10 @@ class Op(enum.IntEnum):
     HPCG27 = 0
     DIFF7_KAPPA = 1
     BLOCK7_5x5 = 2
+    BLOCK7_JAC = 3
+
+
+JAC_PARAMS = 2 + 4 * 55  # sigma, nu, (C_k, E_k, g_k) for k = 0..3
 
 
 class DType(enum.IntEnum):
@@ -54,7 +58,8 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("op", ctypes.c_int), ("mg_levels", ctypes.c_int),
                 ("precond_dtype", ctypes.c_int), ("kappa", ctypes.c_void_p),
-                ("D", ctypes.c_void_p), ("L", ctypes.c_void_p), ("U", ctypes.c_void_p)]
+                ("D", ctypes.c_void_p), ("L", ctypes.c_void_p), ("U", ctypes.c_void_p),
+                ("jac", ctypes.c_void_p)]
 
 
 class PcgOpts(ctypes.Structure):
@@ -182,8 +187,10 @@ def _dtype(t):
 
 
 def m2s_grid_create(descs, stream=None):
-    """descs: list of GridDesc (or dicts with its fields; tensors for kappa/D/L/U)."""
+    """descs: list of GridDesc (or dicts with its fields; tensors for kappa/D/L/U;
+    for op BLOCK7_JAC, `jac` the 222 host parameters, any FP64 array-like)."""
     arr = (GridDesc * len(descs))()
+    keep = []  # host parameter buffers, alive until the library has copied them
     for k, d in enumerate(descs):
         if isinstance(d, GridDesc):
             arr[k] = d
@@ -196,6 +203,12 @@ def m2s_grid_create(descs, stream=None):
         for f in ("kappa", "D", "L", "U"):
             v = d.get(f)
             setattr(g, f, _ptr(v, f) if v is not None else None)
+        if d.get("jac") is not None:
+            if len(d["jac"]) != JAC_PARAMS:
+                raise ValueError("jac needs %d parameters" % JAC_PARAMS)
+            P = (ctypes.c_double * JAC_PARAMS)(*[float(t) for t in d["jac"]])
+            keep.append(P)
+            g.jac = ctypes.cast(P, ctypes.c_void_p)
         arr[k] = g
     h = ctypes.c_void_p()
     _check(load().m2s_grid_create(arr, len(descs), _stream(stream), ctypes.byref(h)),

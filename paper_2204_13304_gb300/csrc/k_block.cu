@@ -142,6 +142,150 @@ __global__ void block_apply_kernel(Dims d, const double* __restrict__ D,
 }
 
 // ---------------------------------------------------------------------------
+// Blocks formed from the state (the NPB-LU situation of paper Sec. 1 and
+// Sec. 4.2.3: the 5x5 blocks of an SSOR step are Jacobians evaluated at the
+// current u and change every step).  Parameters, per problem, JP doubles:
+// sigma, nu, then for k = 0..3 (point term, x, y, z) C_k (5x5), E_k (5x5),
+// g_k (5).  With J_k(q) = C_k + (g_k . q) E_k + (E_k q) g_k^T, the Jacobian
+// of the flux F_k(q) = C_k q + (g_k . q) E_k q:
+//   D_p = sigma I + J_0(u_p),  L_{p,d} = -nu I - J_{d+1}(u_{p-e_d}) / 2,
+//   U_{p,d} = -nu I + J_{d+1}(u_{p+e_d}) / 2   (0 where they leave the grid).
+// One thread per point forms its seven blocks from the 5-vectors of the
+// point and its six neighbours, and in the same pass writes what the two
+// sweeps read -- M = w D^-1 L, N = w D^-1 U and s = D^-1 (b - A(u) u) -- so
+// no block is stored between steps (or y = A(u) u for the operator apply).
+// ---------------------------------------------------------------------------
+constexpr int JB = 128;  // threads per CTA of the block-forming kernel
+
+// B = sj * J_k(q) + dj I, Pk = the 55 parameters of flux k (shared memory)
+__device__ __forceinline__ void jac_form(const double* Pk, const double* q, double sj, double dj,
+                                         double* B) {
+    const double* C = Pk;
+    const double* E = Pk + 25;
+    const double* g = Pk + 50;
+    double gq = 0.0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) gq = fma(g[j], q[j], gq);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        double eq = 0.0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) eq = fma(E[i * 5 + j], q[j], eq);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const double J = fma(eq, g[j], fma(gq, E[i * 5 + j], C[i * 5 + j]));
+            B[i * 5 + j] = i == j ? fma(sj, J, dj) : sj * J;
+        }
+    }
+}
+
+// In-place inverse of a 5x5 matrix, Gauss-Jordan without pivoting (the
+// diagonal blocks are diagonally dominant): 125 FMAs and 5 reciprocals.
+__device__ __forceinline__ void inv5_inplace(double* a) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double piv = 1.0 / a[k * 5 + k];
+        a[k * 5 + k] = 1.0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) a[k * 5 + j] *= piv;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if (i == k) continue;
+            const double f = a[i * 5 + k];
+            a[i * 5 + k] = 0.0;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) a[i * 5 + j] = fma(-f, a[k * 5 + j], a[i * 5 + j]);
+        }
+    }
+}
+
+template <bool SSOR>
+__global__ void __launch_bounds__(JB) block_jac_kernel(Dims d, const double* __restrict__ Pg,
+                                                       double omega, const double* __restrict__ b,
+                                                       const double* __restrict__ u,
+                                                       double* __restrict__ out,
+                                                       double* __restrict__ M,
+                                                       double* __restrict__ N) {
+    __shared__ double P[JP];
+    for (int k = threadIdx.x; k < JP; k += blockDim.x) P[k] = Pg[k];
+    __syncthreads();
+    const i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    int x, y, z;
+    coords(i, d.nx, d.ny, &x, &y, &z);
+    const i64 p = d.off + i;
+    const i64 st[3] = {1, d.nx, (i64)d.nx * d.ny};
+    const bool lo[3] = {x > 0, y > 0, z > 0};
+    const bool hi[3] = {x < d.nx - 1, y < d.ny - 1, z < d.nz - 1};
+    double q[5], B[25], acc[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) q[c] = u[p * 5 + c];
+    jac_form(P + 2, q, 1.0, P[0], B);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) s = fma(B[r * 5 + c], q[c], s);
+        acc[r] = s;
+    }
+    double Di[25];  // w D^-1 (the products below need it scaled by w)
+    if constexpr (SSOR) {
+#pragma unroll
+        for (int k = 0; k < 25; ++k) Di[k] = B[k];
+        inv5_inplace(Di);
+#pragma unroll
+        for (int k = 0; k < 25; ++k) Di[k] *= omega;
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int dd = 0; dd < 3; ++dd) {
+            const bool in = side == 0 ? lo[dd] : hi[dd];
+            double* Ob = SSOR ? (side == 0 ? M : N) + (p * 3 + dd) * 25 : nullptr;
+            if (in) {
+                const i64 qn = side == 0 ? p - st[dd] : p + st[dd];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) q[c] = u[qn * 5 + c];
+                jac_form(P + 2 + 55 * (dd + 1), q, side == 0 ? -0.5 : 0.5, -P[1], B);
+#pragma unroll
+                for (int r = 0; r < 5; ++r)
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) acc[r] = fma(B[r * 5 + c], q[c], acc[r]);
+                if constexpr (SSOR) {
+#pragma unroll
+                    for (int r = 0; r < 5; ++r)
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) {
+                            double s = 0.0;
+#pragma unroll
+                            for (int k = 0; k < 5; ++k) s = fma(Di[r * 5 + k], B[k * 5 + c], s);
+                            Ob[r * 5 + c] = s;
+                        }
+                }
+            } else if constexpr (SSOR) {
+#pragma unroll
+                for (int k = 0; k < 25; ++k) Ob[k] = 0.0;
+            }
+        }
+    if constexpr (SSOR) {
+        double rr[5];
+        const double iw = 1.0 / omega;
+#pragma unroll
+        for (int r = 0; r < 5; ++r) rr[r] = b[p * 5 + r] - acc[r];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) s = fma(Di[r * 5 + c], rr[c], s);
+            out[p * 5 + r] = s * iw;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 5; ++r) out[p * 5 + r] = acc[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Block sweeps as a CTA wavefront (the design of the 7-point sweep in
 // k_wave7.cu, with a group of five lanes per grid point).  A unit is a CTA of
 // BW warps, warp w owning plane z = z0 + w; lane 5g + c of a warp holds
@@ -394,16 +538,25 @@ cudaError_t block_create(BlockOp* b, const m2s_grid_desc* descs, int n_problems,
     }
     const size_t n = (size_t)std::max<i64>(b->npts, 1);
     cudaError_t e;
-    if ((e = alloc((void**)&b->D, n * 25 * 8)) != cudaSuccess) return e;
-    if ((e = alloc((void**)&b->L, n * 75 * 8)) != cudaSuccess) return e;
-    if ((e = alloc((void**)&b->U, n * 75 * 8)) != cudaSuccess) return e;
-    if ((e = alloc((void**)&b->Dinv, n * 25 * 8)) != cudaSuccess) return e;
+    b->jac = descs[0].op == M2S_OP_BLOCK7_JAC;
+    if (b->jac) {
+        if ((e = alloc((void**)&b->P, (size_t)n_problems * JP * 8)) != cudaSuccess) return e;
+        for (int i = 0; i < n_problems; ++i)
+            if ((e = cudaMemcpyAsync(b->P + (size_t)i * JP, descs[i].jac, JP * 8,
+                                     cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return e;
+    } else {
+        if ((e = alloc((void**)&b->D, n * 25 * 8)) != cudaSuccess) return e;
+        if ((e = alloc((void**)&b->L, n * 75 * 8)) != cudaSuccess) return e;
+        if ((e = alloc((void**)&b->U, n * 75 * 8)) != cudaSuccess) return e;
+        if ((e = alloc((void**)&b->Dinv, n * 25 * 8)) != cudaSuccess) return e;
+    }
     if ((e = alloc((void**)&b->M, n * 75 * 8)) != cudaSuccess) return e;
     if ((e = alloc((void**)&b->N, n * 75 * 8)) != cudaSuccess) return e;
     if ((e = alloc((void**)&b->s, n * 5 * 8)) != cudaSuccess) return e;
     if ((e = alloc((void**)&b->v, n * 5 * 8)) != cudaSuccess) return e;
     if ((e = alloc((void**)&b->w, n * 5 * 8)) != cudaSuccess) return e;
-    for (int i = 0; i < n_problems; ++i) {
+    for (int i = 0; i < n_problems && !b->jac; ++i) {
         const Dims& d = b->dims[i];
         if ((e = cudaMemcpyAsync(b->D + d.off * 25, descs[i].D, d.n * 25 * 8,
                                  cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
@@ -471,8 +624,12 @@ cudaError_t block_apply(BlockOp* b, const double* u, double* y, cudaStream_t st)
     for (int i = 0; i < b->np; ++i) {
         const Dims& d = b->dims[i];
         if (d.n == 0) continue;
-        block_apply_kernel<false><<<nblk(d.n, 128), 128, 0, st>>>(d, b->D, b->L, b->U, nullptr,
-                                                                  nullptr, u, y);
+        if (b->jac)
+            block_jac_kernel<false><<<nblk(d.n, JB), JB, 0, st>>>(d, b->P + (size_t)i * JP, 0.0,
+                                                                  nullptr, u, y, nullptr, nullptr);
+        else
+            block_apply_kernel<false><<<nblk(d.n, 128), 128, 0, st>>>(d, b->D, b->L, b->U, nullptr,
+                                                                      nullptr, u, y);
     }
     return cudaGetLastError();
 }
@@ -480,7 +637,16 @@ cudaError_t block_apply(BlockOp* b, const double* u, double* y, cudaStream_t st)
 cudaError_t block_ssor_iter(BlockOp* b, const double* rhs, double* u, double omega,
                             DevStatus* status, long long spin_ns, cudaStream_t st) {
     cudaError_t e;
-    if (omega != b->omega) {
+    if (b->jac) {
+        // blocks of this step from the u it starts from: M, N and s in one pass
+        for (int i = 0; i < b->np; ++i) {
+            const Dims& d = b->dims[i];
+            if (d.n == 0) continue;
+            block_jac_kernel<true><<<nblk(d.n, JB), JB, 0, st>>>(d, b->P + (size_t)i * JP, omega,
+                                                                 rhs, u, b->s, b->M, b->N);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else if (omega != b->omega) {
         for (int i = 0; i < b->np; ++i) {
             const Dims& d = b->dims[i];
             if (d.n == 0) continue;
@@ -491,7 +657,7 @@ cudaError_t block_ssor_iter(BlockOp* b, const double* rhs, double* u, double ome
         b->omega = omega;
     }
     const double cu = omega * (2.0 - omega);
-    for (int i = 0; i < b->np; ++i) {
+    for (int i = 0; i < b->np && !b->jac; ++i) {
         const Dims& d = b->dims[i];
         if (d.n == 0) continue;
         block_apply_kernel<true><<<nblk(d.n, 128), 128, 0, st>>>(d, b->D, b->L, b->U, b->Dinv,

@@ -603,6 +603,8 @@ const char* m2s_status_string(m2s_status s) {
     return "unknown status";
 }
 
+static bool is_block(m2s_op op) { return op == M2S_OP_BLOCK7_5x5 || op == M2S_OP_BLOCK7_JAC; }
+
 m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* stream,
                            m2s_grid** out) {
     if (!out) return M2S_ERR_INVALID_ARG;
@@ -611,8 +613,7 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     const m2s_op op = descs[0].op;
     const int levels = descs[0].mg_levels;
     const m2s_dtype pdt = descs[0].precond_dtype;
-    if (op != M2S_OP_HPCG27 && op != M2S_OP_DIFF7_KAPPA && op != M2S_OP_BLOCK7_5x5)
-        return M2S_ERR_INVALID_ARG;
+    if (op != M2S_OP_HPCG27 && op != M2S_OP_DIFF7_KAPPA && !is_block(op)) return M2S_ERR_INVALID_ARG;
     if (levels < 1 || levels > kMaxLevels) return M2S_ERR_INVALID_ARG;
     if (pdt != M2S_F64 && pdt != M2S_F32) return M2S_ERR_INVALID_ARG;
     for (int i = 0; i < n_problems; ++i) {
@@ -622,13 +623,14 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
         if ((i64)d.nx * d.ny * d.nz > (1LL << 34)) return M2S_ERR_INVALID_ARG;
         if (op == M2S_OP_DIFF7_KAPPA && (!d.kappa || !aligned(d.kappa, 8))) return M2S_ERR_INVALID_ARG;
         if (op == M2S_OP_BLOCK7_5x5 && (!d.D || !d.L || !d.U)) return M2S_ERR_INVALID_ARG;
+        if (op == M2S_OP_BLOCK7_JAC && !d.jac) return M2S_ERR_INVALID_ARG;
     }
     cudaStream_t st = S(stream);
     m2s_grid* g = new (std::nothrow) m2s_grid();
     if (!g) return M2S_ERR_OOM;
     g->np = n_problems;
     g->op = op;
-    g->levels = op == M2S_OP_BLOCK7_5x5 ? 1 : levels;
+    g->levels = is_block(op) ? 1 : levels;
     g->pdtype = pdt;
     g->has32 = op == M2S_OP_HPCG27 || (op == M2S_OP_DIFF7_KAPPA && pdt == M2S_F32);
     const int L = g->levels;
@@ -664,7 +666,7 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     if ((e = cudaMemsetAsync(g->dev, 0, n_problems * sizeof(PcgDev), st)) != cudaSuccess)
         return fail(e);
 
-    if (op == M2S_OP_BLOCK7_5x5) {
+    if (is_block(op)) {
         e = block_create(&g->blk, descs, n_problems, g->dims, st,
                          [g](void** p, size_t bytes) -> cudaError_t {
                              cudaError_t ee = cudaMalloc(p, bytes);
@@ -816,7 +818,7 @@ m2s_status m2s_grid_destroy(m2s_grid* grid) {
 }
 
 m2s_status m2s_debug_stall_unit(m2s_grid* grid, int level, int unit) {
-    if (!valid_level(grid, level) || unit < 0 || grid->op == M2S_OP_BLOCK7_5x5)
+    if (!valid_level(grid, level) || unit < 0 || is_block(grid->op))
         return M2S_ERR_INVALID_ARG;
     grid->stall_level = level;
     grid->stall_unit = unit;
@@ -963,7 +965,7 @@ m2s_status m2s_grid_sync(m2s_grid* grid, void* stream) {
 
 m2s_status m2s_spmv(m2s_grid* g, int level, m2s_dtype dtype, const void* x, void* y, void* stream) {
     if (!valid_level(g, level) || !x || !y || x == y) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5) {
+    if (is_block(g->op)) {
         if (dtype != M2S_F64) return M2S_ERR_INVALID_ARG;
         return cuda_status(block_apply(&g->blk, (const double*)x, (double*)y, S(stream)));
     }
@@ -976,7 +978,7 @@ m2s_status m2s_spmv(m2s_grid* g, int level, m2s_dtype dtype, const void* x, void
 m2s_status m2s_symgs(m2s_grid* g, int level, m2s_dtype dtype, const void* b, void* x,
                      int n_sym_sweeps, void* stream) {
     if (!valid_level(g, level) || !b || !x || b == x || n_sym_sweeps < 0) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (m2s_status cs = check_dtype(g, dtype)) return cs;
     if (n_sym_sweeps == 0) return M2S_OK;
     if (dtype == M2S_F64)
@@ -990,7 +992,7 @@ m2s_status m2s_gs_sweep(m2s_grid* g, int level, m2s_dtype dtype, const void* b, 
                         m2s_direction direction, void* stream) {
     if (!valid_level(g, level) || !b || !x || b == x) return M2S_ERR_INVALID_ARG;
     if (direction != M2S_FORWARD && direction != M2S_BACKWARD) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (m2s_status cs = check_dtype(g, dtype)) return cs;
     const int rev = direction == M2S_BACKWARD;
     if (dtype == M2S_F64)
@@ -1003,7 +1005,7 @@ m2s_status m2s_gs_sweep(m2s_grid* g, int level, m2s_dtype dtype, const void* b, 
 m2s_status m2s_mg_restrict(m2s_grid* g, int level, m2s_dtype dtype, const void* r, const void* z,
                            void* rc, void* stream) {
     if (!g || level < 0 || level + 1 >= g->levels || !r || !z || !rc) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (m2s_status cs = check_dtype(g, dtype)) return cs;
     if (dtype == M2S_F64)
         M2S_TRY(op_restrict<double>(g, level, (const double*)r, (const double*)z, (double*)rc, nullptr,
@@ -1017,7 +1019,7 @@ m2s_status m2s_mg_restrict(m2s_grid* g, int level, m2s_dtype dtype, const void* 
 m2s_status m2s_mg_prolong(m2s_grid* g, int level, m2s_dtype dtype, const void* zc, void* z,
                           void* stream) {
     if (!g || level < 0 || level + 1 >= g->levels || !zc || !z) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (m2s_status cs = check_dtype(g, dtype)) return cs;
     for (int i = 0; i < g->np; ++i) {
         const Dims f = g->dims[i][level], c = g->dims[i][level + 1];
@@ -1029,7 +1031,7 @@ m2s_status m2s_mg_prolong(m2s_grid* g, int level, m2s_dtype dtype, const void* z
 
 m2s_status m2s_mg_vcycle(m2s_grid* g, m2s_dtype dtype, const void* r, void* z, void* stream) {
     if (!g || !r || !z || r == z) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (m2s_status cs = check_dtype(g, dtype)) return cs;
     if (dtype == M2S_F64)
         M2S_TRY(vcycle_from<double>(g, (const double*)r, (double*)z, S(stream)));
@@ -1041,7 +1043,7 @@ m2s_status m2s_mg_vcycle(m2s_grid* g, m2s_dtype dtype, const void* r, void* z, v
 m2s_status m2s_pcg_solve(m2s_grid* g, const double* b, double* x, const m2s_pcg_opts* opts,
                          m2s_pcg_result* out, void* stream) {
     if (!g || !b || !x || !opts || b == x) return M2S_ERR_INVALID_ARG;
-    if (g->op == M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     m2s_pcg_opts o = *opts;
     if (o.max_iters < 1 || o.max_iters > g->hist_cap || !(o.rtol >= 0)) return M2S_ERR_INVALID_ARG;
     if (o.check_every < 1) o.check_every = 1;
@@ -1182,7 +1184,7 @@ m2s_status m2s_line_btri(int nx, int ny, int nz, int axis, const double* blk, do
 
 m2s_status m2s_ssor_sweep(m2s_grid* g, const double* b, double* u, double omega, int n_iters,
                           void* stream) {
-    if (!g || !b || !u || b == u || g->op != M2S_OP_BLOCK7_5x5) return M2S_ERR_INVALID_ARG;
+    if (!g || !b || !u || b == u || !is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (!(omega > 0.0 && omega < 2.0) || n_iters < 0) return M2S_ERR_INVALID_ARG;
     for (int it = 0; it < n_iters; ++it)
         M2S_TRY(block_ssor_iter(&g->blk, b, u, omega, g->status, g->spin_ns, S(stream)));

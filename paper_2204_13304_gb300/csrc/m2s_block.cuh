@@ -7,11 +7,15 @@
 
 namespace m2s {
 
+constexpr int JP = 2 + 4 * 55;  // parameters of the blocks formed from the state
+
 struct BlockOp {
     int np = 0;
+    bool jac = false;           // blocks formed from u every step (op BLOCK7_JAC)
+    double* P = nullptr;        // [np][JP] their parameters (op BLOCK7_JAC)
     std::vector<Dims> dims;     // per problem (points; vectors hold 5 per point)
     i64 npts = 0;               // total points
-    double* D = nullptr;        // [npts][25]
+    double* D = nullptr;        // [npts][25] (op BLOCK7_5x5; D, L, U, Dinv unused for BLOCK7_JAC)
     double* L = nullptr;        // [npts][3][25]  couplings to p - e_{x,y,z}
     double* U = nullptr;        // [npts][3][25]  couplings to p + e_{x,y,z}
     double* Dinv = nullptr;     // [npts][25]

@@ -62,11 +62,27 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     d[0].mg_levels, d[0].op = 2, 1  # kappa operator without kappa
     assert lib.m2s_grid_create(d, 1, None, ctypes.byref(h)) == m.Status.INVALID_ARG
     assert lib.m2s_grid_create(d, 0, None, ctypes.byref(h)) == m.Status.INVALID_ARG
+    d[0].mg_levels, d[0].op = 1, m.Op.BLOCK7_JAC  # blocks from the state without parameters
+    assert lib.m2s_grid_create(d, 1, None, ctypes.byref(h)) == m.Status.INVALID_ARG
+    d[0].op = 4  # no such operator
+    assert lib.m2s_grid_create(d, 1, None, ctypes.byref(h)) == m.Status.INVALID_ARG
+    assert not h.value
     assert lib.m2s_spmv(None, 0, 0, None, None, None) == m.Status.INVALID_ARG
     assert lib.m2s_symgs(None, 0, 0, None, None, 1, None) == m.Status.INVALID_ARG
     assert lib.m2s_pcg_solve(None, None, None, None, None, None) == m.Status.INVALID_ARG
     assert lib.m2s_ssor_sweep(None, None, None, 1.2, 1, None) == m.Status.INVALID_ARG
     assert lib.m2s_grid_destroy(None) == m.Status.OK
+
+
+def test_grid_desc_layout_matches_header():
+    """The ctypes descriptor has the header's fields in the header's order."""
+    import re
+    import paper_2204_13304_gb300 as m
+    hdr = open(os.path.join(ROOT, "include", "m2s.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\} m2s_grid_desc;", hdr).group(1)
+    names = re.findall(r"(\w+)(?:\s*,\s*(\w+))?(?:\s*,\s*(\w+))?;", body)
+    fields = [n for group in names for n in group if n]
+    assert fields == [f[0] for f in m.GridDesc._fields_]
 
 
 def test_library_is_sm103a_only():
