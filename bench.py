@@ -406,9 +406,9 @@ def other_configs(m, torch, hbm):
                 "rel_resid_after_50": rel}
 
     def block_jac_162():
-        # NPB-LU-style step: the blocks are formed from u at every step (fused
-        # with the residual into one pass that writes w D^-1 L, w D^-1 U and
-        # D^-1 r), then the two block sweeps
+        # NPB-LU-style step: the blocks are formed from u at every step (one
+        # pass forms each Jacobian once and scatters its two blocks, a second
+        # assembles the residual), then the two block sweeps apply w D^-1
         n = 162
         shape = (n, n, n)
         P, rhs, u0 = gen.block_jac_inputs(shape)
@@ -427,7 +427,9 @@ def other_configs(m, torch, hbm):
         g.close()
         pts = n ** 3
         it = t / steps
-        ops_step = 1870 + 150  # FP64 operations per point: forming pass + two sweeps
+        # FP64 operations per point: forming pass, residual pass, two sweeps (an
+        # FMA one operation; the sweeps' 20 FP64 instructions per lane-step)
+        ops_step = 775 + 30 + 2 * 100
         ops_apply = 710 + 175
         return {"workload": "NPB-LU-style block SSOR 162^3 x 5 unknowns with the 5x5 blocks "
                             "formed from u every step (synthetic quadratic-flux Jacobians), "
@@ -438,14 +440,16 @@ def other_configs(m, torch, hbm):
                 "fp64_ops_per_point": {"step": ops_step, "apply": ops_apply},
                 "fp64_op_frac": {"step": ops_step * pts / it / FP64_OPS_PEAK,
                                  "apply": ops_apply * pts / ta / FP64_OPS_PEAK},
-                "fp64_ops_note": "per interior point, an FMA one operation: forming the 7 "
-                                 "blocks 710, A(u) u 175, the inverse of D ~175, the six "
-                                 "products w D^-1 L, w D^-1 U 750, the residual 35; each "
-                                 "sweep 75 FMAs",
-                "bytes_per_point_step": 1200 + 80 + 40 + 2 * (600 + 80),
-                "bytes_note": "the forming pass reads u (40 B, neighbours from cache) and b, "
-                              "writes w D^-1 L, w D^-1 U (1200 B) and s; each sweep reads "
-                              "its 600 B of couplings; no block is stored between steps",
+                "fp64_ops_note": "per point: the forming pass 775 (D and D u 110, w D^-1 200, "
+                                 "three Jacobians with their two blocks and J u 465), the "
+                                 "residual pass 30, each sweep 100 (20 per lane-step, 5 lanes); "
+                                 "the apply forms all seven blocks itself (710) and applies "
+                                 "them (175)",
+                "bytes_per_point_step": 80 + 1560 + 240 + 2 * (800 + 80),
+                "bytes_note": "the forming pass reads u and b and writes L, U (1200 B), "
+                              "w D^-1 (200 B), J u (120 B) and b - D u; the residual pass "
+                              "reads those and writes r / w; each sweep reads its 600 B of "
+                              "couplings and 200 B of w D^-1; no block outlives its step",
                 "parity": "tests/test_gpu_block_jac.py (oracle on ragged and degenerate "
                           "shapes, batches, and one full 162^3 step entry by entry)"}
 

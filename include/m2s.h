@@ -273,7 +273,8 @@ m2s_status m2s_line_btri(int nx, int ny, int nz, int axis, const double* blk,
  * i.e. one forward and one backward block-SOR sweep per iteration.
  * On the BLOCK7_JAC operator every iteration first forms its blocks from
  * the u it starts from (A = A(u), the NPB-LU step with Jacobians formed
- * every step), fused with the residual into one pass.
+ * every step): one pass over the points forms each Jacobian once, a second
+ * assembles the residual; no block is kept after the iteration.
  * 0 < omega < 2.  u is in/out ([n][5] FP64). */
 m2s_status m2s_ssor_sweep(m2s_grid* grid, const double* b, double* u,
                           double omega, int n_iters, void* stream);

@@ -10,6 +10,8 @@
 // which is (D + wL) v = r and (D + wU) w = D v with D^-1 applied once per
 // point per step instead of one 5x5 elimination per point per sweep: the
 // products w D^-1 L and w D^-1 U are formed once per omega at set-up.
+// Where the blocks are formed from u every step (op BLOCK7_JAC, below), the
+// products are not formed at all: the sweeps apply w D^-1 themselves.
 //
 // The sweeps run on the wavefront machinery of k_wave.cu (hyperplane
 // x + y + z, one progress counter per unit, ticketed units), with FIVE lanes
@@ -150,10 +152,20 @@ __global__ void block_apply_kernel(Dims d, const double* __restrict__ D,
 // of the flux F_k(q) = C_k q + (g_k . q) E_k q:
 //   D_p = sigma I + J_0(u_p),  L_{p,d} = -nu I - J_{d+1}(u_{p-e_d}) / 2,
 //   U_{p,d} = -nu I + J_{d+1}(u_{p+e_d}) / 2   (0 where they leave the grid).
-// One thread per point forms its seven blocks from the 5-vectors of the
-// point and its six neighbours, and in the same pass writes what the two
-// sweeps read -- M = w D^-1 L, N = w D^-1 U and s = D^-1 (b - A(u) u) -- so
-// no block is stored between steps (or y = A(u) u for the operator apply).
+// Each Jacobian J_d(u_q) (d = x, y, z) serves two blocks, L_{q+e_d,d} and
+// U_{q-e_d,d}, so the forming pass scatters: the thread of point q forms
+// J_0(u_q) and its three J_d(u_q) once, writes the two blocks of each into
+// the slots of q + e_d and q - e_d (zero where no neighbour writes a slot),
+// w D_q^-1, the flux products h_d(q) = J_d(u_q) u_q and b_q - D_q u_q.  A
+// second, memory-bound pass assembles the residual from them,
+//   r_p = b_p - D_p u_p + sum_d [nu (u_{p-e_d} + u_{p+e_d})
+//                                + h_d(p-e_d) / 2 - h_d(p+e_d) / 2],
+// since L_{p,d} u_{p-e_d} = -nu u_{p-e_d} - h_d(p-e_d) / 2 (and U likewise).
+// The sweeps then apply w D^-1 to their neighbour sums (the DI form of
+// block_warp): forming the products w D^-1 L and w D^-1 U here would cost
+// 750 more FP64 operations per point in a pass bound by the FP64 pipe.  No
+// block outlives its step.  The operator apply y = A(u) u (block_jac_apply
+// kernel) gathers instead: one thread forms the seven blocks of its point.
 // ---------------------------------------------------------------------------
 constexpr int JB = 128;  // threads per CTA of the block-forming kernel
 
@@ -199,13 +211,10 @@ __device__ __forceinline__ void inv5_inplace(double* a) {
     }
 }
 
-template <bool SSOR>
-__global__ void __launch_bounds__(JB) block_jac_kernel(Dims d, const double* __restrict__ Pg,
-                                                       double omega, const double* __restrict__ b,
-                                                       const double* __restrict__ u,
-                                                       double* __restrict__ out,
-                                                       double* __restrict__ M,
-                                                       double* __restrict__ N) {
+// y = A(u) u, the blocks of point p formed from u_p and its neighbours
+__global__ void __launch_bounds__(JB) block_jac_apply_kernel(Dims d, const double* __restrict__ Pg,
+                                                             const double* __restrict__ u,
+                                                             double* __restrict__ out) {
     __shared__ double P[JP];
     for (int k = threadIdx.x; k < JP; k += blockDim.x) P[k] = Pg[k];
     __syncthreads();
@@ -217,72 +226,134 @@ __global__ void __launch_bounds__(JB) block_jac_kernel(Dims d, const double* __r
     const i64 st[3] = {1, d.nx, (i64)d.nx * d.ny};
     const bool lo[3] = {x > 0, y > 0, z > 0};
     const bool hi[3] = {x < d.nx - 1, y < d.ny - 1, z < d.nz - 1};
-    double q[5], B[25], acc[5];
+    double q[5], B[25], acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    auto add = [&](const double* Pk, i64 qi, double sj, double dj) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) q[c] = u[qi * 5 + c];
+        jac_form(Pk, q, sj, dj, B);
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) acc[r] = fma(B[r * 5 + c], q[c], acc[r]);
+    };
+    add(P + 2, p, 1.0, P[0]);
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+        if (lo[dd]) add(P + 2 + 55 * (dd + 1), p - st[dd], -0.5, -P[1]);
+        if (hi[dd]) add(P + 2 + 55 * (dd + 1), p + st[dd], 0.5, -P[1]);
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) out[p * 5 + r] = acc[r];
+}
+
+// The forming pass of an SSOR step (scatter form, see above).  Outputs:
+// Lo/Up [n][3][25] the blocks L, U; Dinv [n][25] w D^-1; h [n][3][5] the
+// flux products; w0 [n][5] b - D u.
+__global__ void __launch_bounds__(JB) block_jac_form_kernel(Dims d, const double* __restrict__ Pg,
+                                                            double omega,
+                                                            const double* __restrict__ b,
+                                                            const double* __restrict__ u,
+                                                            double* __restrict__ Lo,
+                                                            double* __restrict__ Up,
+                                                            double* __restrict__ Dinv,
+                                                            double* __restrict__ h,
+                                                            double* __restrict__ w0) {
+    __shared__ double P[JP];
+    for (int k = threadIdx.x; k < JP; k += blockDim.x) P[k] = Pg[k];
+    __syncthreads();
+    const i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    int x, y, z;
+    coords(i, d.nx, d.ny, &x, &y, &z);
+    const i64 p = d.off + i;
+    const i64 st[3] = {1, d.nx, (i64)d.nx * d.ny};
+    const bool lo[3] = {x > 0, y > 0, z > 0};
+    const bool hi[3] = {x < d.nx - 1, y < d.ny - 1, z < d.nz - 1};
+    const double nu = P[1];
+    double q[5], B[25];
 #pragma unroll
     for (int c = 0; c < 5; ++c) q[c] = u[p * 5 + c];
-    jac_form(P + 2, q, 1.0, P[0], B);
+    jac_form(P + 2, q, 1.0, P[0], B);  // D_p
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
         double s = 0.0;
 #pragma unroll
         for (int c = 0; c < 5; ++c) s = fma(B[r * 5 + c], q[c], s);
-        acc[r] = s;
+        w0[p * 5 + r] = b[p * 5 + r] - s;
     }
-    double Di[25];  // w D^-1 (the products below need it scaled by w)
-    if constexpr (SSOR) {
+    inv5_inplace(B);
 #pragma unroll
-        for (int k = 0; k < 25; ++k) Di[k] = B[k];
-        inv5_inplace(Di);
+    for (int k = 0; k < 25; ++k) Dinv[p * 25 + k] = omega * B[k];
 #pragma unroll
-        for (int k = 0; k < 25; ++k) Di[k] *= omega;
-    }
-#pragma unroll
-    for (int side = 0; side < 2; ++side)
-#pragma unroll
-        for (int dd = 0; dd < 3; ++dd) {
-            const bool in = side == 0 ? lo[dd] : hi[dd];
-            double* Ob = SSOR ? (side == 0 ? M : N) + (p * 3 + dd) * 25 : nullptr;
-            if (in) {
-                const i64 qn = side == 0 ? p - st[dd] : p + st[dd];
-#pragma unroll
-                for (int c = 0; c < 5; ++c) q[c] = u[qn * 5 + c];
-                jac_form(P + 2 + 55 * (dd + 1), q, side == 0 ? -0.5 : 0.5, -P[1], B);
-#pragma unroll
-                for (int r = 0; r < 5; ++r)
-#pragma unroll
-                    for (int c = 0; c < 5; ++c) acc[r] = fma(B[r * 5 + c], q[c], acc[r]);
-                if constexpr (SSOR) {
-#pragma unroll
-                    for (int r = 0; r < 5; ++r)
-#pragma unroll
-                        for (int c = 0; c < 5; ++c) {
-                            double s = 0.0;
-#pragma unroll
-                            for (int k = 0; k < 5; ++k) s = fma(Di[r * 5 + k], B[k * 5 + c], s);
-                            Ob[r * 5 + c] = s;
-                        }
-                }
-            } else if constexpr (SSOR) {
-#pragma unroll
-                for (int k = 0; k < 25; ++k) Ob[k] = 0.0;
-            }
-        }
-    if constexpr (SSOR) {
-        double rr[5];
-        const double iw = 1.0 / omega;
-#pragma unroll
-        for (int r = 0; r < 5; ++r) rr[r] = b[p * 5 + r] - acc[r];
+    for (int dd = 0; dd < 3; ++dd) {
+        jac_form(P + 2 + 55 * (dd + 1), q, 1.0, 0.0, B);  // J_d(u_p)
 #pragma unroll
         for (int r = 0; r < 5; ++r) {
             double s = 0.0;
 #pragma unroll
-            for (int c = 0; c < 5; ++c) s = fma(Di[r * 5 + c], rr[c], s);
-            out[p * 5 + r] = s * iw;
+            for (int c = 0; c < 5; ++c) s = fma(B[r * 5 + c], q[c], s);
+            h[(p * 3 + dd) * 5 + r] = s;
         }
-    } else {
+        // L of the point above in d reads u_p; so does U of the point below
+        // (each slot has exactly one writer)
+        if (hi[dd]) {
+            double* Lb = Lo + ((p + st[dd]) * 3 + dd) * 25;
 #pragma unroll
-        for (int r = 0; r < 5; ++r) out[p * 5 + r] = acc[r];
+            for (int k = 0; k < 25; ++k) Lb[k] = fma(-0.5, B[k], k % 6 == 0 ? -nu : 0.0);
+        }
+        if (lo[dd]) {
+            double* Ub = Up + ((p - st[dd]) * 3 + dd) * 25;
+#pragma unroll
+            for (int k = 0; k < 25; ++k) Ub[k] = fma(0.5, B[k], k % 6 == 0 ? -nu : 0.0);
+        }
+        // the slots no neighbour writes: this point's own L (U) where the
+        // grid ends below (above) it in d
+        if (!lo[dd]) {
+            double* Z = Lo + (p * 3 + dd) * 25;
+#pragma unroll
+            for (int k = 0; k < 25; ++k) Z[k] = 0.0;
+        }
+        if (!hi[dd]) {
+            double* Z = Up + (p * 3 + dd) * 25;
+#pragma unroll
+            for (int k = 0; k < 25; ++k) Z[k] = 0.0;
+        }
     }
+}
+
+// r / w at every point from the forming pass's outputs (memory-bound)
+__global__ void block_jac_resid_kernel(Dims d, const double* __restrict__ u,
+                                       const double* __restrict__ h,
+                                       const double* __restrict__ w0, double nu, double iw,
+                                       double* __restrict__ out) {
+    const i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    int x, y, z;
+    coords(i, d.nx, d.ny, &x, &y, &z);
+    const i64 p = d.off + i;
+    const i64 st[3] = {1, d.nx, (i64)d.nx * d.ny};
+    const bool lo[3] = {x > 0, y > 0, z > 0};
+    const bool hi[3] = {x < d.nx - 1, y < d.ny - 1, z < d.nz - 1};
+    double acc[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) acc[r] = w0[p * 5 + r];
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+        if (lo[dd]) {
+            const i64 q = p - st[dd];
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                acc[r] = fma(0.5, h[(q * 3 + dd) * 5 + r], fma(nu, u[q * 5 + r], acc[r]));
+        }
+        if (hi[dd]) {
+            const i64 q = p + st[dd];
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                acc[r] = fma(-0.5, h[(q * 3 + dd) * 5 + r], fma(nu, u[q * 5 + r], acc[r]));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) out[p * 5 + r] = acc[r] * iw;
 }
 
 // ---------------------------------------------------------------------------
@@ -303,6 +374,7 @@ __global__ void __launch_bounds__(JB) block_jac_kernel(Dims d, const double* __r
 constexpr int BW = 8;      // warps (planes) per unit
 constexpr int BROWS = 5;   // computing rows (groups 1-5) per unit
 constexpr int BD = 2;      // prefetch depth in steps
+constexpr int BD_DI = 1;   // the same with D^-1 applied in the sweep
 
 struct BlockCtaArgs {
     int rev;
@@ -319,6 +391,7 @@ struct BlockCtaArgs {
     DevStatus* status;
     int stall_unit;
     cta::u64* mbox;      // per point and component one tagged value (2 words)
+    const double* dinv;  // DI form only: [n][25] w D^-1 (coup then holds L or U)
 };
 
 struct BlockShared {
@@ -326,6 +399,16 @@ struct BlockShared {
     volatile int prog[BW];
 };
 
+// DI = false: coup holds M = w D^-1 L (N = w D^-1 U) and a step is
+//   v_p = s_p - sum_d M_{p,d} v_{p-e_d}   (w_p = v_p - sum_d N_{p,d} w_{p+e_d}).
+// DI = true (blocks formed every step, so the products are not formed):
+// coup holds L (U) itself, dinv holds w D^-1, the lower rhs r / w, and a
+// step applies w D^-1 to the neighbour sum,
+//   v_p = w D_p^-1 (r_p / w - sum_d L_{p,d} v_{p-e_d})
+//   w_p = v_p - w D_p^-1 sum_d U_{p,d} w_{p+e_d},
+// lane c taking row c of w D_p^-1 and the group's five sums by shuffles:
+// 20 FP64 instructions per step against 15 for the product form.
+template <bool DI, int PD>
 __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, BlockShared& sh,
                                            unsigned tag) {
     using namespace cta;
@@ -353,13 +436,16 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
     const double* R = a.rhs + dm.off * 5;
     double* O = a.out + dm.off * 5;
     double* U = a.u ? a.u + dm.off * 5 : nullptr;
+    const double* Dv = DI ? a.dinv + dm.off * 25 : nullptr;
     u64* const mbox = a.mbox + dm.off * 10;  // 5 components x 2 words per point
     const int S = nx + BROWS + 1 + BW;
 
-    // prefetch: the lane's rows of the three coupling blocks and its rhs
-    // component (computing lanes), its component of the replayed row
-    // (group 0), its component of the plane below (warp 0)
-    double pc[BD][15], pr[BD], pm0[BD], pm1[BD];
+    // prefetch: the lane's rows of the three coupling blocks, its rhs
+    // component and (backward sweep) its component of u (computing lanes),
+    // its component of the replayed row (group 0), its component of the
+    // plane below (warp 0).  u[p] is written only by this lane's own step at
+    // p, so the value fetched PD steps ahead is the one the update needs.
+    double pc[PD][15], pr[PD], pu[PD], pm0[PD], pm1[PD], pd[PD][DI ? 5 : 1];
     auto fetch = [&](int k, int s) {
         const int xx = s - g - w;
         const bool in = rv && (unsigned)xx < (unsigned)nx;
@@ -373,11 +459,16 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
         if (in && halo) tw_to_regs(mb_load<double>(mbox, p * 5 + c), &m0, &m1);
         if (in && !halo && zmb) tw_to_regs(mb_load<double>(mbox, (p - szd) * 5 + c), &m0, &m1);
         pr[k] = (in && !halo) ? __ldg(R + p * 5 + c) : 0.0;
+        pu[k] = (in && !halo && U) ? U[p * 5 + c] : 0.0;
+        if constexpr (DI) {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) pd[k][j] = (in && !halo) ? __ldg(Dv + p * 25 + c * 5 + j) : 0.0;
+        }
         pm0[k] = m0;
         pm1[k] = m1;
     };
 #pragma unroll
-    for (int k = 0; k < BD; ++k) fetch(k, k);
+    for (int k = 0; k < PD; ++k) fetch(k, k);
 
     double xprev = 0.0;  // this lane's component at the previous step
     bool ok = true;
@@ -398,8 +489,11 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
         double cf[15];
 #pragma unroll
         for (int j = 0; j < 15; ++j) cf[j] = pc[k][j];
-        const double rh = pr[k], m0 = pm0[k], m1 = pm1[k];
-        fetch(k, s + BD);
+        const double rh = pr[k], uo = pu[k], m0 = pm0[k], m1 = pm1[k];
+        double di[DI ? 5 : 1];
+#pragma unroll
+        for (int j = 0; j < (DI ? 5 : 1); ++j) di[j] = pd[k][j];
+        fetch(k, s + PD);
         const bool in = rv && (unsigned)xx < (unsigned)nx;
         const bool comp = in && !halo;
         double X = 0.0, zc = 0.0;
@@ -428,8 +522,10 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
         }
         // neighbour 5-vectors: x - 1 (own group, previous step), y - 1 (the
         // group below, previous step), z - 1 (warp below / unit underneath)
+        // (one chain: the sweep is bound by the number of FP64 instructions
+        // it issues, so no extra partial sums)
         const int gy = g >= 1 && g < 6 ? gb - 5 : 0;
-        double acc = rh;
+        double acc = DI && a.rev ? 0.0 : rh;
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
             const double vx = __shfl_sync(FULL, xprev, gb + j);
@@ -439,11 +535,19 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
             acc = fma(-cf[5 + j], vy, acc);
             acc = fma(-cf[10 + j], vz, acc);
         }
+        if constexpr (DI) {
+            // dinv holds w D^-1 and the lower rhs r / w: lower
+            // X = w D^-1 (r / w - L v); upper X = v + w D^-1 (-U w)
+            double e = a.rev ? rh : 0.0;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) e = fma(di[j], __shfl_sync(FULL, acc, gb + j), e);
+            acc = e;
+        }
         if (comp) {
             X = acc;
             const i64 p = L + dir * xx;
             O[p * 5 + c] = X;
-            if (U) U[p * 5 + c] = fma(a.cu, X, U[p * 5 + c]);
+            if (U) U[p * 5 + c] = fma(a.cu, X, uo);
             if (mb_out) mb_store<double>(mbox, p * 5 + c, X, tag);
         } else if (!in) {
             X = 0.0;
@@ -478,15 +582,16 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
         __syncwarp();
         if (lane == 0) sh.prog[w] = s;
     };
-    for (int s0 = 0; ok && s0 < S; s0 += BD) {
+    for (int s0 = 0; ok && s0 < S; s0 += PD) {
 #pragma unroll
-        for (int k = 0; k < BD; ++k)
+        for (int k = 0; k < PD; ++k)
             if (ok) step(s0 + k, k);
     }
     __syncwarp();
     if (lane == 0) sh.prog[w] = INT_MAX;
 }
 
+template <bool DI>
 __global__ void __launch_bounds__(BW * 32, 1) block_cta_kernel(BlockCtaArgs a) {
     __shared__ int s_ticket;
     __shared__ unsigned s_tag;
@@ -505,7 +610,7 @@ __global__ void __launch_bounds__(BW * 32, 1) block_cta_kernel(BlockCtaArgs a) {
         int ab = 0;
         if (threadIdx.x == 0) ab = ld_relaxed_gpu(&a.status->abort) || t == a.stall_unit;
         ab = __syncthreads_or(ab);
-        if (!ab) block_warp(a, t, warp, sh, s_tag);
+        if (!ab) block_warp<DI, DI ? BD_DI : BD>(a, t, warp, sh, s_tag);
         __syncthreads();
     }
     __syncthreads();
@@ -541,6 +646,10 @@ cudaError_t block_create(BlockOp* b, const m2s_grid_desc* descs, int n_problems,
     b->jac = descs[0].op == M2S_OP_BLOCK7_JAC;
     if (b->jac) {
         if ((e = alloc((void**)&b->P, (size_t)n_problems * JP * 8)) != cudaSuccess) return e;
+        if ((e = alloc((void**)&b->Dinv, n * 25 * 8)) != cudaSuccess) return e;
+        if ((e = alloc((void**)&b->h, n * 15 * 8)) != cudaSuccess) return e;
+        b->nu.resize(n_problems);
+        for (int i = 0; i < n_problems; ++i) b->nu[i] = descs[i].jac[1];
         for (int i = 0; i < n_problems; ++i)
             if ((e = cudaMemcpyAsync(b->P + (size_t)i * JP, descs[i].jac, JP * 8,
                                      cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -608,9 +717,10 @@ cudaError_t block_create(BlockOp* b, const m2s_grid_desc* descs, int n_problems,
         (e = cudaMemset(u.d_mbox, 0, n * 10 * sizeof(unsigned long long))) != cudaSuccess)
         return e;
     const int smem = (int)sizeof(BlockShared);
-    cudaFuncSetAttribute(block_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto sweep = b->jac ? block_cta_kernel<true> : block_cta_kernel<false>;
+    cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_cta_kernel, BW * 32,
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep, BW * 32,
                                                            smem)) != cudaSuccess)
         return e;
     u.grid = wave_grid(u.n_units, per_sm);
@@ -625,8 +735,7 @@ cudaError_t block_apply(BlockOp* b, const double* u, double* y, cudaStream_t st)
         const Dims& d = b->dims[i];
         if (d.n == 0) continue;
         if (b->jac)
-            block_jac_kernel<false><<<nblk(d.n, JB), JB, 0, st>>>(d, b->P + (size_t)i * JP, 0.0,
-                                                                  nullptr, u, y, nullptr, nullptr);
+            block_jac_apply_kernel<<<nblk(d.n, JB), JB, 0, st>>>(d, b->P + (size_t)i * JP, u, y);
         else
             block_apply_kernel<false><<<nblk(d.n, 128), 128, 0, st>>>(d, b->D, b->L, b->U, nullptr,
                                                                       nullptr, u, y);
@@ -638,12 +747,20 @@ cudaError_t block_ssor_iter(BlockOp* b, const double* rhs, double* u, double ome
                             DevStatus* status, long long spin_ns, cudaStream_t st) {
     cudaError_t e;
     if (b->jac) {
-        // blocks of this step from the u it starts from: M, N and s in one pass
+        // blocks of this step from the u it starts from: L, U (in M, N),
+        // w D^-1, then s = r / w (b - D u parked in v until the lower sweep)
         for (int i = 0; i < b->np; ++i) {
             const Dims& d = b->dims[i];
             if (d.n == 0) continue;
-            block_jac_kernel<true><<<nblk(d.n, JB), JB, 0, st>>>(d, b->P + (size_t)i * JP, omega,
-                                                                 rhs, u, b->s, b->M, b->N);
+            block_jac_form_kernel<<<nblk(d.n, JB), JB, 0, st>>>(d, b->P + (size_t)i * JP, omega,
+                                                                rhs, u, b->M, b->N, b->Dinv, b->h,
+                                                                b->v);
+        }
+        for (int i = 0; i < b->np; ++i) {
+            const Dims& d = b->dims[i];
+            if (d.n == 0) continue;
+            block_jac_resid_kernel<<<nblk(d.n, 256), 256, 0, st>>>(d, u, b->h, b->v, b->nu[i],
+                                                                   1.0 / omega, b->s);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else if (omega != b->omega) {
@@ -674,14 +791,16 @@ cudaError_t block_ssor_iter(BlockOp* b, const double* rhs, double* u, double ome
     a.status = status;
     a.stall_unit = -1;
     a.mbox = un.d_mbox;
-    // lower sweep: v = s - M v (increasing p)
+    a.dinv = b->Dinv;
+    auto sweep = b->jac ? block_cta_kernel<true> : block_cta_kernel<false>;
+    // lower sweep: v = s - M v (increasing p), or v = D^-1 (r - w L v)
     a.rev = 0;
     a.coup = b->M;
     a.rhs = b->s;
     a.out = b->v;
     a.u = nullptr;
     a.cu = 0.0;
-    block_cta_kernel<<<un.grid, BW * 32, sizeof(BlockShared), st>>>(a);
+    sweep<<<un.grid, BW * 32, sizeof(BlockShared), st>>>(a);
     // upper sweep: w = v - N w (decreasing p), u += w(2-w) w
     a.rev = 1;
     a.coup = b->N;
@@ -689,7 +808,7 @@ cudaError_t block_ssor_iter(BlockOp* b, const double* rhs, double* u, double ome
     a.out = b->w;
     a.u = u;
     a.cu = cu;
-    block_cta_kernel<<<un.grid, BW * 32, sizeof(BlockShared), st>>>(a);
+    sweep<<<un.grid, BW * 32, sizeof(BlockShared), st>>>(a);
     return cudaGetLastError();
 }
 

@@ -13,14 +13,16 @@ struct BlockOp {
     int np = 0;
     bool jac = false;           // blocks formed from u every step (op BLOCK7_JAC)
     double* P = nullptr;        // [np][JP] their parameters (op BLOCK7_JAC)
+    double* h = nullptr;        // [npts][3][5] flux products J_d(u_q) u_q (op BLOCK7_JAC)
+    std::vector<double> nu;     // per problem: nu of its parameters (op BLOCK7_JAC)
     std::vector<Dims> dims;     // per problem (points; vectors hold 5 per point)
     i64 npts = 0;               // total points
     double* D = nullptr;        // [npts][25] (op BLOCK7_5x5; D, L, U, Dinv unused for BLOCK7_JAC)
     double* L = nullptr;        // [npts][3][25]  couplings to p - e_{x,y,z}
     double* U = nullptr;        // [npts][3][25]  couplings to p + e_{x,y,z}
-    double* Dinv = nullptr;     // [npts][25]
-    double* M = nullptr;        // [npts][3][25]  omega D^-1 L (0 off the grid)
-    double* N = nullptr;        // [npts][3][25]  omega D^-1 U (0 off the grid)
+    double* Dinv = nullptr;     // [npts][25] (BLOCK7_JAC: w D^-1 of the current step)
+    double* M = nullptr;        // [npts][3][25]  omega D^-1 L (0 off the grid; BLOCK7_JAC: L)
+    double* N = nullptr;        // [npts][3][25]  omega D^-1 U (0 off the grid; BLOCK7_JAC: U)
     double* s = nullptr;        // [npts][5] D^-1 (b - A u)
     double* v = nullptr;        // [npts][5] lower-sweep result
     double* w = nullptr;        // [npts][5] upper-sweep result
