@@ -246,44 +246,74 @@ __global__ void __launch_bounds__(JB) block_jac_apply_kernel(Dims d, const doubl
     for (int r = 0; r < 5; ++r) out[p * 5 + r] = acc[r];
 }
 
+// Warp-wide store of W values per lane, staged in shared memory: each lane
+// has put its values at sb[lane * W + k]; the lane's values go to
+// dst[target + 0..W-1] (target < 0: nowhere).  The warp copies in runs of
+// 32 consecutive values, so a store request covers a few contiguous runs
+// instead of 32 scattered 8-byte words.
+template <int W>
+__device__ __forceinline__ void warp_flush(const double* __restrict__ sb, i64* __restrict__ tg,
+                                           int lane, i64 target, double* __restrict__ dst) {
+    tg[lane] = target;
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < W; ++it) {
+        const int idx = it * 32 + lane;  // = pt * W + k
+        const int pt = idx / W;
+        const i64 t = tg[pt];
+        if (t >= 0) dst[t + (idx - pt * W)] = sb[idx];
+    }
+    __syncwarp();
+}
+
 // The forming pass of an SSOR step (scatter form, see above).  Outputs:
 // Lo/Up [n][3][25] the blocks L, U; Dinv [n][25] w D^-1; h [n][3][5] the
-// flux products; w0 [n][5] b - D u.
-__global__ void __launch_bounds__(JB) block_jac_form_kernel(Dims d, const double* __restrict__ Pg,
-                                                            double omega,
-                                                            const double* __restrict__ b,
-                                                            const double* __restrict__ u,
-                                                            double* __restrict__ Lo,
-                                                            double* __restrict__ Up,
-                                                            double* __restrict__ Dinv,
-                                                            double* __restrict__ h,
-                                                            double* __restrict__ w0) {
+// flux products; w0 [n][5] b - D u.  Every lane of a warp takes part in its
+// staged stores (lanes past the last point store nothing).
+__global__ void __launch_bounds__(JB, 3) block_jac_form_kernel(Dims d, const double* __restrict__ Pg,
+                                                               double omega,
+                                                               const double* __restrict__ b,
+                                                               const double* __restrict__ u,
+                                                               double* __restrict__ Lo,
+                                                               double* __restrict__ Up,
+                                                               double* __restrict__ Dinv,
+                                                               double* __restrict__ h,
+                                                               double* __restrict__ w0) {
     __shared__ double P[JP];
+    __shared__ double sbuf[JB / 32][32 * 25];
+    __shared__ double hbuf[JB / 32][32 * 15];
+    __shared__ i64 stgt[JB / 32][32];
     for (int k = threadIdx.x; k < JP; k += blockDim.x) P[k] = Pg[k];
     __syncthreads();
+    const int lane = threadIdx.x & 31;
+    double* sb = sbuf[threadIdx.x >> 5];
+    double* hb = hbuf[threadIdx.x >> 5];
+    i64* tg = stgt[threadIdx.x >> 5];
     const i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
-    int x, y, z;
-    coords(i, d.nx, d.ny, &x, &y, &z);
-    const i64 p = d.off + i;
+    const bool valid = i < d.n;
+    int x = 0, y = 0, z = 0;
+    if (valid) coords(i, d.nx, d.ny, &x, &y, &z);
+    const i64 p = d.off + (valid ? i : 0);
     const i64 st[3] = {1, d.nx, (i64)d.nx * d.ny};
     const bool lo[3] = {x > 0, y > 0, z > 0};
     const bool hi[3] = {x < d.nx - 1, y < d.ny - 1, z < d.nz - 1};
     const double nu = P[1];
     double q[5], B[25];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) q[c] = u[p * 5 + c];
+    for (int c = 0; c < 5; ++c) q[c] = valid ? u[p * 5 + c] : 0.0;
     jac_form(P + 2, q, 1.0, P[0], B);  // D_p
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
         double s = 0.0;
 #pragma unroll
         for (int c = 0; c < 5; ++c) s = fma(B[r * 5 + c], q[c], s);
-        w0[p * 5 + r] = b[p * 5 + r] - s;
+        sb[lane * 5 + r] = (valid ? b[p * 5 + r] : 0.0) - s;
     }
+    warp_flush<5>(sb, tg, lane, valid ? p * 5 : -1, w0);
     inv5_inplace(B);
 #pragma unroll
-    for (int k = 0; k < 25; ++k) Dinv[p * 25 + k] = omega * B[k];
+    for (int k = 0; k < 25; ++k) sb[lane * 25 + k] = omega * B[k];
+    warp_flush<25>(sb, tg, lane, valid ? p * 25 : -1, Dinv);
 #pragma unroll
     for (int dd = 0; dd < 3; ++dd) {
         jac_form(P + 2 + 55 * (dd + 1), q, 1.0, 0.0, B);  // J_d(u_p)
@@ -292,33 +322,30 @@ __global__ void __launch_bounds__(JB) block_jac_form_kernel(Dims d, const double
             double s = 0.0;
 #pragma unroll
             for (int c = 0; c < 5; ++c) s = fma(B[r * 5 + c], q[c], s);
-            h[(p * 3 + dd) * 5 + r] = s;
+            hb[lane * 15 + dd * 5 + r] = s;
         }
         // L of the point above in d reads u_p; so does U of the point below
         // (each slot has exactly one writer)
-        if (hi[dd]) {
-            double* Lb = Lo + ((p + st[dd]) * 3 + dd) * 25;
 #pragma unroll
-            for (int k = 0; k < 25; ++k) Lb[k] = fma(-0.5, B[k], k % 6 == 0 ? -nu : 0.0);
-        }
-        if (lo[dd]) {
-            double* Ub = Up + ((p - st[dd]) * 3 + dd) * 25;
+        for (int k = 0; k < 25; ++k) sb[lane * 25 + k] = fma(-0.5, B[k], k % 6 == 0 ? -nu : 0.0);
+        warp_flush<25>(sb, tg, lane, valid && hi[dd] ? ((p + st[dd]) * 3 + dd) * 25 : -1, Lo);
 #pragma unroll
-            for (int k = 0; k < 25; ++k) Ub[k] = fma(0.5, B[k], k % 6 == 0 ? -nu : 0.0);
-        }
+        for (int k = 0; k < 25; ++k) sb[lane * 25 + k] = fma(0.5, B[k], k % 6 == 0 ? -nu : 0.0);
+        warp_flush<25>(sb, tg, lane, valid && lo[dd] ? ((p - st[dd]) * 3 + dd) * 25 : -1, Up);
         // the slots no neighbour writes: this point's own L (U) where the
         // grid ends below (above) it in d
-        if (!lo[dd]) {
-            double* Z = Lo + (p * 3 + dd) * 25;
+        if (valid && !lo[dd]) {
+            double* Zb = Lo + (p * 3 + dd) * 25;
 #pragma unroll
-            for (int k = 0; k < 25; ++k) Z[k] = 0.0;
+            for (int k = 0; k < 25; ++k) Zb[k] = 0.0;
         }
-        if (!hi[dd]) {
-            double* Z = Up + (p * 3 + dd) * 25;
+        if (valid && !hi[dd]) {
+            double* Zb = Up + (p * 3 + dd) * 25;
 #pragma unroll
-            for (int k = 0; k < 25; ++k) Z[k] = 0.0;
+            for (int k = 0; k < 25; ++k) Zb[k] = 0.0;
         }
     }
+    warp_flush<15>(hb, tg, lane, valid ? p * 15 : -1, h);
 }
 
 // r / w at every point from the forming pass's outputs (memory-bound)
