@@ -17,14 +17,14 @@ struct BlockOp {
     std::vector<double> nu;     // per problem: nu of its parameters (op BLOCK7_JAC)
     std::vector<Dims> dims;     // per problem (points; vectors hold 5 per point)
     i64 npts = 0;               // total points
-    double* D = nullptr;        // [npts][25] (op BLOCK7_5x5; D, L, U, Dinv unused for BLOCK7_JAC)
+    double* D = nullptr;        // [npts][25] (op BLOCK7_5x5; D, L, U not allocated for BLOCK7_JAC)
     double* L = nullptr;        // [npts][3][25]  couplings to p - e_{x,y,z}
     double* U = nullptr;        // [npts][3][25]  couplings to p + e_{x,y,z}
     double* Dinv = nullptr;     // [npts][25] (BLOCK7_JAC: w D^-1 of the current step)
     double* M = nullptr;        // [npts][3][25]  omega D^-1 L (0 off the grid; BLOCK7_JAC: L)
     double* N = nullptr;        // [npts][3][25]  omega D^-1 U (0 off the grid; BLOCK7_JAC: U)
-    double* s = nullptr;        // [npts][5] D^-1 (b - A u)
-    double* v = nullptr;        // [npts][5] lower-sweep result
+    double* s = nullptr;        // [npts][5] D^-1 (b - A u) (BLOCK7_JAC: (b - A(u) u) / w)
+    double* v = nullptr;        // [npts][5] lower-sweep result (BLOCK7_JAC: b - D u until then)
     double* w = nullptr;        // [npts][5] upper-sweep result
     double omega = -1.0;        // omega that M and N were built for
     WaveUnits sweep;            // CTA wavefront units of all problems (one launch)
