@@ -1,13 +1,18 @@
-"""Full-size parity of the Gauss-Seidel sweeps, where the serial oracle
-cannot run: every sampled point of a sweep must satisfy the sweep identity of
-Sec. 4.3.3 (tests/sweep_defect.py, pinned against the oracle on the CPU in
-tests/test_sweep_defect.py).
+"""Full-size parity of the sweeps.  Where the serial oracle cannot run, every
+sampled point of a sweep must satisfy the sweep identity of Sec. 4.3.3
+(tests/sweep_defect.py, pinned against the oracle on the CPU in
+tests/test_sweep_defect.py); where it can (the block SSOR), the whole result
+is compared with it.
 
 * 256^3 in the launch configuration of the benchmark's solve (FP64: 8-warp
   units, prefetch depth 2; FP32: 8-warp units, depth 8), forward and
   backward;
 * 1536^3 FP64, the paper's SymGS micro-benchmark grid (Sec. 7.2.1): 3.6 G
-  rows, 29 GB per vector; the test holds about 200 GB of device memory.
+  rows, 29 GB per vector; the test holds about 200 GB of device memory;
+* the variable-kappa 7-point sweep at 256^3 (the same identity with face
+  coefficients);
+* the NPB-LU-shaped block SSOR at 162^3 x 5, where the serial oracle does
+  run (two steps in a few seconds): compared entry by entry.
 
 Inputs: b = A*ones (the HPCG right-hand side) and a seeded uniform x0 drawn
 on the device, so both the new and the old neighbour values enter every
@@ -100,3 +105,35 @@ def test_kappa_sweep_256_sampled_identity(m, backward):
         assert kappa_defect_torch(kap, b, x0, x, pts, backward=backward) <= 1e-13
     finally:
         g.close()
+
+
+def test_block_ssor_162_full_size_steps(m):
+    """The NPB-LU-shaped block SSOR at 162^3 x 5 (the benchmark's workload and
+    launch configuration): two steps from u = 0 against the serial oracle,
+    every entry.  The oracle's two steps take a few seconds on one host core
+    and ~6 GB of host memory for the blocks.  Tolerance: normwise,
+    max|g - o| / max(|o|_inf, |u|_inf) <= 1e-13 (each step's residual sums
+    terms of the size of D u ~ 10 |u| and cancels them; the per-entry error
+    is reported)."""
+    import torch
+    import m2s_inputs as gen
+    import oracle
+    n = 162
+    D, L, U, b = gen.block_ssor_inputs(n)
+    dd, ld, ud = [torch.from_numpy(a).cuda() for a in (D, L, U)]
+    g = m.Grid([dict(nx=n, ny=n, nz=n, op=m.Op.BLOCK7_5x5, mg_levels=1, D=dd, L=ld, U=ud)])
+    try:
+        del dd, ld, ud
+        u = torch.zeros((n, n, n, 5), dtype=torch.float64, device="cuda")
+        m.m2s_ssor_sweep(g.handle, torch.from_numpy(b).cuda(), u, 1.2, 2)
+        m.m2s_grid_sync(g.handle)
+        got = u.cpu().numpy()
+    finally:
+        g.close()
+        torch.cuda.empty_cache()
+    want = oracle.ssor(D, L, U, 1.2, b, np.zeros((n, n, n, 5)), 2)
+    d = np.abs(got - want)
+    scale = float(np.max(np.abs(want)))
+    per_entry = float(np.max(d / np.maximum(np.abs(want), 1e-2 * scale)))
+    assert float(np.max(d)) / scale <= 1e-13, "normwise %.3g (per entry %.3g)" % (
+        float(np.max(d)) / scale, per_entry)
