@@ -267,9 +267,10 @@ __device__ __forceinline__ void warp_flush(const double* __restrict__ sb, i64* _
 }
 
 // The forming pass of an SSOR step (scatter form, see above).  Outputs:
-// Lo/Up [n][3][25] the blocks L, U; Dinv [n][25] w D^-1; h [n][3][5] the
-// flux products; w0 [n][5] b - D u.  Every lane of a warp takes part in its
-// staged stores (lanes past the last point store nothing).
+// Lo/Up [n][3][25] the blocks L, U; Dinv [n][25] w D^-1; h [3][n][5] the
+// flux products (one array per direction, so that the residual pass reads
+// its neighbours' contiguously); w0 [n][5] b - D u.  Every lane of a warp
+// takes part in its staged stores (lanes past the last point store nothing).
 __global__ void __launch_bounds__(JB, 3) block_jac_form_kernel(Dims d, const double* __restrict__ Pg,
                                                                double omega,
                                                                const double* __restrict__ b,
@@ -277,17 +278,17 @@ __global__ void __launch_bounds__(JB, 3) block_jac_form_kernel(Dims d, const dou
                                                                double* __restrict__ Lo,
                                                                double* __restrict__ Up,
                                                                double* __restrict__ Dinv,
-                                                               double* __restrict__ h,
+                                                               double* __restrict__ h, i64 nall,
                                                                double* __restrict__ w0) {
     __shared__ double P[JP];
     __shared__ double sbuf[JB / 32][32 * 25];
-    __shared__ double hbuf[JB / 32][32 * 15];
+    __shared__ double hbuf[JB / 32][3][32 * 5];
     __shared__ i64 stgt[JB / 32][32];
     for (int k = threadIdx.x; k < JP; k += blockDim.x) P[k] = Pg[k];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     double* sb = sbuf[threadIdx.x >> 5];
-    double* hb = hbuf[threadIdx.x >> 5];
+    double(*hb)[32 * 5] = hbuf[threadIdx.x >> 5];
     i64* tg = stgt[threadIdx.x >> 5];
     const i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x;
     const bool valid = i < d.n;
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(JB, 3) block_jac_form_kernel(Dims d, const dou
             double s = 0.0;
 #pragma unroll
             for (int c = 0; c < 5; ++c) s = fma(B[r * 5 + c], q[c], s);
-            hb[lane * 15 + dd * 5 + r] = s;
+            hb[dd][lane * 5 + r] = s;
         }
         // L of the point above in d reads u_p; so does U of the point below
         // (each slot has exactly one writer)
@@ -345,12 +346,13 @@ __global__ void __launch_bounds__(JB, 3) block_jac_form_kernel(Dims d, const dou
             for (int k = 0; k < 25; ++k) Zb[k] = 0.0;
         }
     }
-    warp_flush<15>(hb, tg, lane, valid ? p * 15 : -1, h);
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) warp_flush<5>(hb[dd], tg, lane, valid ? p * 5 : -1, h + dd * nall * 5);
 }
 
 // r / w at every point from the forming pass's outputs (memory-bound)
 __global__ void block_jac_resid_kernel(Dims d, const double* __restrict__ u,
-                                       const double* __restrict__ h,
+                                       const double* __restrict__ h, i64 nall,
                                        const double* __restrict__ w0, double nu, double iw,
                                        double* __restrict__ out) {
     const i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x;
@@ -370,13 +372,13 @@ __global__ void block_jac_resid_kernel(Dims d, const double* __restrict__ u,
             const i64 q = p - st[dd];
 #pragma unroll
             for (int r = 0; r < 5; ++r)
-                acc[r] = fma(0.5, h[(q * 3 + dd) * 5 + r], fma(nu, u[q * 5 + r], acc[r]));
+                acc[r] = fma(0.5, h[(dd * nall + q) * 5 + r], fma(nu, u[q * 5 + r], acc[r]));
         }
         if (hi[dd]) {
             const i64 q = p + st[dd];
 #pragma unroll
             for (int r = 0; r < 5; ++r)
-                acc[r] = fma(-0.5, h[(q * 3 + dd) * 5 + r], fma(nu, u[q * 5 + r], acc[r]));
+                acc[r] = fma(-0.5, h[(dd * nall + q) * 5 + r], fma(nu, u[q * 5 + r], acc[r]));
         }
     }
 #pragma unroll
@@ -781,13 +783,13 @@ cudaError_t block_ssor_iter(BlockOp* b, const double* rhs, double* u, double ome
             if (d.n == 0) continue;
             block_jac_form_kernel<<<nblk(d.n, JB), JB, 0, st>>>(d, b->P + (size_t)i * JP, omega,
                                                                 rhs, u, b->M, b->N, b->Dinv, b->h,
-                                                                b->v);
+                                                                b->npts, b->v);
         }
         for (int i = 0; i < b->np; ++i) {
             const Dims& d = b->dims[i];
             if (d.n == 0) continue;
-            block_jac_resid_kernel<<<nblk(d.n, 256), 256, 0, st>>>(d, u, b->h, b->v, b->nu[i],
-                                                                   1.0 / omega, b->s);
+            block_jac_resid_kernel<<<nblk(d.n, 256), 256, 0, st>>>(d, u, b->h, b->npts, b->v,
+                                                                   b->nu[i], 1.0 / omega, b->s);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else if (omega != b->omega) {

@@ -13,7 +13,7 @@ struct BlockOp {
     int np = 0;
     bool jac = false;           // blocks formed from u every step (op BLOCK7_JAC)
     double* P = nullptr;        // [np][JP] their parameters (op BLOCK7_JAC)
-    double* h = nullptr;        // [npts][3][5] flux products J_d(u_q) u_q (op BLOCK7_JAC)
+    double* h = nullptr;        // [3][npts][5] flux products J_d(u_q) u_q (op BLOCK7_JAC)
     std::vector<double> nu;     // per problem: nu of its parameters (op BLOCK7_JAC)
     std::vector<Dims> dims;     // per problem (points; vectors hold 5 per point)
     i64 npts = 0;               // total points
