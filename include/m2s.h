@@ -266,6 +266,18 @@ m2s_status m2s_line_btri(int nx, int ny, int nz, int axis, const double* blk,
                          double* rhs, void* work, long long work_bytes,
                          void* stream);
 
+/* Range-check record of the library variant built with -DM2S_DEBUG_BOUNDS
+ * (the build's "bounds" variant): there, the block, ILU(0) and line-solve
+ * kernels test every global index derived from a neighbour, a line, a
+ * hyperplane or a scatter target against the extent it must stay in, skip a
+ * violating access and count it (no trap, no fault).  Fills out[0..3] (host
+ * memory): the number of violations since the last read, the source line
+ * and index of the first, and its translation unit (0 block, 1 ILU, 2 line
+ * solves); -1 where none.  Clears the record.  In the normal build out[0] =
+ * -1 (checks not compiled in) and no CUDA call is made.  Call it after the
+ * stream that ran the kernels has been synchronised. */
+m2s_status m2s_debug_bounds_read(long long* out);
+
 /* Block SSOR on the BLOCK7_5x5 operator (NPB-LU shape, paper Sec. 1 and
  * Sec. 4.3.3): n_iters times
  *   r = b - A u; lower sweep (D + omega L) v = r; upper sweep

@@ -80,7 +80,7 @@ EXPORTS = (
     "m2s_sweep_timing", "m2s_sweep_timing_read", "m2s_set_sweep_warps", "m2s_set_graphs",
     "m2s_autotune_sweeps", "m2s_line_penta", "m2s_line_penta_work_bytes", "m2s_line_btri",
     "m2s_line_btri_work_bytes", "m2s_ilu0_setup", "m2s_ilu0_apply",
-    "m2s_ilu0_factors",
+    "m2s_ilu0_factors", "m2s_debug_bounds_read",
 )
 
 
@@ -132,6 +132,7 @@ def load():
         "m2s_ilu0_setup": ([vp, vp], i),
         "m2s_ilu0_apply": ([vp, vp, vp, vp], i),
         "m2s_ilu0_factors": ([vp, vp, vp], i),
+        "m2s_debug_bounds_read": ([ctypes.POINTER(ll)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -359,6 +360,15 @@ def m2s_ilu0_setup(grid, stream=None):
 def m2s_ilu0_factors(grid, out, stream=None):
     return _check(load().m2s_ilu0_factors(grid, _ptr(out, "out"), _stream(stream)),
                   "m2s_ilu0_factors")
+
+
+def m2s_debug_bounds_read():
+    """(violations, first line, first index, translation unit) of the range
+    checks of the bounds variant of the library, cleared by the read;
+    violations = -1 when the loaded library was built without them."""
+    out = (ctypes.c_longlong * 4)()
+    _check(load().m2s_debug_bounds_read(out), "m2s_debug_bounds_read")
+    return tuple(int(v) for v in out)
 
 
 def m2s_ilu0_apply(grid, r, z, stream=None):

@@ -14,12 +14,17 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-OUT_DIR = os.path.join(HERE, "_build")
+# M2S_BUILD_VARIANT=bounds builds (and the package then loads) the variant
+# with the range checks of csrc/m2s_bounds.cuh compiled in, in its own folder
+VARIANT = os.environ.get("M2S_BUILD_VARIANT", "")
+if VARIANT not in ("", "bounds"):
+    raise RuntimeError("M2S_BUILD_VARIANT must be empty or 'bounds', not %r" % VARIANT)
+OUT_DIR = os.path.join(HERE, "_build_bounds" if VARIANT == "bounds" else "_build")
 LIB = os.path.join(OUT_DIR, "libm2s.so")
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-I", CSRC, "-I", INCLUDE]
+         "-I", CSRC, "-I", INCLUDE] + (["-DM2S_DEBUG_BOUNDS"] if VARIANT == "bounds" else [])
 
 
 def _sources():

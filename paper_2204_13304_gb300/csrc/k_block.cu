@@ -25,6 +25,7 @@
 #include <climits>
 
 #include "m2s_block.cuh"
+#include "m2s_bounds.cuh"
 #include "m2s_cta.cuh"
 #include "m2s_wave_sync.cuh"
 
@@ -108,6 +109,7 @@ __global__ void block_apply_kernel(Dims d, const double* __restrict__ D,
     const i64 sy = d.nx, sz = (i64)d.nx * d.ny;
     double acc[5] = {0, 0, 0, 0, 0};
     auto mv = [&](const double* B, i64 q) {
+        if (!M2S_IN(q - d.off, d.n)) return;
         const double* uq = u + q * 5;
         double v[5];
 #pragma unroll
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(JB) block_jac_apply_kernel(Dims d, const doubl
     const bool hi[3] = {x < d.nx - 1, y < d.ny - 1, z < d.nz - 1};
     double q[5], B[25], acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     auto add = [&](const double* Pk, i64 qi, double sj, double dj) {
+        if (!M2S_IN(qi - d.off, d.n)) return;
 #pragma unroll
         for (int c = 0; c < 5; ++c) q[c] = u[qi * 5 + c];
         jac_form(Pk, q, sj, dj, B);
@@ -329,10 +332,12 @@ __global__ void __launch_bounds__(JB, 3) block_jac_form_kernel(Dims d, const dou
         // (each slot has exactly one writer)
 #pragma unroll
         for (int k = 0; k < 25; ++k) sb[lane * 25 + k] = fma(-0.5, B[k], k % 6 == 0 ? -nu : 0.0);
-        warp_flush<25>(sb, tg, lane, valid && hi[dd] ? ((p + st[dd]) * 3 + dd) * 25 : -1, Lo);
+        const bool lo_ok = valid && lo[dd] && M2S_IN(p - st[dd] - d.off, d.n);
+        const bool hi_ok = valid && hi[dd] && M2S_IN(p + st[dd] - d.off, d.n);
+        warp_flush<25>(sb, tg, lane, hi_ok ? ((p + st[dd]) * 3 + dd) * 25 : -1, Lo);
 #pragma unroll
         for (int k = 0; k < 25; ++k) sb[lane * 25 + k] = fma(0.5, B[k], k % 6 == 0 ? -nu : 0.0);
-        warp_flush<25>(sb, tg, lane, valid && lo[dd] ? ((p - st[dd]) * 3 + dd) * 25 : -1, Up);
+        warp_flush<25>(sb, tg, lane, lo_ok ? ((p - st[dd]) * 3 + dd) * 25 : -1, Up);
         // the slots no neighbour writes: this point's own L (U) where the
         // grid ends below (above) it in d
         if (valid && !lo[dd]) {
@@ -368,13 +373,13 @@ __global__ void block_jac_resid_kernel(Dims d, const double* __restrict__ u,
     for (int r = 0; r < 5; ++r) acc[r] = w0[p * 5 + r];
 #pragma unroll
     for (int dd = 0; dd < 3; ++dd) {
-        if (lo[dd]) {
+        if (lo[dd] && M2S_IN(p - st[dd] - d.off, d.n)) {
             const i64 q = p - st[dd];
 #pragma unroll
             for (int r = 0; r < 5; ++r)
                 acc[r] = fma(0.5, h[(dd * nall + q) * 5 + r], fma(nu, u[q * 5 + r], acc[r]));
         }
-        if (hi[dd]) {
+        if (hi[dd] && M2S_IN(p + st[dd] - d.off, d.n)) {
             const i64 q = p + st[dd];
 #pragma unroll
             for (int r = 0; r < 5; ++r)
@@ -477,7 +482,7 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
     double pc[PD][15], pr[PD], pu[PD], pm0[PD], pm1[PD], pd[PD][DI ? 5 : 1];
     auto fetch = [&](int k, int s) {
         const int xx = s - g - w;
-        const bool in = rv && (unsigned)xx < (unsigned)nx;
+        const bool in = rv && (unsigned)xx < (unsigned)nx && M2S_IN(L + dir * xx, dm.n);
         const i64 p = L + dir * xx;
 #pragma unroll
         for (int d = 0; d < 3; ++d)
@@ -486,7 +491,8 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
                 pc[k][5 * d + j] = (in && !halo) ? __ldg(C + p * 75 + d * 25 + c * 5 + j) : 0.0;
         double m0 = 0.0, m1 = 0.0;
         if (in && halo) tw_to_regs(mb_load<double>(mbox, p * 5 + c), &m0, &m1);
-        if (in && !halo && zmb) tw_to_regs(mb_load<double>(mbox, (p - szd) * 5 + c), &m0, &m1);
+        if (in && !halo && zmb && M2S_IN(p - szd, dm.n))
+            tw_to_regs(mb_load<double>(mbox, (p - szd) * 5 + c), &m0, &m1);
         pr[k] = (in && !halo) ? __ldg(R + p * 5 + c) : 0.0;
         pu[k] = (in && !halo && U) ? U[p * 5 + c] : 0.0;
         if constexpr (DI) {
@@ -523,7 +529,7 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
 #pragma unroll
         for (int j = 0; j < (DI ? 5 : 1); ++j) di[j] = pd[k][j];
         fetch(k, s + PD);
-        const bool in = rv && (unsigned)xx < (unsigned)nx;
+        const bool in = rv && (unsigned)xx < (unsigned)nx && M2S_IN(L + dir * xx, dm.n);
         const bool comp = in && !halo;
         double X = 0.0, zc = 0.0;
         bool okx = true, okz = true, okr = true;
@@ -538,7 +544,7 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
             for (int it = 1;; ++it) {
                 if (!okr) okr = Tagged<double>::unpack(*(volatile const TW*)re, rtag, &zc);
                 if (!okx) okx = Tagged<double>::unpack(mb_load<double>(mbox, p * 5 + c), tag, &X);
-                if (!okz)
+                if (!okz && M2S_IN(p - szd, dm.n))
                     okz = Tagged<double>::unpack(mb_load<double>(mbox, (p - szd) * 5 + c), tag, &zc);
                 if (__all_sync(FULL, okx && okz && okr)) break;
                 if ((it & 31) == 0) {
@@ -659,6 +665,8 @@ __global__ void __launch_bounds__(BW * 32, 1) block_cta_kernel(BlockCtaArgs a) {
 unsigned nblk(i64 n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
+
+M2S_BOUNDS_READER(bounds_read_block)
 
 cudaError_t block_create(BlockOp* b, const m2s_grid_desc* descs, int n_problems,
                          const std::vector<std::vector<Dims>>& dims, cudaStream_t st,

@@ -15,6 +15,7 @@
 // application replays its 2 (T + 1) launches from a CUDA graph.
 #include <algorithm>
 
+#include "m2s_bounds.cuh"
 #include "m2s_internal.cuh"
 
 namespace m2s {
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(IB) ilu_factor_kernel(Dims d, int t, int z0,
     if (!hyperplane_point(d, t, z0, &x, &y, &z)) return;
     const Inside in = inside_of(d, x, y, z);
     const i64 p = ((i64)z * d.ny + y) * d.nx + x;  // problem-local
+    if (!M2S_IN(p, d.n)) return;
     double* Fb = F + 27 * d.off;
     double* Ib = Finv + d.off;
     double f[27];
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(IB) ilu_factor_kernel(Dims d, int t, int z0,
     for (int ok = 0; ok < 13; ++ok) {
         if (!in(odx(ok), ody(ok), odz(ok))) continue;
         const i64 k = nbr(d, p, odx(ok), ody(ok), odz(ok));
+        if (!M2S_IN(k, d.n)) continue;
         const double* Fk = Fb + 27 * k;
         const double l = f[ok] * Ib[k];  // the pivot's rounded reciprocal
         f[ok] = l;
@@ -114,6 +117,7 @@ __global__ void __launch_bounds__(IB) ilu_lower_kernel(Dims d, int t, int z0,
     if (!hyperplane_point(d, t, z0, &x, &y, &zz)) return;
     const Inside in = inside_of(d, x, y, zz);
     const i64 p = ((i64)zz * d.ny + y) * d.nx + x;
+    if (!M2S_IN(p, d.n)) return;
     const double* Fp = F + 27 * (d.off + p);
     const double* zb = z + d.off;
     if (x + 1 < d.nx) {
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(IB) ilu_lower_kernel(Dims d, int t, int z0,
     double s0 = r[d.off + p], s1 = 0.0;
 #pragma unroll
     for (int o = 0; o < 13; ++o)
-        if (in(odx(o), ody(o), odz(o))) {
+        if (in(odx(o), ody(o), odz(o)) && M2S_IN(nbr(d, p, odx(o), ody(o), odz(o)), d.n)) {
             const double v = zb[nbr(d, p, odx(o), ody(o), odz(o))];
             if (o & 1) s1 = fma(-__ldg(Fp + o), v, s1);
             else s0 = fma(-__ldg(Fp + o), v, s0);
@@ -141,6 +145,7 @@ __global__ void __launch_bounds__(IB) ilu_upper_kernel(Dims d, int t, int z0,
     if (!hyperplane_point(d, t, z0, &x, &y, &zz)) return;
     const Inside in = inside_of(d, x, y, zz);
     const i64 p = ((i64)zz * d.ny + y) * d.nx + x;
+    if (!M2S_IN(p, d.n)) return;
     const double* Fp = F + 27 * (d.off + p);
     const double* zb = z + d.off;
     if (x > 0) {
@@ -151,7 +156,7 @@ __global__ void __launch_bounds__(IB) ilu_upper_kernel(Dims d, int t, int z0,
     double s0 = zb[p], s1 = 0.0;
 #pragma unroll
     for (int o = 14; o < 27; ++o)
-        if (in(odx(o), ody(o), odz(o))) {
+        if (in(odx(o), ody(o), odz(o)) && M2S_IN(nbr(d, p, odx(o), ody(o), odz(o)), d.n)) {
             const double v = zb[nbr(d, p, odx(o), ody(o), odz(o))];
             if (o & 1) s1 = fma(-__ldg(Fp + o), v, s1);
             else s0 = fma(-__ldg(Fp + o), v, s0);
@@ -216,5 +221,7 @@ cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* Finv,
     }
     return cudaSuccess;
 }
+
+M2S_BOUNDS_READER(bounds_read_ilu)
 
 }  // namespace m2s

@@ -25,6 +25,7 @@
 // ~65 % busy on y and z lines), not by HBM.  The coefficients and
 // right-hand sides of the next LD points are loaded ahead of the one being
 // eliminated, which hides the load latency of the few warps per SM.
+#include "m2s_bounds.cuh"
 #include "m2s_internal.cuh"
 
 namespace m2s {
@@ -74,6 +75,8 @@ __global__ void __launch_bounds__(LB) line_penta_kernel(LineArgs a) {
     i64 base, stride;
     int m;
     if (!line_of(a, blockIdx.x * (i64)LB + threadIdx.x, &base, &stride, &m)) return;
+    // the line's points are affine in i: its two ends bound every access
+    if (!(M2S_IN(base, a.n) && M2S_IN(base + (i64)(m - 1) * stride, a.n))) return;
     const double* __restrict__ coef = a.coef;
     double* __restrict__ rhs = a.rhs;
     double* __restrict__ w_inv = a.work;
@@ -195,6 +198,7 @@ __global__ void __launch_bounds__(LB) line_btri_kernel(LineArgs a) {
     i64 base, stride;
     int m;
     if (!line_of(a, blockIdx.x * (i64)LB + threadIdx.x, &base, &stride, &m)) return;
+    if (!(M2S_IN(base, a.n) && M2S_IN(base + (i64)(m - 1) * stride, a.n))) return;
     const double* __restrict__ blk = a.coef;
     double* __restrict__ rhs = a.rhs;
     double* __restrict__ ch = a.work;
@@ -347,5 +351,7 @@ cudaError_t launch_line_penta(int nx, int ny, int nz, int axis, const double* co
     }
     return cudaGetLastError();
 }
+
+M2S_BOUNDS_READER(bounds_read_line)
 
 }  // namespace m2s

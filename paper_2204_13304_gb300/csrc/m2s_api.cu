@@ -1182,6 +1182,24 @@ m2s_status m2s_line_btri(int nx, int ny, int nz, int axis, const double* blk, do
     return M2S_OK;
 }
 
+m2s_status m2s_debug_bounds_read(long long* out) {
+    if (!out) return M2S_ERR_INVALID_ARG;
+    long long r[3][3];
+    M2S_TRY(bounds_read_block(r[0]));
+    M2S_TRY(bounds_read_ilu(r[1]));
+    M2S_TRY(bounds_read_line(r[2]));
+    out[0] = r[0][0] < 0 ? -1 : r[0][0] + r[1][0] + r[2][0];
+    out[1] = out[2] = out[3] = -1;
+    for (int t = 0; t < 3; ++t)
+        if (r[t][0] > 0) {
+            out[1] = r[t][1];
+            out[2] = r[t][2];
+            out[3] = t;
+            break;
+        }
+    return M2S_OK;
+}
+
 m2s_status m2s_ssor_sweep(m2s_grid* g, const double* b, double* u, double omega, int n_iters,
                           void* stream) {
     if (!g || !b || !u || b == u || !is_block(g->op)) return M2S_ERR_INVALID_ARG;

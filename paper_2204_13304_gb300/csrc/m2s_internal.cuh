@@ -200,6 +200,13 @@ cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* Finv,
                              double* z, cudaStream_t st);
 // Block-tridiagonal (5x5) line solves (k_line.cu).
 i64 line_btri_work_doubles(int nx, int ny, int nz);
+
+// range-check records of the instrumented translation units (see
+// m2s_bounds.cuh): out[0] violations (-1: checks not compiled in), out[1]
+// source line and out[2] index of the first; cleared by the read
+cudaError_t bounds_read_block(long long* out);
+cudaError_t bounds_read_ilu(long long* out);
+cudaError_t bounds_read_line(long long* out);
 cudaError_t launch_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* rhs,
                              double* work, cudaStream_t st);
 

@@ -85,6 +85,29 @@ def test_grid_desc_layout_matches_header():
     assert fields == [f[0] for f in m.GridDesc._fields_]
 
 
+def test_bounds_record_of_the_normal_build_without_gpu(lib):
+    """The normal build has no range checks compiled in: the record says so
+    (-1) without a CUDA call."""
+    import paper_2204_13304_gb300 as m
+    assert m.m2s_debug_bounds_read()[0] == -1
+    assert lib.m2s_debug_bounds_read(None) == m.Status.INVALID_ARG
+
+
+def test_bounds_variant_builds_without_gpu():
+    """The range-checked variant compiles for sm_103a into its own folder and
+    exports the same symbols (it runs only in the GPU tests)."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r); "
+            "from paper_2204_13304_gb300 import build as b; p = b.build(); "
+            "import ctypes; L = ctypes.CDLL(p); L.m2s_debug_bounds_read; print(p)" % ROOT)
+    env = dict(os.environ, M2S_BUILD_VARIANT="bounds")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=1200)
+    assert r.returncode == 0, r.stderr[-3000:]
+    assert r.stdout.strip().endswith(os.path.join("_build_bounds", "libm2s.so"))
+
+
 def test_library_is_sm103a_only():
     """The build targets exactly compute_103a/sm_103a."""
     from paper_2204_13304_gb300 import build as b
