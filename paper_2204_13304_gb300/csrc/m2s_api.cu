@@ -12,6 +12,17 @@
 #include "m2s_block.cuh"
 #include "m2s_internal.cuh"
 #include "m2s_pcg.cuh"
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// An NVTX range around a public call, for timelines taken under a profiler
+// (a no-op when none is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
+#define M2S_RANGE(name) NvtxRange m2s_nvtx_range_(name)
 
 using namespace m2s;
 
@@ -607,6 +618,7 @@ static bool is_block(m2s_op op) { return op == M2S_OP_BLOCK7_5x5 || op == M2S_OP
 
 m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* stream,
                            m2s_grid** out) {
+    M2S_RANGE("m2s_grid_create");
     if (!out) return M2S_ERR_INVALID_ARG;
     *out = nullptr;
     if (!descs || n_problems < 1) return M2S_ERR_INVALID_ARG;
@@ -862,6 +874,7 @@ m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps) {
 }
 
 m2s_status m2s_autotune_sweeps(m2s_grid* g, int reps, void* stream, int* chosen) {
+    M2S_RANGE("m2s_autotune_sweeps");
     if (!g || g->op != M2S_OP_HPCG27 || reps < 1) return M2S_ERR_INVALID_ARG;
     M2S_TRY(ensure_f32(g));
     cudaStream_t st = S(stream);
@@ -964,6 +977,7 @@ m2s_status m2s_grid_sync(m2s_grid* grid, void* stream) {
 }
 
 m2s_status m2s_spmv(m2s_grid* g, int level, m2s_dtype dtype, const void* x, void* y, void* stream) {
+    M2S_RANGE("m2s_spmv");
     if (!valid_level(g, level) || !x || !y || x == y) return M2S_ERR_INVALID_ARG;
     if (is_block(g->op)) {
         if (dtype != M2S_F64) return M2S_ERR_INVALID_ARG;
@@ -977,6 +991,7 @@ m2s_status m2s_spmv(m2s_grid* g, int level, m2s_dtype dtype, const void* x, void
 
 m2s_status m2s_symgs(m2s_grid* g, int level, m2s_dtype dtype, const void* b, void* x,
                      int n_sym_sweeps, void* stream) {
+    M2S_RANGE("m2s_symgs");
     if (!valid_level(g, level) || !b || !x || b == x || n_sym_sweeps < 0) return M2S_ERR_INVALID_ARG;
     if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (m2s_status cs = check_dtype(g, dtype)) return cs;
@@ -990,6 +1005,7 @@ m2s_status m2s_symgs(m2s_grid* g, int level, m2s_dtype dtype, const void* b, voi
 
 m2s_status m2s_gs_sweep(m2s_grid* g, int level, m2s_dtype dtype, const void* b, void* x,
                         m2s_direction direction, void* stream) {
+    M2S_RANGE("m2s_gs_sweep");
     if (!valid_level(g, level) || !b || !x || b == x) return M2S_ERR_INVALID_ARG;
     if (direction != M2S_FORWARD && direction != M2S_BACKWARD) return M2S_ERR_INVALID_ARG;
     if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
@@ -1004,6 +1020,7 @@ m2s_status m2s_gs_sweep(m2s_grid* g, int level, m2s_dtype dtype, const void* b, 
 
 m2s_status m2s_mg_restrict(m2s_grid* g, int level, m2s_dtype dtype, const void* r, const void* z,
                            void* rc, void* stream) {
+    M2S_RANGE("m2s_mg_restrict");
     if (!g || level < 0 || level + 1 >= g->levels || !r || !z || !rc) return M2S_ERR_INVALID_ARG;
     if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (m2s_status cs = check_dtype(g, dtype)) return cs;
@@ -1018,6 +1035,7 @@ m2s_status m2s_mg_restrict(m2s_grid* g, int level, m2s_dtype dtype, const void* 
 
 m2s_status m2s_mg_prolong(m2s_grid* g, int level, m2s_dtype dtype, const void* zc, void* z,
                           void* stream) {
+    M2S_RANGE("m2s_mg_prolong");
     if (!g || level < 0 || level + 1 >= g->levels || !zc || !z) return M2S_ERR_INVALID_ARG;
     if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (m2s_status cs = check_dtype(g, dtype)) return cs;
@@ -1030,6 +1048,7 @@ m2s_status m2s_mg_prolong(m2s_grid* g, int level, m2s_dtype dtype, const void* z
 }
 
 m2s_status m2s_mg_vcycle(m2s_grid* g, m2s_dtype dtype, const void* r, void* z, void* stream) {
+    M2S_RANGE("m2s_mg_vcycle");
     if (!g || !r || !z || r == z) return M2S_ERR_INVALID_ARG;
     if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (m2s_status cs = check_dtype(g, dtype)) return cs;
@@ -1042,6 +1061,7 @@ m2s_status m2s_mg_vcycle(m2s_grid* g, m2s_dtype dtype, const void* r, void* z, v
 
 m2s_status m2s_pcg_solve(m2s_grid* g, const double* b, double* x, const m2s_pcg_opts* opts,
                          m2s_pcg_result* out, void* stream) {
+    M2S_RANGE("m2s_pcg_solve");
     if (!g || !b || !x || !opts || b == x) return M2S_ERR_INVALID_ARG;
     if (is_block(g->op)) return M2S_ERR_INVALID_ARG;
     m2s_pcg_opts o = *opts;
@@ -1053,6 +1073,7 @@ m2s_status m2s_pcg_solve(m2s_grid* g, const double* b, double* x, const m2s_pcg_
 
 m2s_status m2s_kappa_grad(m2s_grid* g, const double* u, const double* lambda, double* dLdkappa,
                           void* stream) {
+    M2S_RANGE("m2s_kappa_grad");
     if (!g || !u || !lambda || !dLdkappa || g->op != M2S_OP_DIFF7_KAPPA) return M2S_ERR_INVALID_ARG;
     M2S_TRY(launch_kappa_grad_b(g->batch[0], u, lambda, dLdkappa, S(stream)));
     return M2S_OK;
@@ -1061,6 +1082,7 @@ m2s_status m2s_kappa_grad(m2s_grid* g, const double* u, const double* lambda, do
 m2s_status m2s_adjoint_solve(m2s_grid* g, const double* u, const double* dLdu, double* lambda,
                              double* dLdkappa, const m2s_pcg_opts* opts, m2s_pcg_result* out,
                              void* stream) {
+    M2S_RANGE("m2s_adjoint_solve");
     if (!g || !u || !dLdu || !lambda || !dLdkappa || !opts) return M2S_ERR_INVALID_ARG;
     if (g->op != M2S_OP_DIFF7_KAPPA) return M2S_ERR_INVALID_ARG;
     // A is symmetric (k_f is the same for both cells of a face), so A^T = A
@@ -1081,6 +1103,7 @@ long long m2s_line_penta_work_bytes(int nx, int ny, int nz) {
 
 m2s_status m2s_line_penta(int nx, int ny, int nz, int axis, const double* coef, double* rhs,
                           int k, void* work, long long work_bytes, void* stream) {
+    M2S_RANGE("m2s_line_penta");
     if (nx < 1 || ny < 1 || nz < 1 || axis < 0 || axis > 2 || k < 1 || k > 8)
         return M2S_ERR_INVALID_ARG;
     if ((i64)nx * ny * nz > (1LL << 34)) return M2S_ERR_INVALID_ARG;
@@ -1101,6 +1124,7 @@ m2s_status m2s_line_penta(int nx, int ny, int nz, int axis, const double* coef, 
 }
 
 m2s_status m2s_ilu0_setup(m2s_grid* g, void* stream) {
+    M2S_RANGE("m2s_ilu0_setup");
     if (!g || g->op != M2S_OP_HPCG27) return M2S_ERR_INVALID_ARG;
     cudaStream_t st = S(stream);
     if (!g->ilu_F) M2S_TRY(galloc(g, &g->ilu_F, 27 * g->ltot[0]));
@@ -1119,6 +1143,7 @@ m2s_status m2s_ilu0_factors(m2s_grid* g, double* out, void* stream) {
 }
 
 m2s_status m2s_ilu0_apply(m2s_grid* g, const double* r, double* z, void* stream) {
+    M2S_RANGE("m2s_ilu0_apply");
     if (!g || g->op != M2S_OP_HPCG27 || !g->ilu_F || !r || !z) return M2S_ERR_INVALID_ARG;
     if (!aligned(r, 8) || !aligned(z, 8)) return M2S_ERR_INVALID_ARG;
     const i64 bytes = g->ltot[0] * 8;
@@ -1165,6 +1190,7 @@ long long m2s_line_btri_work_bytes(int nx, int ny, int nz) {
 
 m2s_status m2s_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* rhs,
                          void* work, long long work_bytes, void* stream) {
+    M2S_RANGE("m2s_line_btri");
     if (nx < 1 || ny < 1 || nz < 1 || axis < 0 || axis > 2) return M2S_ERR_INVALID_ARG;
     if ((i64)nx * ny * nz > (1LL << 32)) return M2S_ERR_INVALID_ARG;
     if (!blk || !rhs || !work || !aligned(blk, 8) || !aligned(rhs, 8) || !aligned(work, 8))
@@ -1202,6 +1228,7 @@ m2s_status m2s_debug_bounds_read(long long* out) {
 
 m2s_status m2s_ssor_sweep(m2s_grid* g, const double* b, double* u, double omega, int n_iters,
                           void* stream) {
+    M2S_RANGE("m2s_ssor_sweep");
     if (!g || !b || !u || b == u || !is_block(g->op)) return M2S_ERR_INVALID_ARG;
     if (!(omega > 0.0 && omega < 2.0) || n_iters < 0) return M2S_ERR_INVALID_ARG;
     for (int it = 0; it < n_iters; ++it)

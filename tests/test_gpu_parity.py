@@ -289,6 +289,28 @@ def test_pcg_timeout_on_a_coarse_level_is_reported_and_the_next_solve_is_correct
     assert st == m.Status.OK and err64(host(x), ox) <= TOL64
 
 
+@pytest.mark.parametrize("precond", ["f64", "f32"])
+def test_nan_in_b_reports_breakdown_and_the_next_solve_is_correct(m, precond):
+    """A NaN injected into b on the host: the solve stops with BREAKDOWN (the
+    device-side scalars turn non-finite; nothing traps, and the tagged
+    mailboxes carry a NaN like any other value), and the next solve on the
+    same grid matches the oracle."""
+    import torch
+    shape = (16, 16, 16)
+    g = m.Grid([dict(nx=16, ny=16, nz=16, op=m.Op.HPCG27, mg_levels=3,
+                     precond_dtype=m.DType.F32 if precond == "f32" else m.DType.F64)])
+    b = oracle.apply(H27, np.ones(shape))
+    bad = b.copy()
+    bad[3, 4, 5] = np.nan
+    x = torch.empty(shape, dtype=torch.float64, device="cuda")
+    st, _ = m.m2s_pcg_solve(g.handle, dev(bad), x, max_iters=20, rtol=1e-10, fixed_iters=False,
+                            raise_on_error=False)
+    assert st == m.Status.BREAKDOWN
+    st, res = m.m2s_pcg_solve(g.handle, dev(b), x, max_iters=200, rtol=1e-10, fixed_iters=False)
+    assert st == m.Status.OK and res.rel_resid <= 1e-10
+    assert np.max(np.abs(host(x) - 1.0)) <= 1e-8
+
+
 @pytest.mark.parametrize("shape", [(5, 3, 4), (17, 33, 32), (33, 17, 35), (64, 64, 64),
                                    (40, 11, 3), (40, 7, 3), (70, 5, 2)])
 @pytest.mark.parametrize("f32", [False, True])
