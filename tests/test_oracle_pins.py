@@ -681,6 +681,26 @@ def test_ssor_jac_step_uses_blocks_of_its_start_state():
     assert np.array_equal(u2, oracle.ssor(D, L, U, 1.2, b, u1, 1))
 
 
+def test_block_jac_rows_stay_diagonally_dominant():
+    """The input recipe's claim: for |u| <= 1.5 every Jacobian entry is below
+    0.25, so every scalar row of A(u) is strictly diagonally dominant (the 5x5
+    eliminations need no pivoting).  Checked on the recipe's parameters at
+    u = +-1.5 with random signs, where the bound is tightest."""
+    shape = (4, 5, 3)
+    P, _, _ = gen.block_jac_inputs(shape, seed=67)
+    rng = np.random.default_rng(3)
+    u = 1.5 * rng.choice([-1.0, 1.0], size=shape + (5,))
+    D, L, U = oracle.block_jac(P, u)
+    for k in range(4):
+        C, E, g = jac_parts(P, k)
+        for q in u.reshape(-1, 5)[:20]:
+            J = C + (g @ q) * E + np.outer(E @ q, g)
+            assert np.max(np.abs(J)) < 0.25
+    diag = np.abs(D[..., range(5), range(5)])
+    off = np.abs(D).sum(axis=-1) - diag + np.abs(L).sum(axis=(-3, -1)) + np.abs(U).sum(axis=(-3, -1))
+    assert np.all(diag > off) and diag.min() >= 9.75 and off.max() < 8.0
+
+
 def test_ssor_jac_converges_to_the_nonlinear_solution():
     """The fixed point of the steps solves A(u) u = b, checked with the
     closed form of A(u) u (not with the oracle's blocks)."""
