@@ -736,6 +736,23 @@ def test_inputs_deterministic_and_distributed():
     assert len(s) == 64 and set(s) <= set(gen.BATCH_SIDES) and len(set(s)) >= 4
 
 
+@pytest.mark.parametrize("make", [
+    lambda seed: gen.block_ssor_inputs(0, shape=(3, 4, 5), seed=seed),
+    lambda seed: gen.block_jac_inputs((3, 4, 5), seed=seed),
+    lambda seed: gen.line_penta_inputs((3, 4, 5), k=5, seed=seed),
+    lambda seed: gen.line_btri_inputs((3, 4, 5), seed=seed),
+])
+def test_every_generator_is_deterministic_per_seed(make):
+    """Same seed: bitwise the same arrays; another seed: different ones (the
+    counter-based streams depend on the seed, the array id and the index
+    only)."""
+    a, b, c = make(11), make(11), make(12)
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x, y)
+        if np.size(x) > 2:  # the parameter vector's fixed sigma, nu aside
+            assert not np.array_equal(x, z)
+
+
 @pytest.mark.parametrize("n", [64, 128, 256])
 def test_stored_pcg_histories_start_at_closed_form_norm_of_b(n):
     """The stored oracle residual histories (tests/golden) start at
