@@ -2,7 +2,9 @@
 
 Thin marshalling only: every function below forwards device pointers, sizes
 and the current CUDA stream of PyTorch to the function of the same name in
-``_build/libm2s.so``; all computation happens in that library's CUDA kernels.
+``_build/libm2s.so`` (``_build_bounds/libm2s.so``, the range-checked variant,
+when M2S_BUILD_VARIANT=bounds is set at import); all computation happens in
+that library's CUDA kernels.
 PyTorch supplies device memory and streams.  There is no CPU fallback: if the
 library has not been built (``paper_2204_13304_gb300.build.build()``) the
 first call raises.
