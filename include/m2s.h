@@ -83,7 +83,9 @@ typedef enum { M2S_FORWARD = 0, M2S_BACKWARD = 1 } m2s_direction;
  *   jac            op = BLOCK7_JAC: HOST FP64 array of 222 parameters,
  *                  copied at creation: sigma, nu, then for k = 0..3 (point
  *                  term, x, y, z) C_k (5x5 row-major), E_k (5x5), g_k (5).
- *                  The blocks are NPB-LU-style Jacobians of the synthetic
+ *                  The blocks are NPB-LU-style Jacobians (the SSOR of
+ *                  paper Sec. 1 on the 5-vectors and 5x5 blocks of Sec.
+ *                  4.2.3; NPB's own flux is not in the paper) of the synthetic
  *                  flux F_k(q) = C_k q + (g_k . q) E_k q evaluated at the
  *                  state, J_k(q) = C_k + (g_k . q) E_k + (E_k q) g_k^T:
  *                    D_p     = sigma I + J_0(u_p)
