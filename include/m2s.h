@@ -126,7 +126,13 @@ typedef struct {
 } m2s_pcg_result;
 
 /* Create a grid of n_problems problems (n_problems >= 1; every desc must
- * use the same op).  Allocates the multigrid hierarchy, coefficient copies,
+ * use the same op).  The grid is the problem statement of paper Sec. 2.1
+ * (a linear system A u = b on a regular Cartesian grid, the operator never
+ * assembled: Sec. 2.1.2) with the operator given as a row function over a
+ * multi-dimensional domain (Sec. 4.2, Sec. 4.2.1; 5-vector unknowns and
+ * 5x5 blocks as inner values, Sec. 4.2.3), and the multigrid hierarchy of
+ * the HPCG solver of Sec. 7.1 (coarse domains derived from the fine one,
+ * Sec. 4.2.2).  Allocates the multigrid hierarchy, coefficient copies,
  * the FP64 sweep workspaces and schedules, and the FP32 copies of the
  * variable-kappa operator when requested; copies coefficients with
  * stream-ordered copies on `stream` and synchronises it before returning.
@@ -182,7 +188,11 @@ m2s_status m2s_mg_restrict(m2s_grid* grid, int level, m2s_dtype dtype,
 m2s_status m2s_mg_prolong(m2s_grid* grid, int level, m2s_dtype dtype,
                           const void* zc, void* z, void* stream);
 
-/* One multigrid V-cycle z = M^-1 r with the grid's mg_levels levels: z = 0;
+/* One multigrid V-cycle z = M^-1 r (the multigrid preconditioner of the
+ * HPCG solver, paper Sec. 7.1; its transfers are the "HPCG Prolong" row
+ * function of Sec. 4.2 Table 1 and its transpose, fused into the
+ * neighbouring sweeps as the strided loop fusion of Sec. 6.2.2 allows)
+ * with the grid's mg_levels levels: z = 0;
  * coarsest level one symmetric GS; otherwise symmetric GS (pre-smoothing),
  * restrict the residual, recurse, prolongate, symmetric GS (post). dtype
  * F64 runs the FP64 hierarchy, F32 the FP32 one.  r and z must not
@@ -190,7 +200,10 @@ m2s_status m2s_mg_prolong(m2s_grid* grid, int level, m2s_dtype dtype,
 m2s_status m2s_mg_vcycle(m2s_grid* grid, m2s_dtype dtype, const void* r,
                          void* z, void* stream);
 
-/* Preconditioned CG from x0 = 0 (r0 = b) with the V-cycle preconditioner
+/* Preconditioned CG (the MG-preconditioned conjugate gradient that HPCG
+ * runs, paper Sec. 7.1, 50 iterations per HPCG run; its vector updates are
+ * the pointwise operations inlined into neighbouring loops in Sec. 6.2.1)
+ * from x0 = 0 (r0 = b) with the V-cycle preconditioner
  * (FP64, or FP32 inside flexible CG when precond_dtype = F32).  b, x are
  * FP64.  Synchronises `stream`; fills *out (may be NULL).  Returns
  * M2S_ERR_NOT_CONVERGED if rtol was not met within max_iters (unless
@@ -293,7 +306,13 @@ m2s_status m2s_debug_bounds_read(long long* out);
 m2s_status m2s_ssor_sweep(m2s_grid* grid, const double* b, double* u,
                           double omega, int n_iters, void* stream);
 
-/* Adjoint of the kappa solve (op DIFF7_KAPPA).  Given the forward solution u
+/* Adjoint of the kappa solve (op DIFF7_KAPPA).  The paper states no
+ * adjoint: this is the implicit (solve-level) adjoint of the solve of A u = b
+ * (Sec. 2.1) for the variable-coefficient diffusion operator whose face
+ * coefficient averages its two cells (the averaging matrix of Sec. 4.1),
+ * run with the transposed Gauss-Seidel sweeps of Sec. 4.3.3 (a transposed
+ * forward sweep is a backward sweep with transposed couplings) inside the
+ * same MG-PCG (Sec. 7.1).  Given the forward solution u
  * of A(kappa) u = b and dLdu, solves A^T lambda = dLdu with PCG (the
  * transposed V-cycle: transposed sweeps in mirrored order, which for this
  * symmetric operator is the same V-cycle) and writes
@@ -323,11 +342,11 @@ m2s_status m2s_set_spin_limit(m2s_grid* grid, long long limit_ns);
  * exists for callers that cannot allocate -- applications that reserve all
  * device memory for their own pool, or latency-critical loops that cannot
  * afford cudaMalloc's implicit synchronisation.)
- *   b, x     device [nz][ny][nx] vectors of type dtype (x in/out, b and x
- *            must not overlap).
- *   limits   nx*ny*nz <= 262144 (64^3) points and at most 8192 wavefront
- *            units; larger requests return M2S_ERR_INVALID_ARG before any
- *            launch.
+ *   b, x     device [nz][ny][nx] vectors of type dtype (x in/out); b and x
+ *            must not share any byte (M2S_ERR_INVALID_ARG otherwise).
+ *   limits   nx*ny*nz <= 262144 (64^3) points, at most 8192 wavefront
+ *            units (so at most 32768 planes of z); larger requests return
+ *            M2S_ERR_INVALID_ARG before any launch.
  *   scratch  one fixed-size array (about 4.4 MB) in the library's static
  *            device memory, shared by every call on every stream; the
  *            counters that must start at zero are cleared by each call.
@@ -335,8 +354,11 @@ m2s_status m2s_set_spin_limit(m2s_grid* grid, long long limit_ns);
  *   set-up   the first call on a device looks up the array's device address
  *            (cudaGetSymbolAddress, that device current); make that first
  *            call before any stream capture.
- *   sync     synchronises `stream` before returning and reports an expired
- *            spin-wait as M2S_ERR_TIMEOUT. */
+ *   sync     every call copies its unit tables from host memory,
+ *            synchronises `stream` before returning and reports an expired
+ *            spin-wait as M2S_ERR_TIMEOUT.
+ *   waits    every spin-wait is bounded by a fixed 4 s; m2s_set_spin_limit
+ *            (a per-grid setting) does not apply to this entry point. */
 m2s_status m2s_symgs_noalloc(int nx, int ny, int nz, m2s_dtype dtype,
                              const void* b, void* x, int n_sym_sweeps,
                              void* stream);

@@ -180,6 +180,25 @@ def _ptr(t, what):
     return t.data_ptr()
 
 
+def _same(what, ref, *others, exact_shape=False):
+    """Raise ValueError unless every tensor of `others` has the element count
+    (the shape, if exact_shape), dtype and device of `ref`: checked before any
+    pointer reaches the library, which cannot see the extent of a device
+    allocation."""
+    import torch
+    if not isinstance(ref, torch.Tensor):
+        raise TypeError("%s: vectors must be torch.Tensors" % what)
+    for name, t in others:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("%s: %s must be a torch.Tensor" % (what, name))
+        size_ok = t.shape == ref.shape if exact_shape else t.numel() == ref.numel()
+        if not size_ok or t.dtype != ref.dtype or t.device != ref.device:
+            raise ValueError("%s: %s must match %s in shape, dtype and device "
+                             "(%s %s %s vs %s %s %s)"
+                             % (what, name, "the first vector", tuple(t.shape), t.dtype,
+                                t.device, tuple(ref.shape), ref.dtype, ref.device))
+
+
 def _dtype(t):
     import torch
     if t.dtype == torch.float64:
@@ -275,7 +294,12 @@ def m2s_sweep_timing_read(grid, level):
 def m2s_symgs_noalloc(b, x, n_sym_sweeps=1, stream=None):
     """Symmetric Gauss-Seidel (27-point operator) that allocates no device
     memory, for callers that cannot allocate (its scratch is a fixed static
-    array of the library: at most 64^3 points; calls must not overlap)."""
+    array of the library: at most 64^3 points; calls must not overlap).
+    b and x are (nz, ny, nx) CUDA tensors of one dtype on one device."""
+    import torch
+    if not isinstance(x, torch.Tensor) or x.dim() != 3:
+        raise ValueError("m2s_symgs_noalloc: x must be a (nz, ny, nx) tensor")
+    _same("m2s_symgs_noalloc", x, ("b", b), exact_shape=True)
     nz, ny, nx = x.shape
     return _check(load().m2s_symgs_noalloc(nx, ny, nz, _dtype(x), _ptr(b, "b"), _ptr(x, "x"),
                                            int(n_sym_sweeps), _stream(stream)),
@@ -283,31 +307,40 @@ def m2s_symgs_noalloc(b, x, n_sym_sweeps=1, stream=None):
 
 
 def m2s_spmv(grid, level, x, y, stream=None):
+    _same("m2s_spmv", x, ("y", y))
     return _check(load().m2s_spmv(grid, level, _dtype(x), _ptr(x, "x"), _ptr(y, "y"),
                                   _stream(stream)), "m2s_spmv")
 
 
 def m2s_symgs(grid, level, b, x, n_sym_sweeps=1, stream=None):
+    _same("m2s_symgs", x, ("b", b))
     return _check(load().m2s_symgs(grid, level, _dtype(x), _ptr(b, "b"), _ptr(x, "x"),
                                    int(n_sym_sweeps), _stream(stream)), "m2s_symgs")
 
 
 def m2s_gs_sweep(grid, level, b, x, direction=FORWARD, stream=None):
+    _same("m2s_gs_sweep", x, ("b", b))
     return _check(load().m2s_gs_sweep(grid, level, _dtype(x), _ptr(b, "b"), _ptr(x, "x"),
                                       int(direction), _stream(stream)), "m2s_gs_sweep")
 
 
 def m2s_mg_restrict(grid, level, r, z, rc, stream=None):
+    _same("m2s_mg_restrict", r, ("z", z))
+    if rc.dtype != r.dtype or rc.device != r.device:
+        raise ValueError("m2s_mg_restrict: rc must match r in dtype and device")
     return _check(load().m2s_mg_restrict(grid, level, _dtype(r), _ptr(r, "r"), _ptr(z, "z"),
                                          _ptr(rc, "rc"), _stream(stream)), "m2s_mg_restrict")
 
 
 def m2s_mg_prolong(grid, level, zc, z, stream=None):
+    if zc.dtype != z.dtype or zc.device != z.device:
+        raise ValueError("m2s_mg_prolong: zc must match z in dtype and device")
     return _check(load().m2s_mg_prolong(grid, level, _dtype(z), _ptr(zc, "zc"), _ptr(z, "z"),
                                         _stream(stream)), "m2s_mg_prolong")
 
 
 def m2s_mg_vcycle(grid, r, z, stream=None):
+    _same("m2s_mg_vcycle", r, ("z", z))
     return _check(load().m2s_mg_vcycle(grid, _dtype(r), _ptr(r, "r"), _ptr(z, "z"),
                                        _stream(stream)), "m2s_mg_vcycle")
 
@@ -323,6 +356,7 @@ def m2s_pcg_solve(grid, b, x, max_iters=50, rtol=0.0, fixed_iters=True, check_ev
                   stream=None, raise_on_error=True):
     """Returns (status, PcgResult).  Raises on errors other than NOT_CONVERGED
     unless raise_on_error is False."""
+    _same("m2s_pcg_solve", b, ("x", x))
     o = _opts(max_iters, rtol, fixed_iters, check_every)
     res = PcgResult()
     st = load().m2s_pcg_solve(grid, _ptr(b, "b"), _ptr(x, "x"), ctypes.byref(o),
@@ -374,6 +408,7 @@ def m2s_debug_bounds_read():
 
 
 def m2s_ilu0_apply(grid, r, z, stream=None):
+    _same("m2s_ilu0_apply", r, ("z", z))
     return _check(load().m2s_ilu0_apply(grid, _ptr(r, "r"), _ptr(z, "z"), _stream(stream)),
                   "m2s_ilu0_apply")
 
@@ -401,11 +436,13 @@ def m2s_line_btri(blk, rhs, axis, work=None, stream=None):
 
 
 def m2s_ssor_sweep(grid, b, u, omega=1.2, n_iters=1, stream=None):
+    _same("m2s_ssor_sweep", u, ("b", b))
     return _check(load().m2s_ssor_sweep(grid, _ptr(b, "b"), _ptr(u, "u"), float(omega),
                                         int(n_iters), _stream(stream)), "m2s_ssor_sweep")
 
 
 def m2s_kappa_grad(grid, u, lam, dLdkappa, stream=None):
+    _same("m2s_kappa_grad", u, ("lambda", lam), ("dLdkappa", dLdkappa))
     return _check(load().m2s_kappa_grad(grid, _ptr(u, "u"), _ptr(lam, "lambda"),
                                         _ptr(dLdkappa, "dLdkappa"), _stream(stream)),
                   "m2s_kappa_grad")
@@ -413,6 +450,7 @@ def m2s_kappa_grad(grid, u, lam, dLdkappa, stream=None):
 
 def m2s_adjoint_solve(grid, u, dLdu, lam, dLdkappa, max_iters=200, rtol=1e-10,
                       fixed_iters=False, check_every=1, stream=None, raise_on_error=True):
+    _same("m2s_adjoint_solve", u, ("dLdu", dLdu), ("lambda", lam), ("dLdkappa", dLdkappa))
     o = _opts(max_iters, rtol, fixed_iters, check_every)
     res = PcgResult()
     st = load().m2s_adjoint_solve(grid, _ptr(u, "u"), _ptr(dLdu, "dLdu"), _ptr(lam, "lambda"),

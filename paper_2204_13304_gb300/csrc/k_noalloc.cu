@@ -21,7 +21,14 @@
 // Set-up: the first call on a device looks up the array's device address
 // with cudaGetSymbolAddress (with that device current) and caches it; make
 // that first call before any stream capture.
+// Every call copies its unit tables from host memory, launches the sweeps on
+// `stream`, synchronises `stream` and reads the status word back.  Its
+// spin-waits are bounded by a fixed 4 s (m2s_set_spin_limit sets the bound
+// of a grid and has no effect here).
+#include <algorithm>
+#include <cstdint>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "m2s_internal.cuh"
@@ -31,6 +38,7 @@ namespace {
 
 constexpr i64 kMaxPoints = 1LL << 18;
 constexpr int kMaxUnits = 8192;
+constexpr long long kSpinNs = 4000000000LL;  // bound of every spin-wait
 constexpr size_t kQBytes = (size_t)kMaxPoints * sizeof(double);  // one buffer
 constexpr size_t kOriginOff = 2 * kQBytes;
 constexpr size_t kProdOff = kOriginOff + (size_t)kMaxUnits * sizeof(int2);
@@ -69,7 +77,7 @@ cudaError_t run(Dims d, const T* b, T* x, int sweeps, unsigned char* base, const
     T* Qb = (T*)(base + kQBytes);
     WaveCall c;
     c.publish_every = 4;
-    c.spin_ns = 4000000000LL;
+    c.spin_ns = kSpinNs;
     c.status = status;
     c.rz_partials = nullptr;
     c.stall_unit = -1;
@@ -98,11 +106,24 @@ extern "C" m2s_status m2s_symgs_noalloc(int nx, int ny, int nz, m2s_dtype dtype,
     if (((uintptr_t)b % align) != 0 || ((uintptr_t)x % align) != 0) return M2S_ERR_INVALID_ARG;
     const i64 n = (i64)nx * ny * nz;
     if (n > kMaxPoints) return M2S_ERR_INVALID_ARG;
+    // b and x must not share a byte: the sweeps write x while reading b
+    const uintptr_t bb = (uintptr_t)b, xb = (uintptr_t)x, bytes = (uintptr_t)n * align;
+    if (bb < xb + bytes && xb < bb + bytes) return M2S_ERR_INVALID_ARG;
     if (n_sym_sweeps == 0) return M2S_OK;
+    // Every row V of units (kWaveSlots - 1 planes of z) holds at least one
+    // unit, so a grid with more such rows than kMaxUnits is rejected before
+    // the host builds its unit table (whose index is (ny + nz) / 30 + 1 by
+    // nz / 4 + 1 entries).
+    const int slots = kWaveSlots - 1;
+    if ((nz + slots - 1) / slots > kMaxUnits) return M2S_ERR_INVALID_ARG;
     Dims d{nx, ny, nz, n, 0};
     std::vector<int2> org;
     std::vector<int4> prod;
-    build_units_host(30, 1, 1, kWaveSlots, d, org, prod);
+    try {
+        build_units_host(30, 1, 1, kWaveSlots, d, org, prod);
+    } catch (const std::bad_alloc&) {
+        return M2S_ERR_OOM;
+    }
     if ((int)org.size() > kMaxUnits) return M2S_ERR_INVALID_ARG;
 
     cudaStream_t st = (cudaStream_t)stream;
