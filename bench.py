@@ -133,26 +133,104 @@ def job_value(ws, t_rank):
     return max_over_ranks(ws, t_rank) / ws
 
 
-def cpu_baseline(n, budget_s=20.0):
-    """The serial oracle on a bounded sample of the workload: MG-PCG
-    iterations of the same 256^3 problem, scaled to seconds per solve with
-    the GPU's iteration count."""
+def oracle_pcg_seconds_per_iteration(n, iters):
+    """The serial oracle's FP64 MG-PCG on the n^3 HPCG problem (b = A*ones,
+    x0 = 0, 4 levels), run for exactly `iters` iterations (the oracle as it
+    stands: V-cycle, SpMV, Dot2 dots and updates); returns seconds per
+    iteration."""
     import numpy as np
     import oracle
-    shape = (n, n, n)
+    b = oracle.apply(oracle.HPCG27, np.ones((n, n, n)))
     t0 = time.perf_counter()
-    b = oracle.apply(oracle.HPCG27, np.ones(shape))
-    # time one V-cycle + one SpMV (the per-iteration work) a few times
-    reps = 0
-    t1 = time.perf_counter()
-    while True:
-        z = oracle.mg_vcycle(oracle.HPCG27, b, 4)
-        oracle.apply(oracle.HPCG27, z)
-        reps += 1
-        if time.perf_counter() - t1 > budget_s / 2 or reps >= 3:
-            break
-    per_iter = (time.perf_counter() - t1) / reps
-    return per_iter, reps, time.perf_counter() - t0
+    oracle.pcg(oracle.HPCG27, b, 4, max_iters=iters, fixed_iters=True)
+    return (time.perf_counter() - t0) / iters
+
+
+def cpu_baseline(n, iters=3):
+    """The serial oracle on a bounded sample of the workload: the first
+    `iters` iterations of the same n^3 MG-PCG solve, timed on one host core
+    and scaled to a solve by the oracle's iteration count."""
+    per_iter = oracle_pcg_seconds_per_iteration(n, iters)
+    return per_iter, iters
+
+
+def oracle_config_times(gpu):
+    """The serial oracle on the other workload configurations, one host core,
+    each on a bounded sample stated beside it.  `gpu` holds the GPU run's
+    iteration counts used to scale per-iteration samples to solves."""
+    import numpy as np
+    import m2s_inputs as gen
+    import oracle
+    out = {}
+    tic = time.perf_counter
+
+    # 32^3 HPCG: the whole configuration (SpMV, one symmetric GS, 50
+    # SGS-PCG iterations)
+    n = 32
+    b = oracle.apply(oracle.HPCG27, np.ones((n, n, n)))
+    t0 = tic()
+    oracle.apply(oracle.HPCG27, b)
+    t1 = tic()
+    oracle.symgs(oracle.HPCG27, b, np.zeros_like(b), 1)
+    t2 = tic()
+    oracle.pcg(oracle.HPCG27, b, 1, max_iters=50, fixed_iters=True)
+    t3 = tic()
+    out["hpcg_32"] = {"spmv_us": (t1 - t0) * 1e6, "symgs_us": (t2 - t1) * 1e6,
+                      "sgs_pcg_50_ms": (t3 - t2) * 1e3, "sample": "the whole configuration"}
+
+    # 162^3 x 5 block SSOR: one iteration on a 64^3 x 5 grid of the same
+    # recipe, scaled by the point count to 162^3 and by 50 iterations
+    ns = 64
+    D, L, U, rhs = gen.block_ssor_inputs(ns)
+    t0 = tic()
+    oracle.ssor(D, L, U, 1.2, rhs, np.zeros_like(rhs), 1)
+    per_pt = (tic() - t0) / ns ** 3
+    del D, L, U
+    out["block_ssor_162x5"] = {"s_50_iters": per_pt * 162 ** 3 * 50,
+                               "ms_per_iter": per_pt * 162 ** 3 * 1e3,
+                               "sample": "one SSOR iteration on 64^3 x 5, scaled by points "
+                                         "(x %.1f) and iterations (x 50)" % ((162 / 64) ** 3)}
+
+    # 256^3 variable-kappa MG-PCG to 1e-10, FP64 and FP32 preconditioner:
+    # two iterations of each at full size, scaled by the GPU's iteration
+    # counts (the same method to the same tolerance)
+    n = 256
+    kap = gen.kappa_field(n)
+    b = oracle.apply(oracle.KAPPA7, np.ones((n, n, n)), kap)
+    r = {}
+    for name, f32 in (("fp64", False), ("fp32_precond", True)):
+        it = gpu.get("kappa_iters_" + name)
+        t0 = tic()
+        oracle.pcg(oracle.KAPPA7, b, 4, kap, max_iters=2, fixed_iters=True, precond_f32=f32)
+        per = (tic() - t0) / 2
+        r[name] = {"s": per * it if it else None, "s_per_iter": per,
+                   "sample": "2 iterations at 256^3 x %s iterations (the GPU solve's count)"
+                             % it}
+    out["kappa_256"] = r
+    del kap, b
+
+    # 64 batched variable-kappa problems, forward solve and adjoint: two
+    # forward iterations and one gradient on a 64^3 problem (3 levels), per
+    # point, scaled by the batch's points and the GPU's iteration counts
+    n = 64
+    kap = gen.kappa_field(n)
+    b = np.ones((n, n, n))
+    t0 = tic()
+    u, _, _, _ = oracle.pcg(oracle.KAPPA7, b, 3, kap, max_iters=2, fixed_iters=True)
+    per_pt_it = (tic() - t0) / 2 / n ** 3
+    t0 = tic()
+    oracle.kappa_grad(u, u)
+    per_pt_grad = (tic() - t0) / n ** 3
+    pts = gpu.get("batch_points")
+    itf, ita = gpu.get("batch_iters_forward"), gpu.get("batch_iters_adjoint")
+    if pts and itf and ita:
+        out["batched_adjoint_64"] = {
+            "forward_s": per_pt_it * pts * itf, "adjoint_s": per_pt_it * pts * ita +
+            per_pt_grad * pts,
+            "sample": "2 PCG iterations and one dL/dkappa on a 64^3 problem, per point, x %d "
+                      "points x the GPU's largest iteration counts (%d forward, %d adjoint)"
+                      % (pts, itf, ita)}
+    return out
 
 
 def oracle_iterations(n):
@@ -167,10 +245,13 @@ def oracle_iterations(n):
         return None, "no stored oracle history for this size"
 
 
-def sweep_traffic(kernel_tag):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None when the kernel's sources changed since the capture."""
+def profile_value(kernel_tag, key, sources=None):
+    """A machine-read figure (`- key: value` line) of the committed ncu summary
+    profiles/<kernel_tag>.md, or None when the summary is missing or the
+    kernel's sources changed since the capture (their sha256 must equal the
+    summary's source_sha256)."""
     import hashlib
+    sources = SWEEP_SOURCES if sources is None else sources
     path = os.path.join(ROOT, "profiles", "%s.md" % kernel_tag)
     try:
         with open(path) as f:
@@ -183,15 +264,21 @@ def sweep_traffic(kernel_tag):
             k, v = ln[2:].split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
     h = hashlib.sha256()
-    for rel in SWEEP_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     if kv.get("source_sha256") != h.hexdigest():
         return None, "kernel changed since the ncu capture"
     try:
-        return float(kv["dram_bytes_per_launch"]), "ncu capture " + os.path.basename(path)
+        return float(kv[key]), "ncu capture " + os.path.basename(path)
     except (KeyError, ValueError):
-        return None, "no DRAM figure in the ncu summary"
+        return None, "no %s in the ncu summary" % key
+
+
+def sweep_traffic(kernel_tag):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel's sources changed since the capture."""
+    return profile_value(kernel_tag, "dram_bytes_per_launch", SWEEP_SOURCES)
 
 
 # sources of the dominant kernel (its DRAM traffic is invalid once they change)
@@ -200,6 +287,12 @@ def sweep_traffic(kernel_tag):
 SWEEP_SOURCES = ("paper_2204_13304_gb300/csrc/k_wave2.cu",
                  "paper_2204_13304_gb300/csrc/m2s_cta.cuh",
                  "paper_2204_13304_gb300/csrc/m2s_wave_sync.cuh")
+SPMV_SOURCES = ("paper_2204_13304_gb300/csrc/k_stencil27.cu",)
+
+# FP64 operations the 27-point sweep executes per row: the separable box sums
+# (row 3-sum, lane-below 2-sum, plane sum) and the update FMA: 8 in a forward
+# sweep (which also writes the next sweep's sums), 7 in a backward one.
+SWEEP_FP64_OPS_PER_ROW = 7.5
 
 
 def profile_case(args):
@@ -484,6 +577,7 @@ def other_configs(m, torch, hbm):
         return {"workload": "64 variable-kappa problems, cube sides from {32,48,64,96,128} by "
                             "seed (%d points), b = 1, MG-PCG (3 levels) to 1e-10, then the "
                             "adjoint solve and dL/dkappa, u_target ~ U(0,1)" % ntot,
+                "points": ntot,
                 "forward_s": tf, "adjoint_s": ta, "iters_max_forward": res[0].iters,
                 "iters_max_adjoint": res[1].iters}
 
@@ -629,32 +723,45 @@ def other_configs(m, torch, hbm):
 
 
 def run_reference(args):
-    """--impl reference: the serial CPU oracle on the same problem, bounded."""
-    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    """--impl reference: the serial CPU oracle on the same problem.  A step is
+    one iteration of the oracle's MG-PCG solve of the n^3 problem on one host
+    core (the oracle as it stands): W iterations untimed, then exactly K
+    iterations of a solve from x0 = 0 timed, so ms_per_step x steps is the
+    timed run.  value scales the measured time per iteration to the metric,
+    seconds per solve to 1e-10, by the oracle's own iteration count for this
+    problem (stored by tests/golden/make_hpcg_pcg_history.py)."""
+    ws, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import numpy as np
     import oracle
     oracle.lib()
-    iters_per_solve, src = oracle_iterations(args.n)
+    n = args.n
+    iters_per_solve, src = oracle_iterations(n)
     if iters_per_solve is None:
         # small grids: the oracle solves the whole problem to count
-        import numpy as np
-        shape = (args.n,) * 3
         _, iters_per_solve, _, _ = oracle.pcg(oracle.HPCG27, oracle.apply(oracle.HPCG27,
-                                                                          np.ones(shape)),
+                                                                          np.ones((n, n, n))),
                                               4, max_iters=500, rtol=1e-10, fixed_iters=False)
         src = "oracle iteration count of a full oracle solve"
-    per_iter, reps, _ = cpu_baseline(args.n, budget_s=min(60.0, 10.0 * max(1, args.steps)))
+    b = oracle.apply(oracle.HPCG27, np.ones((n, n, n)))
+    if args.warmup > 0:
+        oracle.pcg(oracle.HPCG27, b, 4, max_iters=args.warmup, fixed_iters=True)
+    t0 = time.perf_counter()
+    oracle.pcg(oracle.HPCG27, b, 4, max_iters=max(1, args.steps), fixed_iters=True)
+    per_iter = (time.perf_counter() - t0) / max(1, args.steps)
     value = per_iter * iters_per_solve
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3,
+        "step": "one iteration of the oracle's MG-PCG solve (%d per solve)" % iters_per_solve,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(args.n),
+        "data": "synthetic", "config": workload_config(n),
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "s",
-                         "sample": "%d timed V-cycle+SpMV iterations of the %d^3 problem on 1 "
-                                   "host core, x %d iterations per solve (%s)"
-                                   % (reps, args.n, iters_per_solve, src)},
+                         "sample": "%d timed iterations of the oracle's %d^3 MG-PCG solve from "
+                                   "x0 = 0 on 1 host core (after %d untimed), x %d iterations "
+                                   "per solve (%s)" % (args.steps, n, args.warmup,
+                                                       iters_per_solve, src)},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -794,23 +901,54 @@ def main():
         "symgs_sweep_f32": {"ms": t_sweep32 * 1e3, "alg_GBs": 12 * rows / t_sweep32 / 1e9},
     }
     # dominant kernel of the FP64 solve: the Gauss-Seidel sweep on the finest
-    # level, bound by the FP64 issue rate; 27 FP64 operations per row by
-    # definition (26 neighbour terms + the division), against 629 G FP64
-    # op/s.  Its launch duration is the live event timing of the timed solves.
+    # level.  Its roofline is HBM: 24 algorithmic bytes per row (read b and
+    # x, write x), the launch duration the live event timing of the sweeps
+    # inside the timed solves, against the measured copy bandwidth.  The
+    # sweep is bound by its critical path (7(n-1) dependent point updates)
+    # and the FP64 issue rate, so the same launch is also stated against the
+    # FP64 issue peak on the FP64 operations the kernel executes.
     n_l0, ms_l0, _ = sweep_lv[0]
     t_launch = ms_l0 / 1e3 / max(1, n_l0)
-    ach = 27 * rows / t_launch / 1e9
+    alg_bytes = 24 * rows
+    ach = alg_bytes / t_launch / 1e9
     traffic, traffic_src = sweep_traffic("gs27_cta_kernel_f64_%d" % n)
-    roof = {"kernel": "gs27_cta_kernel<double,2,8,2,-1> (Gauss-Seidel sweep, %d^3 level)" % n,
-            "bound": "alu", "achieved": ach, "peak": FP64_OPS_PEAK / 1e9,
-            "unit": "G FP64 op/s", "frac": ach / (FP64_OPS_PEAK / 1e9), "traffic": traffic,
-            "traffic_source": traffic_src,
+    fp64_warp_inst, fp64_src = profile_value("gs27_cta_kernel_f64_%d" % n,
+                                             "fp64_warp_instructions_per_launch")
+    useful = SWEEP_FP64_OPS_PER_ROW * rows
+    fp64 = {"useful_fp64_ops_per_row": SWEEP_FP64_OPS_PER_ROW,
+            "useful_achieved": useful / t_launch / 1e9,
+            "peak": FP64_OPS_PEAK / 1e9, "unit": "G FP64 op/s",
+            "useful_frac": useful / t_launch / FP64_OPS_PEAK,
+            "issued_lane_slots_frac": (fp64_warp_inst * 32 / t_launch / FP64_OPS_PEAK
+                                       if fp64_warp_inst else None),
+            "issued_source": fp64_src,
+            "note": "FP64 operations the kernel executes per row (separable 3x3x3 sums: 8 in "
+                    "a forward sweep, 7 in a backward one), not the definition's 27; the "
+                    "issued fraction counts every lane slot of the FP64 warp instructions "
+                    "ncu counted (idle halo and ramp lanes included); peak 152 SMs x 2 FP64 "
+                    "lanes/clk x 2.07 GHz (derived)"}
+    roof = {"kernel": "gs27_cta_kernel (FP64 Gauss-Seidel sweep, %d^3 level)" % n,
+            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": traffic, "traffic_source": traffic_src,
+            "alg_bytes_per_launch": alg_bytes,
+            "alg_bytes_note": "24 B/row: read b and x, write x (the kernel moves 32 B/row: it "
+                              "reads the pre-scaled old-neighbour sums Q/26 and b/26 and writes "
+                              "x and the next sweep's Q'/26)",
             "launches_timed": n_l0, "ms_per_launch": t_launch * 1e3,
-            "alg_bytes_per_launch": 24 * rows,
-            "hbm_GBs": 24 * rows / t_launch / 1e9,
-            "hbm_frac": 24 * rows / t_launch / 1e9 / hbm,
-            "peak_note": "FP64 issue rate 152 SMs x 2 lanes/clk x 2.07 GHz (derived); HBM %s "
-                         "%.0f GB/s" % (peak_kind, hbm)}
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind,
+            "fp64_issue": fp64}
+    # the SpMV the metric names: HBM rooflines of the FP64 and FP32 forms
+    spmv_roofs = {}
+    for tag, t_k, bpr in (("spmv27_f64", t_spmv, 16), ("spmv27_f32", t_spmv32, 8)):
+        traf, tsrc = profile_value("st27_kernel_%s_%d" % (tag[-3:], n), "dram_bytes_per_launch",
+                                   SPMV_SOURCES)
+        a_ = bpr * rows / t_k / 1e9
+        spmv_roofs[tag] = {"bound": "hbm", "achieved": a_, "peak": hbm, "unit": "GB/s",
+                           "frac": a_ / hbm, "traffic": traf, "traffic_source": tsrc,
+                           "ms_per_launch": t_k * 1e3,
+                           "alg_bytes_per_launch": bpr * rows,
+                           "alg_bytes_note": "%d B/row: read x, write y" % bpr}
+    spmv_roofs["spmv27_f64"]["fp64_useful_frac"] = 7.5 * rows / t_spmv / FP64_OPS_PEAK
     sweep_share = sum(v[1] for v in sweep_lv) / 1e3 / args.steps / t64
 
     # end to end through the public API with host buffers
@@ -851,19 +989,36 @@ def main():
                          "speedup_vs_fp64": t64 / t32},
         "kernels": kern, "sweep_share_of_solve": sweep_share,
         "sweep_ms_per_launch_by_level": [v[1] / max(1, v[0]) for v in sweep_lv],
-        "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps,
+        "roofline": roof, "roofline_spmv": spmv_roofs, "e2e": e2e, "gpu_launches": launches * args.steps,
         "other_configs": configs,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        per_iter, reps, _ = cpu_baseline(n)
+        per_iter, reps = cpu_baseline(n)
         oit, src = oracle_iterations(n)
         if oit is None:
             oit, src = res64.iters, "iteration count of the GPU solve"
         line["cpu_baseline"] = {"value": per_iter * oit, "unit": "s", "cores": 1,
                                 "kind": "oracle",
-                                "sample": "%d V-cycle+SpMV iterations of the %d^3 problem on one "
-                                          "host core, x %d iterations (%s)" % (reps, n, oit, src)}
+                                "sample": "the first %d iterations of the oracle's %d^3 MG-PCG "
+                                          "solve on one host core, x %d iterations (%s)"
+                                          % (reps, n, oit, src)}
+        if configs:
+            gpu_counts = {}
+            try:
+                gpu_counts["kappa_iters_fp64"] = configs["kappa_256"]["fp64"]["iters"]
+                gpu_counts["kappa_iters_fp32_precond"] = \
+                    configs["kappa_256"]["fp32_precond"]["iters"]
+            except (KeyError, TypeError):
+                pass
+            try:
+                c5 = configs["batched_adjoint_64"]
+                gpu_counts.update(batch_points=c5["points"],
+                                  batch_iters_forward=c5["iters_max_forward"],
+                                  batch_iters_adjoint=c5["iters_max_adjoint"])
+            except (KeyError, TypeError):
+                pass
+            line["cpu_baseline"]["other_configs"] = oracle_config_times(gpu_counts)
     if rank == 0:
         print(json.dumps(line))
     g64.close()

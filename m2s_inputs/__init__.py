@@ -51,6 +51,7 @@ STREAM_BTRI_RHS = 12
 STREAM_JAC = 13
 STREAM_JAC_RHS = 14
 STREAM_JAC_U0 = 15
+STREAM_SAMPLES = 16
 
 BATCH_SIDES = (32, 48, 64, 96, 128)
 
@@ -194,3 +195,46 @@ def line_btri_inputs(shape, seed=BASE_SEED):
     blk[..., 1, :, :] = 2.0 * u[..., 1, :, :] - 1.0 + 10.0 * np.eye(5)
     rhs = (2.0 * uniform(seed, STREAM_BTRI_RHS, npts * 5) - 1.0).reshape(shape + (5,))
     return blk, rhs
+
+
+def sample_points(shape, count, seed=BASE_SEED):
+    """Sorted distinct flat indices p = (z * ny + y) * nx + x of a grid of
+    `shape` (nz, ny, nx) at which a full-size result is sampled: every
+    corner, points on every edge and every face, points one cell inside the
+    boundary, and uniform interior points; `count` is the number of drawn
+    points before duplicates are removed (the corners come on top)."""
+    nz, ny, nx = (int(v) for v in shape)
+    ext = np.array([nx, ny, nz], dtype=np.int64)
+    pts = []
+    for cz in (0, nz - 1):
+        for cy in (0, ny - 1):
+            for cx in (0, nx - 1):
+                pts.append((cx, cy, cz))
+    corners = np.array(pts, dtype=np.int64).reshape(-1, 3)
+    u = uniform(seed, STREAM_SAMPLES, 3 * count).reshape(count, 3)
+    xyz = np.minimum((u * ext).astype(np.int64), ext - 1)
+    q = count // 8
+    # classes: [0, q) edges, [q, 3q) faces, [3q, 4q) one cell inside a face,
+    # the rest interior
+    cls = np.arange(count)
+    sel = uniform(seed, STREAM_SAMPLES + 64, 2 * count).reshape(count, 2)
+    axis = np.minimum((sel[:, 0] * 3).astype(np.int64), 2)
+    side = sel[:, 1] < 0.5
+    hi = ext[axis] - 1
+    edge = cls < q
+    face = (cls >= q) & (cls < 3 * q)
+    inner = (cls >= 3 * q) & (cls < 4 * q)
+    rows = np.arange(count)
+    # faces: pin one coordinate to 0 or n - 1
+    f = face | edge
+    xyz[rows[f], axis[f]] = np.where(side[f], 0, hi[f])
+    # edges: pin a second coordinate as well
+    a2 = (axis + 1) % 3
+    hi2 = ext[a2] - 1
+    xyz[rows[edge], a2[edge]] = np.where(sel[edge, 0] * 6 % 1.0 < 0.5, 0, hi2[edge])
+    # one cell inside a face
+    xyz[rows[inner], axis[inner]] = np.where(side[inner], np.minimum(1, hi[inner]),
+                                             np.maximum(hi[inner] - 1, 0))
+    allp = np.concatenate([corners, xyz])
+    flat = (allp[:, 2] * ny + allp[:, 1]) * nx + allp[:, 0]
+    return np.unique(flat)

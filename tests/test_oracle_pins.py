@@ -771,6 +771,57 @@ def test_stored_pcg_histories_start_at_closed_form_norm_of_b(n):
     assert hist[-1] <= 1e-10 * hist[0] < hist[-2]
 
 
+def _load_samples(n, mode):
+    import os
+    hist, idx, val, iters = [], [], [], None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "hpcg_pcg_samples_%d_%s.txt" % (n, mode))
+    with open(path) as f:
+        for line in f:
+            if line.startswith("# iterations"):
+                iters = int(line.split()[2])
+            elif line.startswith("#") or not line.strip():
+                continue
+            elif line.startswith("h "):
+                hist.append(float(line.split()[2]))
+            else:
+                a, v = line.split()
+                idx.append(int(a))
+                val.append(float(v))
+    return iters, np.array(hist), np.array(idx), np.array(val)
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_stored_pcg_samples_are_consistent_oracle_runs(n):
+    """The stored samples of the oracle's full-size MG-PCG solves
+    (tests/golden/make_hpcg_pcg_samples.py) against facts outside the run
+    that wrote them: the history starts at the closed-form ||b||; the
+    50-iteration run and the run to 1e-10 are separate oracle runs whose
+    first 51 residuals agree bitwise (the stopping rule does not change the
+    iterates), and the run to 1e-10 reproduces the separately stored
+    residual history; the sample positions are m2s_inputs.sample_points; the
+    converged solution is the exact solution ones to within the solve's
+    error (the system is A x = A*ones), while 50 iterations are not yet."""
+    import os
+    from math import comb
+    it50, h50, i50, x50 = _load_samples(n, "fixed50")
+    itr, hr, ir, xr = _load_samples(n, "rtol")
+    bb = sum(comb(3, k) * 2 ** k * (n - 2) ** (3 - k) * (27 - 3 ** (3 - k) * 2 ** k) ** 2
+             for k in range(4))
+    assert abs(h50[0] - np.sqrt(bb)) <= 1e-12 * np.sqrt(bb)
+    assert it50 == 50 and len(h50) == 51 and itr == len(hr) - 1
+    assert np.array_equal(h50, hr[:51])
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "hpcg_pcg_history_%d.txt" % n)
+    with open(path) as f:
+        stored = np.array([float(v) for v in f if v.strip() and not v.startswith("#")])
+    assert np.array_equal(hr, stored)
+    want = gen.sample_points((n, n, n), 16384)
+    assert np.array_equal(i50, want) and np.array_equal(ir, want)
+    assert np.max(np.abs(xr - 1.0)) <= 1e-8
+    assert np.max(np.abs(x50 - 1.0)) > 1e-8
+
+
 # ---------------------------------------------------------------------------
 # NPB-SP-shaped line solves (Sec. 1, Sec. 7.2.2): pentadiagonal systems along
 # the lines of one axis, terms outside a line dropped.
