@@ -17,6 +17,7 @@
 // in registers across the z march, so every input plane is read once per
 // CTA (plus the two halo planes).
 #include "m2s_internal.cuh"
+#include "m2s_pcg.cuh"
 
 namespace m2s {
 
@@ -200,8 +201,16 @@ dim3 st27_grid(Dims d) {
 }  // namespace
 
 int st27_num_partials(Dims d) {
+    if (st27_tma_shape_ok(d, sizeof(double))) return st27_tma_pcg_partials(d);
     dim3 g = st27_grid(d);
     return (int)(g.x * g.y * g.z);
+}
+
+template <typename T>
+cudaError_t launch_spmv27(Dims d, const T* x, T* y, int* err, cudaStream_t st) {
+    const cudaError_t e = launch_spmv27_tma<T>(d, x, y, err, st);
+    if (e != cudaErrorNotSupported) return e;
+    return launch_st27<T>(ST27_SPMV, d, d, x, nullptr, nullptr, y, st);
 }
 
 template <typename T>
@@ -256,8 +265,11 @@ cudaError_t launch_scale26(i64 n, const T* x, T* y, cudaStream_t st) {
 // p-update + SpMV + dot: pout = z + beta*pin (beta NULL => pout = z),
 // q = A pout, partials[cta] = sum pout.q over the CTA.
 cudaError_t launch_pspmv_dot(Dims d, const double* z, const double* pin, double* pout,
-                             double* q, const double* beta, double* partials,
+                             double* q, const double* beta, double* partials, int* err,
                              cudaStream_t st) {
+    // the partial count was fixed by st27_num_partials: no fallback from here
+    if (st27_tma_shape_ok(d, sizeof(double)))
+        return launch_pspmv_dot_tma(d, z, pin, pout, q, beta, partials, err, st);
     St27Args<double> a;
     a.d = d;
     a.dc = d;
@@ -300,6 +312,8 @@ template cudaError_t launch_st27_q26<double>(St27Mode, Dims, Dims, const double*
                                              const double*, double*, double*, cudaStream_t);
 template cudaError_t launch_st27_q26<float>(St27Mode, Dims, Dims, const float*, const float*,
                                             const float*, float*, float*, cudaStream_t);
+template cudaError_t launch_spmv27<double>(Dims, const double*, double*, int*, cudaStream_t);
+template cudaError_t launch_spmv27<float>(Dims, const float*, float*, int*, cudaStream_t);
 template cudaError_t launch_scale26<double>(i64, const double*, double*, cudaStream_t);
 template cudaError_t launch_scale26<float>(i64, const float*, float*, cudaStream_t);
 template cudaError_t launch_restrict27<double>(Dims, Dims, const double*, const double*, double*,

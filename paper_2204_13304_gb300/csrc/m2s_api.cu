@@ -278,7 +278,7 @@ cudaError_t op_spmv(m2s_grid* g, int l, const T* x, T* y, cudaStream_t st) {
     if (g->op == M2S_OP_HPCG27) {
         for (int i = 0; i < g->np; ++i) {
             const Dims d = g->dims[i][l];
-            cudaError_t e = launch_st27<T>(ST27_SPMV, d, d, x, nullptr, nullptr, y, st);
+            cudaError_t e = launch_spmv27<T>(d, x, y, &g->status->err, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -469,7 +469,8 @@ cudaError_t pcg_iteration(m2s_grid* g, int k, cudaStream_t st) {
         for (int i = 0; i < np; ++i) {
             const double* beta = (k == 1) ? nullptr : &g->dev[i].beta;
             if ((e = launch_pspmv_dot(g->dims[i][0], g->z, pin, pout, g->q, beta,
-                                      g->part + g->h_st27pre[i], st)) != cudaSuccess)
+                                      g->part + g->h_st27pre[i], &g->status->err, st)) !=
+                cudaSuccess)
                 return e;
         }
         if ((e = launch_finalize_b(FIN_PQ, g->dev, np, g->part, g->d_st27pre, nullptr, nullptr,

@@ -79,7 +79,23 @@ cudaError_t launch_st27_q26(St27Mode mode, Dims d, Dims dc, const T* x, const T*
 // y = x / 26 (as x * fl(1/26)), n elements
 template <typename T>
 cudaError_t launch_scale26(i64 n, const T* x, T* y, cudaStream_t st);
+// p.q partials the fused CG step writes for one problem (one per CTA).
 int st27_num_partials(Dims d);
+
+// TMA-staged forms (k_st27_tma.cu) for rows that are 16-byte aligned:
+// st27_tma_shape_ok(d, sizeof(T)) tells whether d qualifies.
+bool st27_tma_shape_ok(const Dims& d, size_t elem);
+int st27_tma_pcg_partials(const Dims& d);
+template <typename T>
+cudaError_t launch_spmv27_tma(const Dims& d, const T* x, T* y, int* err, cudaStream_t st);
+cudaError_t launch_pspmv_dot_tma(const Dims& d, const double* z, const double* pin, double* pout,
+                                 double* q, const double* beta, double* partials, int* err,
+                                 cudaStream_t st);
+// y = A x of the 27-point operator on one problem's level: the TMA kernel
+// where the shape and the vectors allow it, st27_kernel otherwise.  err is
+// the grid's status word (an expired stage wait records M2S_ERR_TIMEOUT).
+template <typename T>
+cudaError_t launch_spmv27(Dims d, const T* x, T* y, int* err, cudaStream_t st);
 
 // rc = injection of r - A z; rc/26 also written to rcs when rcs is not NULL
 template <typename T>

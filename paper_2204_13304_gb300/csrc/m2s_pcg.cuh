@@ -86,7 +86,10 @@ cudaError_t launch_restrict7_b(const Batch& f, const Batch& c, const KappaLevel<
                                const T* r, const T* z, T* rc, cudaStream_t st);
 cudaError_t launch_kappa_grad_b(const Batch& b, const double* u, const double* lam, double* g,
                                 cudaStream_t st);
+// p = z + beta p_in, q = A p, p.q partials (st27_num_partials(d) of them):
+// the TMA kernel where st27_tma_shape_ok(d, 8), st27_kernel otherwise; err is
+// the grid's status word.
 cudaError_t launch_pspmv_dot(Dims d, const double* z, const double* pin, double* pout, double* q,
-                             const double* beta, double* partials, cudaStream_t st);
+                             const double* beta, double* partials, int* err, cudaStream_t st);
 
 }  // namespace m2s

@@ -125,6 +125,52 @@ def test_spmv_f32(m, kind, shape):
     assert err32(host(y), want) <= TOL32
 
 
+# Shapes for the TMA-staged 27-point SpMV (rows 16-byte aligned: nx a
+# multiple of 2 in FP64, of 4 in FP32): tiles ragged in x (64 / 128 points)
+# and in y (32 rows), several z-chunks, a single plane, a single row, and a
+# row shorter than the tile's halo.
+TMA_SHAPES = [(9, 37, 36), (70, 33, 68), (5, 65, 132), (40, 40, 40), (1, 1, 8), (3, 2, 4),
+              (130, 3, 12)]
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("f32", [False, True])
+def test_spmv27_tma_tiles(m, shape, f32):
+    """The TMA path against the oracle on random data, and bitwise on integer
+    data (b = A*ones is exact in any association)."""
+    import torch
+    g = make_grid(m, shape, pdt=1 if f32 else 0)
+    dt = torch.float32 if f32 else torch.float64
+    x = rnd(shape, 3)
+    y = torch.empty(shape, dtype=dt, device="cuda")
+    if f32:
+        x = x.astype(np.float32)
+        m.m2s_spmv(g.handle, 0, dev(x), y)
+        assert err32(host(y), oracle.apply_f32(H27, x)) <= TOL32
+    else:
+        m.m2s_spmv(g.handle, 0, dev(x), y)
+        assert err64(host(y), oracle.apply(H27, x)) <= TOL64
+    m.m2s_spmv(g.handle, 0, torch.ones(shape, dtype=dt, device="cuda"), y)
+    assert np.array_equal(host(y).astype(np.float64), oracle.apply(H27, np.ones(shape)))
+    m.m2s_grid_sync(g.handle)
+    g.close()
+
+
+@pytest.mark.parametrize("shape", [(9, 37, 36), (40, 40, 40), (3, 2, 4)])
+def test_pcg_tma_step_matches_oracle(m, shape):
+    """The fused CG step (p = z + beta p, q = A p, p.q) through the TMA path
+    inside 12 fixed PCG iterations, against the oracle's PCG."""
+    import torch
+    g = make_grid(m, shape, levels=2)
+    bh = rnd(shape, 4)
+    x = torch.empty(shape, dtype=torch.float64, device="cuda")
+    st, res = m.m2s_pcg_solve(g.handle, dev(bh), x, max_iters=12, fixed_iters=True)
+    assert st == m.Status.OK
+    ox, _, _, _ = oracle.pcg(H27, bh, 2, max_iters=12, fixed_iters=True)
+    assert err64(host(x), ox) <= TOL64
+    g.close()
+
+
 # ---------------------------------------------------------------------------
 # a2-a4: Gauss-Seidel sweeps (exact lexicographic order)
 # ---------------------------------------------------------------------------
@@ -745,3 +791,49 @@ def test_autotuned_sweep_units_keep_the_result(m):
     x = dev(x0)
     m.m2s_symgs(g.handle, 0, dev(b), x, 2)
     assert err64(host(x), oracle.symgs(H27, b, x0, 2)) <= TOL64
+
+
+@pytest.mark.parametrize("f32", [False, True])
+@pytest.mark.parametrize("warps", [4, 8])
+def test_sweep_step_forms_agree_bitwise(m, f32, warps):
+    """The straight-line warp step and the branching one compute the same
+    arithmetic in the same order: bitwise the same sweeps (forward and
+    backward, a batch of ragged problems, 3 levels), and the oracle's."""
+    import os
+    import torch
+    shapes = [(33, 17, 35), (7, 40, 9), (64, 64, 64), (1, 1, 5)]
+    dt = torch.float32 if f32 else torch.float64
+    descs = [dict(nx=s[2], ny=s[1], nz=s[0], op=m.Op.HPCG27, mg_levels=1) for s in shapes]
+    bs = [rnd(s, 90 + i) for i, s in enumerate(shapes)]
+    xs = [rnd(s, 95 + i) for i, s in enumerate(shapes)]
+    out = []
+    old = os.environ.get("M2S_SWEEP_STEP")
+    try:
+        for form in ("classic", "lean"):
+            os.environ["M2S_SWEEP_STEP"] = form
+            g = m.Grid(descs)
+            m.m2s_set_sweep_warps(g.handle, -1, warps)
+            b = dev(np.concatenate([v.ravel() for v in bs]), dt)
+            x = dev(np.concatenate([v.ravel() for v in xs]), dt)
+            m.m2s_symgs(g.handle, 0, b, x, 3)
+            if not f32:
+                m.m2s_gs_sweep(g.handle, 0, b, x, m.FORWARD)
+            m.m2s_grid_sync(g.handle)
+            out.append(host(x))
+            g.close()
+    finally:
+        if old is None:
+            os.environ.pop("M2S_SWEEP_STEP", None)
+        else:
+            os.environ["M2S_SWEEP_STEP"] = old
+    assert np.array_equal(out[0], out[1])
+    off = 0
+    for s, bb, x0 in zip(shapes, bs, xs):
+        n = int(np.prod(s))
+        if f32:
+            o = oracle.symgs_f32(H27, bb, x0, 3)
+            assert err32(out[1][off:off + n].reshape(s), o) <= TOL32
+        else:
+            o = oracle.gs_forward(H27, bb, oracle.symgs(H27, bb, x0, 3))
+            assert err64(out[1][off:off + n].reshape(s), o) <= TOL64
+        off += n
