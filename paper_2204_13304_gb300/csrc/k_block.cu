@@ -65,7 +65,22 @@ __device__ void inv5(const double* a, double* out) {
         for (int j = 0; j < 5; ++j) out[i * 5 + j] = m[i][5 + j];
 }
 
-__global__ void block_setup_kernel(Dims d, const double* __restrict__ D,
+// The stored blocks of op BLOCK7_5x5 are kept entry-major ("structure of
+// arrays"): entry k of the blocks of point p at [k][npts] (D, D^-1: k < 25;
+// L, U: k = d * 25 + r * 5 + c < 75), so that one thread per point reads
+// every entry with one coalesced warp access (32 consecutive points, 256 B)
+// instead of 8-byte words 200-600 B apart.  block_to_soa_kernel makes the
+// copies from the caller's point-major arrays at creation.
+__global__ void block_to_soa_kernel(i64 n, i64 npts, i64 off, int nent,
+                                    const double* __restrict__ src, double* __restrict__ dst) {
+    const i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < nent; ++k) dst[(i64)k * npts + off + i] = src[i * nent + k];
+}
+
+// D^-1 (entry-major, for the residual) and the products M = w D^-1 L,
+// N = w D^-1 U (point-major, for the sweeps' five lanes per point).
+__global__ void block_setup_kernel(Dims d, i64 npts, const double* __restrict__ D,
                                    const double* __restrict__ L, const double* __restrict__ U,
                                    double omega, double* __restrict__ Dinv,
                                    double* __restrict__ M, double* __restrict__ N) {
@@ -74,20 +89,21 @@ __global__ void block_setup_kernel(Dims d, const double* __restrict__ D,
     int x, y, z;
     coords(i, d.nx, d.ny, &x, &y, &z);
     const i64 p = d.off + i;
-    double di[25];
-    inv5(D + p * 25, di);
-    for (int k = 0; k < 25; ++k) Dinv[p * 25 + k] = di[k];
+    double dp[25], di[25];
+    for (int k = 0; k < 25; ++k) dp[k] = D[(i64)k * npts + p];
+    inv5(dp, di);
+    for (int k = 0; k < 25; ++k) Dinv[(i64)k * npts + p] = di[k];
     const bool lo[3] = {x > 0, y > 0, z > 0};
     const bool hi[3] = {x < d.nx - 1, y < d.ny - 1, z < d.nz - 1};
     for (int dd = 0; dd < 3; ++dd) {
-        const double* Lb = L + (p * 3 + dd) * 25;
-        const double* Ub = U + (p * 3 + dd) * 25;
+        const double* Lb = L + (i64)(dd * 25) * npts + p;
+        const double* Ub = U + (i64)(dd * 25) * npts + p;
         for (int r = 0; r < 5; ++r)
             for (int c = 0; c < 5; ++c) {
                 double sl = 0.0, su = 0.0;
                 for (int k = 0; k < 5; ++k) {
-                    sl = fma(di[r * 5 + k], Lb[k * 5 + c], sl);
-                    su = fma(di[r * 5 + k], Ub[k * 5 + c], su);
+                    sl = fma(di[r * 5 + k], Lb[(i64)(k * 5 + c) * npts], sl);
+                    su = fma(di[r * 5 + k], Ub[(i64)(k * 5 + c) * npts], su);
                 }
                 M[(p * 3 + dd) * 25 + r * 5 + c] = lo[dd] ? omega * sl : 0.0;
                 N[(p * 3 + dd) * 25 + r * 5 + c] = hi[dd] ? omega * su : 0.0;
@@ -95,12 +111,13 @@ __global__ void block_setup_kernel(Dims d, const double* __restrict__ D,
     }
 }
 
-// y = A u, or (resid) s = D^-1 (b - A u).  One thread per point.
+// y = A u, or (resid) s = D^-1 (b - A u).  One thread per point, the blocks
+// entry-major (coalesced across the warp); the 5-vectors of u point-major.
 template <bool RESID>
-__global__ void block_apply_kernel(Dims d, const double* __restrict__ D,
-                                   const double* __restrict__ L, const double* __restrict__ U,
-                                   const double* __restrict__ Dinv, const double* __restrict__ b,
-                                   const double* __restrict__ u, double* __restrict__ out) {
+__global__ void __launch_bounds__(128) block_apply_kernel(
+    Dims d, i64 npts, const double* __restrict__ D, const double* __restrict__ L,
+    const double* __restrict__ U, const double* __restrict__ Dinv, const double* __restrict__ b,
+    const double* __restrict__ u, double* __restrict__ out) {
     const i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     int x, y, z;
@@ -108,6 +125,7 @@ __global__ void block_apply_kernel(Dims d, const double* __restrict__ D,
     const i64 p = d.off + i;
     const i64 sy = d.nx, sz = (i64)d.nx * d.ny;
     double acc[5] = {0, 0, 0, 0, 0};
+    // B: entry 0 of the block at this point; entry k at B[k * npts]
     auto mv = [&](const double* B, i64 q) {
         if (!M2S_IN(q - d.off, d.n)) return;
         const double* uq = u + q * 5;
@@ -117,31 +135,31 @@ __global__ void block_apply_kernel(Dims d, const double* __restrict__ D,
 #pragma unroll
         for (int r = 0; r < 5; ++r)
 #pragma unroll
-            for (int c = 0; c < 5; ++c) acc[r] = fma(B[r * 5 + c], v[c], acc[r]);
+            for (int c = 0; c < 5; ++c) acc[r] = fma(B[(i64)(r * 5 + c) * npts], v[c], acc[r]);
     };
-    if (z > 0) mv(L + (p * 3 + 2) * 25, p - sz);
-    if (y > 0) mv(L + (p * 3 + 1) * 25, p - sy);
-    if (x > 0) mv(L + (p * 3 + 0) * 25, p - 1);
-    mv(D + p * 25, p);
-    if (x < d.nx - 1) mv(U + (p * 3 + 0) * 25, p + 1);
-    if (y < d.ny - 1) mv(U + (p * 3 + 1) * 25, p + sy);
-    if (z < d.nz - 1) mv(U + (p * 3 + 2) * 25, p + sz);
+    if (z > 0) mv(L + (i64)50 * npts + p, p - sz);
+    if (y > 0) mv(L + (i64)25 * npts + p, p - sy);
+    if (x > 0) mv(L + p, p - 1);
+    mv(D + p, p);
+    if (x < d.nx - 1) mv(U + p, p + 1);
+    if (y < d.ny - 1) mv(U + (i64)25 * npts + p, p + sy);
+    if (z < d.nz - 1) mv(U + (i64)50 * npts + p, p + sz);
     if constexpr (!RESID) {
 #pragma unroll
         for (int r = 0; r < 5; ++r) out[p * 5 + r] = acc[r];
         return;
     } else {
-    double rr[5];
+        double rr[5];
 #pragma unroll
-    for (int r = 0; r < 5; ++r) rr[r] = b[p * 5 + r] - acc[r];
-    const double* Di = Dinv + p * 25;
+        for (int r = 0; r < 5; ++r) rr[r] = b[p * 5 + r] - acc[r];
+        const double* Di = Dinv + p;
 #pragma unroll
-    for (int r = 0; r < 5; ++r) {
-        double s = 0.0;
+        for (int r = 0; r < 5; ++r) {
+            double s = 0.0;
 #pragma unroll
-        for (int c = 0; c < 5; ++c) s = fma(Di[r * 5 + c], rr[c], s);
-        out[p * 5 + r] = s;
-    }
+            for (int c = 0; c < 5; ++c) s = fma(Di[(i64)(r * 5 + c) * npts], rr[c], s);
+            out[p * 5 + r] = s;
+        }
     }
 }
 
@@ -704,15 +722,12 @@ cudaError_t block_create(BlockOp* b, const m2s_grid_desc* descs, int n_problems,
     if ((e = alloc((void**)&b->w, n * 5 * 8)) != cudaSuccess) return e;
     for (int i = 0; i < n_problems && !b->jac; ++i) {
         const Dims& d = b->dims[i];
-        if ((e = cudaMemcpyAsync(b->D + d.off * 25, descs[i].D, d.n * 25 * 8,
-                                 cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-            return e;
-        if ((e = cudaMemcpyAsync(b->L + d.off * 75, descs[i].L, d.n * 75 * 8,
-                                 cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-            return e;
-        if ((e = cudaMemcpyAsync(b->U + d.off * 75, descs[i].U, d.n * 75 * 8,
-                                 cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-            return e;
+        if (d.n == 0) continue;
+        const unsigned nb = (unsigned)nblk(d.n, 128);
+        block_to_soa_kernel<<<nb, 128, 0, st>>>(d.n, b->npts, d.off, 25, descs[i].D, b->D);
+        block_to_soa_kernel<<<nb, 128, 0, st>>>(d.n, b->npts, d.off, 75, descs[i].L, b->L);
+        block_to_soa_kernel<<<nb, 128, 0, st>>>(d.n, b->npts, d.off, 75, descs[i].U, b->U);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // sweep units of all problems: 5 rows x BW planes, ordered by the step
     // at which they could start on an idle GPU (the unit to the right lags
@@ -774,8 +789,8 @@ cudaError_t block_apply(BlockOp* b, const double* u, double* y, cudaStream_t st)
         if (b->jac)
             block_jac_apply_kernel<<<nblk(d.n, JB), JB, 0, st>>>(d, b->P + (size_t)i * JP, u, y);
         else
-            block_apply_kernel<false><<<nblk(d.n, 128), 128, 0, st>>>(d, b->D, b->L, b->U, nullptr,
-                                                                      nullptr, u, y);
+            block_apply_kernel<false><<<nblk(d.n, 128), 128, 0, st>>>(d, b->npts, b->D, b->L, b->U,
+                                                                      nullptr, nullptr, u, y);
     }
     return cudaGetLastError();
 }
@@ -804,8 +819,8 @@ cudaError_t block_ssor_iter(BlockOp* b, const double* rhs, double* u, double ome
         for (int i = 0; i < b->np; ++i) {
             const Dims& d = b->dims[i];
             if (d.n == 0) continue;
-            block_setup_kernel<<<nblk(d.n, 64), 64, 0, st>>>(d, b->D, b->L, b->U, omega, b->Dinv,
-                                                             b->M, b->N);
+            block_setup_kernel<<<nblk(d.n, 64), 64, 0, st>>>(d, b->npts, b->D, b->L, b->U, omega,
+                                                             b->Dinv, b->M, b->N);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         b->omega = omega;
@@ -814,8 +829,8 @@ cudaError_t block_ssor_iter(BlockOp* b, const double* rhs, double* u, double ome
     for (int i = 0; i < b->np && !b->jac; ++i) {
         const Dims& d = b->dims[i];
         if (d.n == 0) continue;
-        block_apply_kernel<true><<<nblk(d.n, 128), 128, 0, st>>>(d, b->D, b->L, b->U, b->Dinv,
-                                                                 rhs, u, b->s);
+        block_apply_kernel<true><<<nblk(d.n, 128), 128, 0, st>>>(d, b->npts, b->D, b->L, b->U,
+                                                                 b->Dinv, rhs, u, b->s);
     }
     const WaveUnits& un = b->sweep;
     if (un.n_units == 0) return cudaGetLastError();

@@ -17,10 +17,13 @@ struct BlockOp {
     std::vector<double> nu;     // per problem: nu of its parameters (op BLOCK7_JAC)
     std::vector<Dims> dims;     // per problem (points; vectors hold 5 per point)
     i64 npts = 0;               // total points
-    double* D = nullptr;        // [npts][25] (op BLOCK7_5x5; D, L, U not allocated for BLOCK7_JAC)
-    double* L = nullptr;        // [npts][3][25]  couplings to p - e_{x,y,z}
-    double* U = nullptr;        // [npts][3][25]  couplings to p + e_{x,y,z}
-    double* Dinv = nullptr;     // [npts][25] (BLOCK7_JAC: w D^-1 of the current step)
+    // op BLOCK7_5x5: D, L, U and D^-1 entry-major, entry k of point p at
+    // [k][npts] (L, U: k = d * 25 + r * 5 + c, couplings to p -/+ e_{x,y,z});
+    // D, L, U are not allocated for BLOCK7_JAC
+    double* D = nullptr;        // [25][npts]
+    double* L = nullptr;        // [75][npts]
+    double* U = nullptr;        // [75][npts]
+    double* Dinv = nullptr;     // [25][npts] (BLOCK7_JAC: w D^-1 of the current step, [npts][25])
     double* M = nullptr;        // [npts][3][25]  omega D^-1 L (0 off the grid; BLOCK7_JAC: L)
     double* N = nullptr;        // [npts][3][25]  omega D^-1 U (0 off the grid; BLOCK7_JAC: U)
     double* s = nullptr;        // [npts][5] D^-1 (b - A u) (BLOCK7_JAC: (b - A(u) u) / w)

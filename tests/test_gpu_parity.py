@@ -197,7 +197,12 @@ def test_symgs_ten_sweeps(m, kind, shape):
     b, x0 = rnd(shape, 5), rnd(shape, 6)
     x = dev(x0)
     m.m2s_symgs(g.handle, 0, dev(b), x, 10)
-    assert err64(host(x), oracle.symgs(kind, b, x0, 10, kap)) <= TOL64
+    o = oracle.symgs(kind, b, x0, 10, kap)
+    # the random-sign floor: stated at 1e-2 |o|_inf, reported at 1e-3 too
+    print("\n[floor] %s %s: e(1e-2) = %.3e, e(1e-3) = %.3e, max|g - o| / |o|_inf = %.3e"
+          % ("H27" if kind == H27 else "K7", shape, err64(host(x), o), err(host(x), o),
+             np.max(np.abs(host(x) - o)) / np.max(np.abs(o))))
+    assert err64(host(x), o) <= TOL64
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 32), (33, 17, 35), (64, 64, 64)])
@@ -792,48 +797,3 @@ def test_autotuned_sweep_units_keep_the_result(m):
     m.m2s_symgs(g.handle, 0, dev(b), x, 2)
     assert err64(host(x), oracle.symgs(H27, b, x0, 2)) <= TOL64
 
-
-@pytest.mark.parametrize("f32", [False, True])
-@pytest.mark.parametrize("warps", [4, 8])
-def test_sweep_step_forms_agree_bitwise(m, f32, warps):
-    """The straight-line warp step and the branching one compute the same
-    arithmetic in the same order: bitwise the same sweeps (forward and
-    backward, a batch of ragged problems, 3 levels), and the oracle's."""
-    import os
-    import torch
-    shapes = [(33, 17, 35), (7, 40, 9), (64, 64, 64), (1, 1, 5)]
-    dt = torch.float32 if f32 else torch.float64
-    descs = [dict(nx=s[2], ny=s[1], nz=s[0], op=m.Op.HPCG27, mg_levels=1) for s in shapes]
-    bs = [rnd(s, 90 + i) for i, s in enumerate(shapes)]
-    xs = [rnd(s, 95 + i) for i, s in enumerate(shapes)]
-    out = []
-    old = os.environ.get("M2S_SWEEP_STEP")
-    try:
-        for form in ("classic", "lean"):
-            os.environ["M2S_SWEEP_STEP"] = form
-            g = m.Grid(descs)
-            m.m2s_set_sweep_warps(g.handle, -1, warps)
-            b = dev(np.concatenate([v.ravel() for v in bs]), dt)
-            x = dev(np.concatenate([v.ravel() for v in xs]), dt)
-            m.m2s_symgs(g.handle, 0, b, x, 3)
-            if not f32:
-                m.m2s_gs_sweep(g.handle, 0, b, x, m.FORWARD)
-            m.m2s_grid_sync(g.handle)
-            out.append(host(x))
-            g.close()
-    finally:
-        if old is None:
-            os.environ.pop("M2S_SWEEP_STEP", None)
-        else:
-            os.environ["M2S_SWEEP_STEP"] = old
-    assert np.array_equal(out[0], out[1])
-    off = 0
-    for s, bb, x0 in zip(shapes, bs, xs):
-        n = int(np.prod(s))
-        if f32:
-            o = oracle.symgs_f32(H27, bb, x0, 3)
-            assert err32(out[1][off:off + n].reshape(s), o) <= TOL32
-        else:
-            o = oracle.gs_forward(H27, bb, oracle.symgs(H27, bb, x0, 3))
-            assert err64(out[1][off:off + n].reshape(s), o) <= TOL64
-        off += n
