@@ -458,6 +458,15 @@ def other_configs(m, torch, hbm):
                                          fixed_iters=False)[1]
 
             t = time_cuda(torch, solve, 1, 1)
+            if name == "fp64":
+                # the 7-point SpMV: read x and the packed kappa record, write y
+                sets = [(ones.clone(), torch.empty_like(ones)) for _ in range(3)]
+                ts = time_cuda(torch, lambda: [m.m2s_spmv(g.handle, 0, v[0], v[1]) for v in sets],
+                               4, 1) / 3
+                del sets
+                r["spmv7_f64"] = {"ms": ts * 1e3, "alg_GBs": 24.0 * n ** 3 / ts / 1e9,
+                                  "hbm_frac": 24.0 * n ** 3 / ts / 1e9 / hbm,
+                                  "alg_bytes_note": "24 B/row: x, kappa, y"}
             m.m2s_sweep_timing(g.handle, True)
             solve()
             k, ms, _ = m.m2s_sweep_timing_read(g.handle, 0)
@@ -700,13 +709,17 @@ def other_configs(m, torch, hbm):
         return {"workload": "ILU(0) of the HPCG 27-point matrix at 256^3: factorisation and one "
                             "application (forward L, backward U solve), FP64",
                 "factor_ms": t_fac * 1e3, "apply_ms": t_app * 1e3,
-                "hyperplanes": hp, "launches_per_apply": 2 * hp,
-                "apply_alg_GBs": 248.0 * rows / t_app / 1e9,
-                "apply_hbm_frac": 248.0 * rows / t_app / 1e9 / hbm,
-                "alg_bytes_note": "248 B/point per application: the 27 factors, r in, z out and "
-                                  "the intermediate y written and re-read",
-                "bound_note": "one launch per hyperplane x + 2y + 4z (CUDA graph): launch- and "
-                              "latency-bound",
+                "hyperplanes": hp, "launches_per_factor": hp, "launches_per_apply": 2,
+                "apply_alg_GBs": 240.0 * rows / t_app / 1e9,
+                "apply_hbm_frac": 240.0 * rows / t_app / 1e9 / hbm,
+                "alg_bytes_note": "240 B/point per application: the 26 off-diagonal factors and "
+                                  "the pivot's reciprocal (216 B), r in, z out, the intermediate y "
+                                  "written and re-read",
+                "fp64_ops_per_point": 2 * 17,
+                "apply_fp64_frac": 34.0 * rows / t_app / FP64_OPS_PEAK,
+                "bound_note": "each triangle one persistent wavefront launch (the sweep's "
+                              "critical path, 17 FP64 operations per point and triangle); the "
+                              "factorisation one launch per hyperplane x + 2y + 4z",
                 "parity": "tests/test_gpu_ilu.py (oracle on ragged shapes; sampled (LU)_pq = "
                           "a_pq and L U z = r at 256^3)"}
 
@@ -967,7 +980,20 @@ def main():
                            "ms_per_launch": t_k * 1e3,
                            "alg_bytes_per_launch": bpr * rows,
                            "alg_bytes_note": "%d B/row: read x, write y" % bpr}
-    spmv_roofs["spmv27_f64"]["fp64_useful_frac"] = 7.5 * rows / t_spmv / FP64_OPS_PEAK
+    spmv_roofs["spmv27_f64"]["fp64_useful_frac"] = 6.4 * rows / t_spmv / FP64_OPS_PEAK
+    # the residual restriction of the V-cycle's finest level (256^3 -> 128^3):
+    # read z (8 B/fine row; the 3x3x3 boxes around the even points cover it)
+    # and r at the even points, write r_c and r_c/26: ~11 B per fine row
+    rc = torch.empty(((n + 1) // 2,) * 3, dtype=torch.float64, device="cuda")
+    sets_r = [(b.clone(), x64.clone()) for _ in range(2)]
+    t_restrict = time_rotating(lambda v: m.m2s_mg_restrict(g64.handle, 0, v[0], v[1], rc), sets_r)
+    del sets_r
+    a_r = 11.0 * rows / t_restrict / 1e9
+    spmv_roofs["restrict27_f64"] = {"bound": "hbm", "achieved": a_r, "peak": hbm, "unit": "GB/s",
+                                    "frac": a_r / hbm, "ms_per_launch": t_restrict * 1e3,
+                                    "alg_bytes_note": "11 B per fine row: z, r at the even points, "
+                                                      "r_c and r_c/26 written",
+                                    "fp64_useful_frac": 28 * rows / 8 / t_restrict / FP64_OPS_PEAK}
     sweep_share = sum(v[1] for v in sweep_lv) / 1e3 / args.steps / t64
 
     # end to end through the public API with host buffers

@@ -230,9 +230,12 @@ m2s_status m2s_ilu0_factors(m2s_grid* grid, double* out, void* stream);
 /* z = (L U)^{-1} r with the factors of m2s_ilu0_setup: forward substitution
  * with L, then backward substitution with U (packed FP64 finest-level
  * vectors of all problems).  r and z are either the same array or do not
- * overlap.  The launches for a given (r, z) are recorded once into a CUDA
- * graph and replayed; ordered on `stream`.  M2S_ERR_INVALID_ARG before
- * m2s_ilu0_setup or for another operator. */
+ * overlap.  Each substitution is one persistent wavefront launch over all
+ * problems (the dependence of the lexicographic Gauss-Seidel sweep),
+ * ordered on `stream`; its spin-waits are bounded by the grid's spin limit
+ * and an expired wait is reported as M2S_ERR_TIMEOUT by the next
+ * synchronising call.  M2S_ERR_INVALID_ARG before m2s_ilu0_setup or for
+ * another operator. */
 m2s_status m2s_ilu0_apply(m2s_grid* grid, const double* r, double* z,
                           void* stream);
 

@@ -9,10 +9,10 @@
 // finished rows of its lower neighbours, and so do the forward and backward
 // substitutions: the same dependence as the lexicographic Gauss-Seidel
 // sweep, so every point of a hyperplane t = x + 2y + 4z depends only on
-// earlier hyperplanes.  Each launch here processes one hyperplane (one
-// thread per point), and stream order between the launches carries every
-// dependence: no kernel waits on another, nothing can hang.  The
-// application replays its 2 (T + 1) launches from a CUDA graph.
+// earlier hyperplanes.  Each factorisation launch here processes one
+// hyperplane (one thread per point), and stream order between the launches
+// carries every dependence: no kernel waits on another.  The application
+// (k_ilu_wave.cu) runs each triangle as one persistent wavefront launch.
 #include <algorithm>
 
 #include "m2s_bounds.cuh"
@@ -101,69 +101,6 @@ __global__ void __launch_bounds__(IB) ilu_factor_kernel(Dims d, int t, int z0,
     Ib[p] = 1.0 / f[13];
 }
 
-// Ask L2 for the 216 bytes of factors (and, forward, the right-hand side)
-// of this row's point on the next hyperplane, x + 1 forward and x - 1
-// backward: that launch then reads them from L2 instead of HBM.
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-// forward: y_p = r_p - sum_{o < 13} F[p][o] y_q, y kept in z (two partial
-// sums halve the chain of dependent FMAs)
-__global__ void __launch_bounds__(IB) ilu_lower_kernel(Dims d, int t, int z0,
-                                                       const double* __restrict__ F,
-                                                       const double* r, double* z) {
-    int x, y, zz;
-    if (!hyperplane_point(d, t, z0, &x, &y, &zz)) return;
-    const Inside in = inside_of(d, x, y, zz);
-    const i64 p = ((i64)zz * d.ny + y) * d.nx + x;
-    if (!M2S_IN(p, d.n)) return;
-    const double* Fp = F + 27 * (d.off + p);
-    const double* zb = z + d.off;
-    if (x + 1 < d.nx) {
-        prefetch_l2(Fp + 27);
-        prefetch_l2(Fp + 27 + 16);
-        prefetch_l2(r + d.off + p + 1);
-    }
-    double s0 = r[d.off + p], s1 = 0.0;
-#pragma unroll
-    for (int o = 0; o < 13; ++o)
-        if (in(odx(o), ody(o), odz(o)) && M2S_IN(nbr(d, p, odx(o), ody(o), odz(o)), d.n)) {
-            const double v = zb[nbr(d, p, odx(o), ody(o), odz(o))];
-            if (o & 1) s1 = fma(-__ldg(Fp + o), v, s1);
-            else s0 = fma(-__ldg(Fp + o), v, s0);
-        }
-    z[d.off + p] = s0 + s1;
-}
-
-// backward: z_p = (y_p - sum_{o > 13} F[p][o] z_q) / F[p][13], the division
-// as a product with the pivot's rounded reciprocal
-__global__ void __launch_bounds__(IB) ilu_upper_kernel(Dims d, int t, int z0,
-                                                       const double* __restrict__ F,
-                                                       const double* __restrict__ Finv, double* z) {
-    int x, y, zz;
-    if (!hyperplane_point(d, t, z0, &x, &y, &zz)) return;
-    const Inside in = inside_of(d, x, y, zz);
-    const i64 p = ((i64)zz * d.ny + y) * d.nx + x;
-    if (!M2S_IN(p, d.n)) return;
-    const double* Fp = F + 27 * (d.off + p);
-    const double* zb = z + d.off;
-    if (x > 0) {
-        prefetch_l2(Fp - 27);
-        prefetch_l2(Fp - 27 + 16);
-        prefetch_l2(Finv + d.off + p - 1);
-    }
-    double s0 = zb[p], s1 = 0.0;
-#pragma unroll
-    for (int o = 14; o < 27; ++o)
-        if (in(odx(o), ody(o), odz(o)) && M2S_IN(nbr(d, p, odx(o), ody(o), odz(o)), d.n)) {
-            const double v = zb[nbr(d, p, odx(o), ody(o), odz(o))];
-            if (o & 1) s1 = fma(-__ldg(Fp + o), v, s1);
-            else s0 = fma(-__ldg(Fp + o), v, s0);
-        }
-    z[d.off + p] = (s0 + s1) * __ldg(Finv + d.off + p);
-}
-
 // Launch shape of hyperplane t: the z that meet it (0 <= t - 4z <= (nx-1) +
 // 2(ny-1)), one CTA row each; the window of at most nx/2 + 2 values of y
 // per z in CTAs of up to IB threads (a warp multiple).
@@ -195,27 +132,6 @@ cudaError_t launch_ilu_factor(const Dims& d, double* F, double* Finv, cudaStream
         const HpLaunch h = hyperplane_launch(d, t);
         if (h.grid.y == 0) continue;
         ilu_factor_kernel<<<h.grid, h.block, 0, st>>>(d, t, h.z0, F, Finv);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* Finv, const double* r,
-                             double* z, cudaStream_t st) {
-    if (d.n == 0) return cudaSuccess;
-    const int T = ilu_hyperplanes(d);
-    for (int t = 0; t < T; ++t) {
-        const HpLaunch h = hyperplane_launch(d, t);
-        if (h.grid.y == 0) continue;
-        ilu_lower_kernel<<<h.grid, h.block, 0, st>>>(d, t, h.z0, F, r, z);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    for (int t = T - 1; t >= 0; --t) {
-        const HpLaunch h = hyperplane_launch(d, t);
-        if (h.grid.y == 0) continue;
-        ilu_upper_kernel<<<h.grid, h.block, 0, st>>>(d, t, h.z0, F, Finv, z);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -100,13 +100,13 @@ struct m2s_grid {
     // workspaces made at first use, so that a grid used only for FP64
     // sweeps holds no Krylov vectors and no FP32 hierarchy (a 1536^3 FP64
     // vector is 29 GB)
-    // ILU(0) factors of the finest level (m2s_ilu0_setup) and the CUDA graph
-    // of their application for the vectors (ilu_r, ilu_z)
+    // ILU(0) factors of the finest level (m2s_ilu0_setup)
     double* ilu_F = nullptr;
     double* ilu_inv = nullptr;  // 1 / pivot per point
-    cudaGraphExec_t ilu_graph = nullptr;
-    const double* ilu_r = nullptr;
-    double* ilu_z = nullptr;
+    // the application's weight records (forward, backward) and wavefront units
+    double* ilu_Lw = nullptr;
+    double* ilu_Uw = nullptr;
+    WaveUnits ilu_units{};
     bool pcg_ready = false;  // r, z, zold, p0, p1, q
     bool f32_ready = false;  // FP32 level arrays, sweep schedules, r32, z32
     std::vector<int> w32_choice;  // 27-point FP32 warps per unit, per level
@@ -155,7 +155,7 @@ void destroy_grid(m2s_grid* g) {
         for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
     for (cudaGraphExec_t& ge : g->graph)
         if (ge) cudaGraphExecDestroy(ge);
-    if (g->ilu_graph) cudaGraphExecDestroy(g->ilu_graph);
+    free_wave_units(&g->ilu_units);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
 }
@@ -1130,8 +1130,14 @@ m2s_status m2s_ilu0_setup(m2s_grid* g, void* stream) {
     cudaStream_t st = S(stream);
     if (!g->ilu_F) M2S_TRY(galloc(g, &g->ilu_F, 27 * g->ltot[0]));
     if (!g->ilu_inv) M2S_TRY(galloc(g, &g->ilu_inv, g->ltot[0]));
+    if (!g->ilu_Lw) M2S_TRY(galloc(g, &g->ilu_Lw, 16 * g->ltot[0]));
+    if (!g->ilu_Uw) M2S_TRY(galloc(g, &g->ilu_Uw, 16 * g->ltot[0]));
     for (int i = 0; i < g->np; ++i)
         M2S_TRY(launch_ilu_factor(g->dims[i][0], g->ilu_F, g->ilu_inv, st));
+    std::vector<Dims> d0(g->np);
+    for (int i = 0; i < g->np; ++i) d0[i] = g->dims[i][0];
+    M2S_TRY(ilu_wave_setup(d0, g->ltot[0], g->ilu_F, g->ilu_inv, g->ilu_Lw, g->ilu_Uw,
+                           &g->ilu_units, st));
     g->last_stream = st;
     return M2S_OK;
 }
@@ -1151,35 +1157,10 @@ m2s_status m2s_ilu0_apply(m2s_grid* g, const double* r, double* z, void* stream)
     const uintptr_t a = (uintptr_t)r, b = (uintptr_t)z;
     if (a != b && a < b + (uintptr_t)bytes && b < a + (uintptr_t)bytes) return M2S_ERR_INVALID_ARG;
     cudaStream_t st = S(stream);
-    if (!g->ilu_graph || g->ilu_r != r || g->ilu_z != z) {
-        // record the 2 (T + 1) launches of every problem once on the grid's
-        // own stream, replay them on the caller's
-        if (g->ilu_graph) {
-            cudaGraphExecDestroy(g->ilu_graph);
-            g->ilu_graph = nullptr;
-        }
-        if (!g->cap_stream)
-            M2S_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
-        cudaGraph_t gr = nullptr;
-        M2S_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t ce = cudaSuccess;
-        for (int i = 0; i < g->np && ce == cudaSuccess; ++i)
-            ce = launch_ilu_apply(g->dims[i][0], g->ilu_F, g->ilu_inv, r, z, g->cap_stream);
-        const cudaError_t ee = cudaStreamEndCapture(g->cap_stream, &gr);
-        if (ce != cudaSuccess || ee != cudaSuccess) {
-            if (gr) cudaGraphDestroy(gr);
-            return cuda_status(ce != cudaSuccess ? ce : ee);
-        }
-        const cudaError_t ie = cudaGraphInstantiate(&g->ilu_graph, gr, 0);
-        cudaGraphDestroy(gr);
-        if (ie != cudaSuccess) {
-            g->ilu_graph = nullptr;
-            return cuda_status(ie);
-        }
-        g->ilu_r = r;
-        g->ilu_z = z;
-    }
-    M2S_TRY(cudaGraphLaunch(g->ilu_graph, st));
+    // forward substitution y = L^-1 r into z, then backward z = U^-1 y in
+    // place: one wavefront launch each, all problems of the grid
+    M2S_TRY(launch_ilu_wave(g->ilu_units, 0, g->spin_ns, g->status, g->ilu_Lw, r, z, st));
+    M2S_TRY(launch_ilu_wave(g->ilu_units, 1, g->spin_ns, g->status, g->ilu_Uw, z, z, st));
     g->last_stream = st;
     return M2S_OK;
 }

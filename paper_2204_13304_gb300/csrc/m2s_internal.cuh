@@ -212,8 +212,6 @@ int ilu_hyperplanes(const Dims& d);
 // Finv[n]: the pivots' rounded reciprocals 1/F[p][13], written by the
 // factorisation and used in place of divisions
 cudaError_t launch_ilu_factor(const Dims& d, double* F, double* Finv, cudaStream_t st);
-cudaError_t launch_ilu_apply(const Dims& d, const double* F, const double* Finv, const double* r,
-                             double* z, cudaStream_t st);
 // Block-tridiagonal (5x5) line solves (k_line.cu).
 i64 line_btri_work_doubles(int nx, int ny, int nz);
 
@@ -222,6 +220,16 @@ i64 line_btri_work_doubles(int nx, int ny, int nz);
 // source line and out[2] index of the first; cleared by the read
 cudaError_t bounds_read_block(long long* out);
 cudaError_t bounds_read_ilu(long long* out);
+// ILU(0) application as two CTA-wavefront launches (k_ilu_wave.cu): weight
+// records Lw, Uw ([n][16] each, packed over problems) from F and Finv, and
+// the sweep units of the problems (made at the first call).
+cudaError_t ilu_wave_setup(const std::vector<Dims>& dims, i64 n, const double* F,
+                           const double* Finv, double* Lw, double* Uw, WaveUnits* units,
+                           cudaStream_t st);
+// forward (rev 0: Wt = Lw, in = r, out = z) or backward (rev 1: Wt = Uw,
+// in = out = z) substitution of all problems, one launch
+cudaError_t launch_ilu_wave(const WaveUnits& u, int rev, long long spin_ns, DevStatus* status,
+                            const double* Wt, const double* in, double* out, cudaStream_t st);
 cudaError_t bounds_read_line(long long* out);
 cudaError_t launch_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* rhs,
                              double* work, cudaStream_t st);
