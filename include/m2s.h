@@ -420,8 +420,9 @@ m2s_status m2s_sweep_timing_read(m2s_grid* grid, int level, int* launches,
                                  double* total_ms, int* dropped);
 
 /* Fault-injection hook for tests (host side; nothing faults on the GPU):
- * in the next Gauss-Seidel sweep on `level`, wavefront unit `unit` (in ticket
- * order) neither computes nor publishes its progress.  The units that wait
+ * in the next Gauss-Seidel sweep on `level` (level = -1: in the forward
+ * substitution of the next m2s_ilu0_apply of this 27-point grid), wavefront
+ * unit `unit` (in ticket order) neither computes nor publishes its progress.  The units that wait
  * on it run into their bounded spin-wait, every sweep unit stops, and the
  * next synchronising call returns M2S_ERR_TIMEOUT; the sweep machinery is
  * reset and usable afterwards.  The sweep's output is then undefined. */

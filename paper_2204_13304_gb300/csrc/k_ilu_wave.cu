@@ -18,9 +18,9 @@
 // below it (x - 1, x, x + 1: one shuffle per step) and of the three rows of
 // the plane below (rows u - 2, u - 1, u of the warp below, from its ring, or
 // for warp 0 from the top plane of the unit underneath, read from a
-// mailbox of full rows), and forms the 13-term sum in four independent
-// chains.  Each point's 13 weights and its scale sit in one 128-byte record
-// (eight 16-byte loads, prefetched two steps ahead).
+// mailbox of full rows), and forms the 13-term sum in two chains.  Each
+// point's 13 weights and its scale sit in one 128-byte record (seven 16-byte
+// loads into registers two steps ahead, asked of L2 six steps ahead).
 #include <algorithm>
 #include <climits>
 #include <vector>
@@ -66,6 +66,7 @@ struct IluArgs {
     u64* mbox;  // tagged x of the rows the unit to the right replays
     u64* mbt;   // tagged x of the top plane of every unit, full rows
     const long long* mboff;
+    int stall_unit;  // test hook: this unit neither computes nor publishes (-1: none)
 };
 
 template <int W>
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(W * 32, 1) ilu_cta_kernel(IluArgs a) {
         const int v1 = un.y + warp, y1 = un.x - 2 + lane - v1;
         const int mine = lane >= 2 && v1 < dd.nz && y1 >= 0 && y1 < dd.ny;
         int ab = 0;
-        if (threadIdx.x == 0) ab = ld_relaxed_gpu(&a.status->abort);
+        if (threadIdx.x == 0) ab = ld_relaxed_gpu(&a.status->abort) || t == a.stall_unit;
         const int any = __syncthreads_or(mine);
         ab = __syncthreads_or(ab);
         if (any && !ab) ilu_warp<W>(a, t, warp, sh, s_tag);
@@ -409,7 +410,8 @@ cudaError_t ilu_wave_setup(const std::vector<Dims>& dims, i64 n, const double* F
 }
 
 cudaError_t launch_ilu_wave(const WaveUnits& u, int rev, long long spin_ns, DevStatus* status,
-                            const double* Wt, const double* in, double* out, cudaStream_t st) {
+                            const double* Wt, const double* in, double* out, int stall_unit,
+                            cudaStream_t st) {
     if (u.n_units == 0) return cudaSuccess;
     IluArgs a;
     a.rev = rev;
@@ -425,6 +427,7 @@ cudaError_t launch_ilu_wave(const WaveUnits& u, int rev, long long spin_ns, DevS
     a.mbox = u.d_mbox;
     a.mbt = u.d_mbox + u.mb_words;
     a.mboff = u.d_mboff;
+    a.stall_unit = stall_unit;
     ilu_cta_kernel<kW><<<u.grid, kW * 32, kIluSmem, st>>>(a);
     return cudaGetLastError();
 }

@@ -107,6 +107,7 @@ struct m2s_grid {
     double* ilu_Lw = nullptr;
     double* ilu_Uw = nullptr;
     WaveUnits ilu_units{};
+    int ilu_stall_unit = -1;  // test hook consumed by the next ILU(0) application
     bool pcg_ready = false;  // r, z, zold, p0, p1, q
     bool f32_ready = false;  // FP32 level arrays, sweep schedules, r32, z32
     std::vector<int> w32_choice;  // 27-point FP32 warps per unit, per level
@@ -831,8 +832,13 @@ m2s_status m2s_grid_destroy(m2s_grid* grid) {
 }
 
 m2s_status m2s_debug_stall_unit(m2s_grid* grid, int level, int unit) {
-    if (!valid_level(grid, level) || unit < 0 || is_block(grid->op))
-        return M2S_ERR_INVALID_ARG;
+    if (!grid || unit < 0 || is_block(grid->op)) return M2S_ERR_INVALID_ARG;
+    if (level == -1) {  // the next ILU(0) application's forward substitution
+        if (grid->op != M2S_OP_HPCG27) return M2S_ERR_INVALID_ARG;
+        grid->ilu_stall_unit = unit;
+        return M2S_OK;
+    }
+    if (!valid_level(grid, level)) return M2S_ERR_INVALID_ARG;
     grid->stall_level = level;
     grid->stall_unit = unit;
     return M2S_OK;
@@ -1159,8 +1165,10 @@ m2s_status m2s_ilu0_apply(m2s_grid* g, const double* r, double* z, void* stream)
     cudaStream_t st = S(stream);
     // forward substitution y = L^-1 r into z, then backward z = U^-1 y in
     // place: one wavefront launch each, all problems of the grid
-    M2S_TRY(launch_ilu_wave(g->ilu_units, 0, g->spin_ns, g->status, g->ilu_Lw, r, z, st));
-    M2S_TRY(launch_ilu_wave(g->ilu_units, 1, g->spin_ns, g->status, g->ilu_Uw, z, z, st));
+    const int stall = g->ilu_stall_unit;
+    g->ilu_stall_unit = -1;
+    M2S_TRY(launch_ilu_wave(g->ilu_units, 0, g->spin_ns, g->status, g->ilu_Lw, r, z, stall, st));
+    M2S_TRY(launch_ilu_wave(g->ilu_units, 1, g->spin_ns, g->status, g->ilu_Uw, z, z, -1, st));
     g->last_stream = st;
     return M2S_OK;
 }

@@ -228,8 +228,11 @@ cudaError_t ilu_wave_setup(const std::vector<Dims>& dims, i64 n, const double* F
                            cudaStream_t st);
 // forward (rev 0: Wt = Lw, in = r, out = z) or backward (rev 1: Wt = Uw,
 // in = out = z) substitution of all problems, one launch
+// stall_unit >= 0: that unit (ticket order) neither computes nor publishes
+// (host-side fault injection for tests; its consumers' waits expire)
 cudaError_t launch_ilu_wave(const WaveUnits& u, int rev, long long spin_ns, DevStatus* status,
-                            const double* Wt, const double* in, double* out, cudaStream_t st);
+                            const double* Wt, const double* in, double* out, int stall_unit,
+                            cudaStream_t st);
 cudaError_t bounds_read_line(long long* out);
 cudaError_t launch_line_btri(int nx, int ny, int nz, int axis, const double* blk, double* rhs,
                              double* work, cudaStream_t st);

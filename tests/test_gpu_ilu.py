@@ -158,3 +158,28 @@ def test_ilu0_256_sampled_identities(m):
         worst = max(worst, float((acc - torch.from_numpy(want).cuda()).abs().max()))
     assert worst <= 1e-12
     g.close()
+
+
+def test_ilu0_apply_timeout_is_reported_and_recoverable(m):
+    """Host-injected stall in the ILU(0) application's wavefront: one unit
+    of the forward substitution never publishes, its consumers' bounded waits
+    expire, the next synchronising call reports TIMEOUT, and the next
+    application is correct."""
+    import torch
+    shape = (40, 40, 40)
+    g = grid(m, [shape])
+    m.m2s_ilu0_setup(g.handle)
+    m.m2s_set_spin_limit(g.handle, 50_000_000)
+    r = gen.random_vector(shape, seed=gen.BASE_SEED + 97)
+    rd = torch.from_numpy(r).cuda()
+    z = torch.empty(shape, dtype=torch.float64, device="cuda")
+    m.m2s_debug_stall_unit(g.handle, -1, 0)
+    m.m2s_ilu0_apply(g.handle, rd, z)
+    with pytest.raises(m.M2SError) as ei:
+        m.m2s_grid_sync(g.handle)
+    assert ei.value.status == m.Status.TIMEOUT
+    m.m2s_ilu0_apply(g.handle, rd, z)
+    m.m2s_grid_sync(g.handle)
+    want = oracle.ilu0_apply(oracle.ilu0_factor(shape), r)
+    assert err(z.cpu().numpy(), want) <= 1e-13
+    g.close()

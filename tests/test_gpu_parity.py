@@ -797,3 +797,30 @@ def test_autotuned_sweep_units_keep_the_result(m):
     m.m2s_symgs(g.handle, 0, dev(b), x, 2)
     assert err64(host(x), oracle.symgs(H27, b, x0, 2)) <= TOL64
 
+
+
+def test_batched_pcg_mixes_tma_and_fallback_steps(m):
+    """One grid of four problems whose packed offsets and row lengths send
+    the fused CG step of two of them through the TMA kernel and of two
+    through st27_kernel (a ragged row, then an odd offset): each problem's
+    p.q partials stay in its own range, so every problem still matches the
+    oracle's PCG of that problem alone."""
+    import torch
+    shapes = [(8, 10, 12), (3, 5, 6), (3, 3, 5), (4, 4, 8)]
+    descs = [dict(nx=s[2], ny=s[1], nz=s[0], op=m.Op.HPCG27, mg_levels=2) for s in shapes]
+    g = m.Grid(descs)
+    bs = [rnd(s, 110 + i) for i, s in enumerate(shapes)]
+    b = dev(np.concatenate([v.ravel() for v in bs]))
+    x = torch.empty_like(b)
+    st, res = m.m2s_pcg_solve(g.handle, b, x, max_iters=12, fixed_iters=True)
+    assert st == m.Status.OK
+    y = torch.empty_like(b)
+    m.m2s_spmv(g.handle, 0, b, y)
+    xh, yh = host(x), host(y)
+    off = 0
+    for s, bb in zip(shapes, bs):
+        n = int(np.prod(s))
+        ox, _, _, _ = oracle.pcg(H27, bb, 2, max_iters=12, fixed_iters=True)
+        assert err64(xh[off:off + n].reshape(s), ox) <= TOL64
+        assert err64(yh[off:off + n].reshape(s), oracle.apply(H27, bb)) <= TOL64
+        off += n
