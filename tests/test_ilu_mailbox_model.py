@@ -85,10 +85,11 @@ SHAPES = [(5, 3, 4), (17, 33, 32), (33, 17, 35), (16, 64, 16), (40, 11, 3), (70,
 
 
 @pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("W", [4, 8])
 @pytest.mark.parametrize("rev", [False, True])
-def test_ilu_mailbox_layout(shape, rev):
+def test_ilu_mailbox_layout(shape, W, rev):
     nz, ny, nx = shape
-    check_ilu_layout(nx, ny, nz, 4, rev)
+    check_ilu_layout(nx, ny, nz, W, rev)
 
 
 def test_ilu_mailbox_reads_happen():
