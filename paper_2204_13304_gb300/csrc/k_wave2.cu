@@ -214,51 +214,31 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
         if (in0) good = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &gin) && good;
         const TW* re = ring_in ? &sh.ring[w - 1][(tnow - 1) & (RING - 1)][lane] : nullptr;
         const unsigned gtag = (unsigned)(tnow - 1 + BIAS);
-        if constexpr (sizeof(T) == 8) {
-            // The warp below writes a ring entry at each of its steps; this
-            // warp's step s reads the entry of its step s + 1 (all but the
-            // last), so the wait needs no vote.  A poll reloads only what is
-            // missing and reads the abort word and the clock once every 32
-            // polls, so that it costs one load.
-            bool okx = good, okg = true;
-            if (ring_in && s + 1 < S) okg = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin);
-            if (!__all_sync(FULL, okx && okg)) {
-                bool ok1 = !(in1 && halo), ok0 = !in0;
-                if (!ok1) ok1 = Tagged<T>::unpack(regs_to_tw(q, bv), tag, &X1);
-                if (!ok0) ok0 = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &gin);
-                unsigned long long t0 = 0;
-                for (int it = 1;; ++it) {
-                    if (!okg) okg = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin);
-                    if (!ok1) ok1 = Tagged<T>::unpack(mb_load<T>(mbox_p, L1 + step_dir * x1), tag, &X1);
-                    if (!ok0) ok0 = Tagged<T>::unpack(mb_load<T>(mbg_p, L1 + step_dir * x1), tag, &gin);
-                    if (__all_sync(FULL, ok1 && ok0 && okg)) break;
-                    if ((it & 31) == 0) {
-                        const unsigned long long now = global_ns();
-                        if (t0 == 0) t0 = now;
-                        if (fail()) { ok = false; return; }
-                        if ((long long)(now - t0) > a.spin_ns) { timeout(); ok = false; return; }
-                    }
-                }
-            }
-        } else {
-            // FP32: the plane-sum wait is taken when a lane computes, and a
-            // poll rereads every source and the abort word and clock: the
-            // longer poll leaves issue slots to the warp that shares the
-            // sub-partition, which measured faster for the cheap FP32 step.
-            const bool need_g = ring_in && __any_sync(FULL, comp);
-            if (need_g) good = Tagged<T>::unpack(*re, gtag, &gin) && good;
-            if (!__all_sync(FULL, good)) {
-                const unsigned long long t0 = global_ns();
-                for (;;) {
-                    good = true;
-                    if (in1 && halo)
-                        good = Tagged<T>::unpack(mb_load<T>(mbox_p, L1 + step_dir * x1), tag, &X1);
-                    if (in0)
-                        good = Tagged<T>::unpack(mb_load<T>(mbg_p, L1 + step_dir * x1), tag, &gin) && good;
-                    if (need_g) good = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin) && good;
-                    if (__all_sync(FULL, good)) break;
+        // The warp below writes a ring entry at each of its steps; this warp's
+        // step s reads the entry of its step s + 1 (all but the last), so the
+        // wait needs no vote.  A poll reloads only what is missing and reads
+        // the abort word and the clock once every 32 polls, so that it costs
+        // one load: a consumer sees its producer's value within a few dozen
+        // cycles of its arrival (FP32 measured 1.15 -> 1.11 ms per 256^3
+        // sweep against a poll that rereads every source, the abort word and
+        // the clock each time).
+        bool okx = good, okg = true;
+        if (ring_in && s + 1 < S) okg = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin);
+        if (!__all_sync(FULL, okx && okg)) {
+            bool ok1 = !(in1 && halo), ok0 = !in0;
+            if (!ok1) ok1 = Tagged<T>::unpack(regs_to_tw(q, bv), tag, &X1);
+            if (!ok0) ok0 = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &gin);
+            unsigned long long t0 = 0;
+            for (int it = 1;; ++it) {
+                if (!okg) okg = Tagged<T>::unpack(*(volatile const TW*)re, gtag, &gin);
+                if (!ok1) ok1 = Tagged<T>::unpack(mb_load<T>(mbox_p, L1 + step_dir * x1), tag, &X1);
+                if (!ok0) ok0 = Tagged<T>::unpack(mb_load<T>(mbg_p, L1 + step_dir * x1), tag, &gin);
+                if (__all_sync(FULL, ok1 && ok0 && okg)) break;
+                if ((it & 31) == 0) {
+                    const unsigned long long now = global_ns();
+                    if (t0 == 0) t0 = now;
                     if (fail()) { ok = false; return; }
-                    if ((long long)(global_ns() - t0) > a.spin_ns) { timeout(); ok = false; return; }
+                    if ((long long)(now - t0) > a.spin_ns) { timeout(); ok = false; return; }
                 }
             }
         }
