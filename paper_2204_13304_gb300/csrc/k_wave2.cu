@@ -399,12 +399,14 @@ int cta_occupancy() {
 bool cta_warps_supported(int warps) { return warps == 4 || warps == 8; }
 
 // Default warps per unit, from sweep timings on a GB300 (m2s_autotune_sweeps
-// measures instead): FP64 levels of at most 64^3 points run faster with
-// 4-warp units (more, shorter units shorten the critical path: 0.41 vs
-// 0.46 ms at 64^3, 0.21 vs 0.23 ms at 32^3), larger FP64 levels and all FP32
-// levels with 8 (1.93 vs 2.81 ms at 256^3).
+// measures instead), with one CTA per SM: FP64 levels run fastest with
+// 4-warp units at every size (256^3: 1.69 vs 1.70 ms, 128^3: 0.73 vs
+// 0.80 ms; a lone warp on its sub-partition steps at 0.65 us against 0.73 us
+// for two), FP32 levels with 8 (256^3: 1.12 vs 1.30 ms: the cheaper FP32
+// step leaves the SM short of resident units when they are half as tall).
 int cta_default_warps(int dtype_is_f64, Dims d) {
-    return dtype_is_f64 && d.n <= (i64)64 * 64 * 64 ? 4 : 8;
+    (void)d;
+    return dtype_is_f64 ? 4 : 8;
 }
 
 // Ghost units: warp 0 of unit (U, V) reads the plane sums G of the top plane
@@ -543,7 +545,14 @@ cudaError_t build_cta_units(const std::vector<Dims>& dims, int W, WaveUnits* out
     constexpr int D1 = CtaShape<T>::D, D2 = CtaShape<T>::D2;
     const int per_sm = W == 4 ? (u.depth == D1 ? cta_occupancy<T, 4, D1>() : cta_occupancy<T, 4, D2>())
                               : (u.depth == D1 ? cta_occupancy<T, 8, D1>() : cta_occupancy<T, 8, D2>());
-    u.grid = wave_grid(u.n_units, per_sm);
+    // One CTA per SM: units that share an SM share its FP64 pipes and issue
+    // slots, and the unit on the critical path then steps slower (256^3 FP64
+    // with 4-warp units: 1.69 ms at one CTA per SM, 2.14 ms at two).
+    u.grid = per_sm > 0 ? wave_grid(u.n_units, 1) : 0;
+    if (u.grid == 0) {
+        free_wave_units(&u);
+        return cudaErrorInvalidConfiguration;
+    }
     *out = u;
     return cudaGetLastError();
 }
