@@ -361,6 +361,35 @@ def profile_case(args):
         return 0
     f32 = args.profile_case.endswith("32")
     dt = torch.float32 if f32 else torch.float64
+    if args.profile_case.startswith("unit"):
+        # one unit column fed by no other unit: W planes (the default unit
+        # height, 4 in FP64 and 8 in FP32) of 31 - W rows, so that the 30
+        # rows u = y + z of each plane form one unit, and nx = 8192 points
+        # per row: the sweep takes nx + 65 + 2 W steps of that unit, which
+        # gives the period of one unit-step with no wait on other units
+        W = 8 if f32 else 4
+        nx, ny, nz = 8192, 31 - W, W
+        g = m.Grid([dict(nx=nx, ny=ny, nz=nz, op=m.Op.HPCG27, mg_levels=1,
+                         precond_dtype=m.DType.F32 if f32 else m.DType.F64)])
+        ones = torch.ones((nz, ny, nx), dtype=dt, device="cuda")
+        b = torch.empty_like(ones)
+        m.m2s_spmv(g.handle, 0, ones, b)
+        x = torch.zeros_like(ones)
+        for _ in range(3):
+            m.m2s_gs_sweep(g.handle, 0, b, x, m.FORWARD)
+        torch.cuda.synchronize()
+        m.m2s_sweep_timing(g.handle, True)
+        reps = 10
+        for _ in range(reps):
+            m.m2s_gs_sweep(g.handle, 0, b, x, m.FORWARD)
+        torch.cuda.synchronize()
+        nl, ms, _ = m.m2s_sweep_timing_read(g.handle, 0)
+        m.m2s_sweep_timing(g.handle, False)
+        g.close()
+        steps = nx + 65 + 2 * W
+        print("profile case %s: %d-warp unit, %.1f ns per unit-step (%d sweeps, %.3f ms each)" % (
+            args.profile_case, W, ms / max(1, nl) * 1e6 / steps, nl, ms / max(1, nl)))
+        return 0
     if args.profile_case.startswith("kappa"):
         import m2s_inputs as gen
         kap = torch.from_numpy(gen.kappa_field(n)).cuda()
@@ -802,7 +831,8 @@ def main():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workload configurations (32^3 SGS-PCG, block SSOR, "
                          "variable-kappa, batched adjoint, line solves, 1536^3 SymGS)")
-    ap.add_argument("--profile-case", choices=["sweep64", "sweep32", "spmv64", "spmv32",
+    ap.add_argument("--profile-case", choices=["sweep64", "sweep32", "unit64", "unit32",
+                                               "spmv64", "spmv32",
                                                "kappa_sweep64", "block_ssor", "block_jac", "line_penta",
                                                "line_btri", "ilu0"],
                     help="run a few launches of one kernel for an ncu capture and exit")

@@ -89,6 +89,21 @@ __device__ __forceinline__ Tagged<double>::W regs_to_tw(double q, double b) {
     return Tagged<double>::W{(u64)__double_as_longlong(q), (u64)__double_as_longlong(b)};
 }
 
+// A ring entry read from shared memory as it is now (the producer warp may
+// be writing it: each 64-bit half is read once, and its tag tells whether it
+// is the entry wanted).
+__device__ __forceinline__ Tagged<float>::W ring_load(const Tagged<float>::W* p) {
+    Tagged<float>::W r;
+    r.w = ((volatile const Tagged<float>::W*)p)->w;
+    return r;
+}
+__device__ __forceinline__ Tagged<double>::W ring_load(const Tagged<double>::W* p) {
+    Tagged<double>::W r;
+    r.lo = ((volatile const Tagged<double>::W*)p)->lo;
+    r.hi = ((volatile const Tagged<double>::W*)p)->hi;
+    return r;
+}
+
 constexpr int RING = 32;  // steps held by a plane-sum ring
 
 // Shared memory of one CTA: per warp, a ring of tagged plane sums G read by
