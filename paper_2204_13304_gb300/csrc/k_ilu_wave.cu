@@ -42,10 +42,6 @@ constexpr int kRec = 16;  // doubles per weight record: 13 weights, the scale, 2
 constexpr int kUsed = 14;  // record entries read
 constexpr int kL2 = 6;     // steps ahead that a lane asks L2 for its record and input
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // Mailbox row geometry of build_cta_units (k_wave2.cu): rows u = y + z of a
 // plane, 30 per unit column; the row mailbox holds the rows u mod 30 = 28, 29
 // of every plane, the plane mailbox full rows of the planes v = W m - 1.

@@ -171,6 +171,14 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
             if (!halo) {
                 q = __ldg(Qin + p);
                 bv = __ldg(B + p);
+                // once per 128-byte line of the row, ask L2 for the line one
+                // line ahead (256^3 FP64 sweep 1.58 -> 1.55 ms; no change in
+                // FP32)
+                constexpr int kLine = 128 / (int)sizeof(T);
+                if ((x1 & (kLine - 1)) == 0 && x1 + kLine < nx) {
+                    prefetch_l2(Qin + p + step_dir * kLine);
+                    prefetch_l2(B + p + step_dir * kLine);
+                }
                 if (g_in) tw_to_regs(mb_load<T>(mbg_p, p), &m0, &m1);
             } else {
                 tw_to_regs(mb_load<T>(mbox_p, p), &q, &bv);
@@ -226,6 +234,7 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
         const T hu2 = __shfl_up_sync(FULL, h2, 1);
         const T su2 = __shfl_up_sync(FULL, s22, 1);
         const T xh = xm1 + hu1;
+        const T x2 = xm2 + xm1;  // the first add of the row sum H
         const TW* re = ring_in ? &sh.ring[w - 1][(tnow - 1) & (RING - 1)][lane] : nullptr;
         const unsigned gtag = (unsigned)(tnow - 1 + BIAS);
         // The warp below writes a ring entry at each of its steps; this warp's
@@ -268,7 +277,7 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
             }
             if (mb_out) mb_store<T>(mbox_p, p, X1, tag);
         }
-        const T H = (xm2 + xm1) + X1;
+        const T H = x2 + X1;
         xm2 = xm1;
         xm1 = X1;
         h2 = h1;
@@ -410,15 +419,48 @@ int cta_occupancy() {
 
 bool cta_warps_supported(int warps) { return warps == 4 || warps == 8; }
 
-// Default warps per unit, from sweep timings on a GB300 (m2s_autotune_sweeps
-// measures instead), with one CTA per SM: FP64 levels run fastest with
-// 4-warp units at every size (256^3: 1.69 vs 1.70 ms, 128^3: 0.73 vs
-// 0.80 ms; a lone warp on its sub-partition steps at 0.65 us against 0.73 us
-// for two), FP32 levels with 8 (256^3: 1.12 vs 1.30 ms: the cheaper FP32
-// step leaves the SM short of resident units when they are half as tall).
+// The most units of W planes that the wavefront keeps busy at once on one
+// problem: unit (U, V) has rows u in [30 U, 30 U + 30) and planes v in
+// [W V, W V + W), computes when some row y = u - v lies in [0, ny), starts at
+// the step 60 U + 2 W V of its schedule key and runs nx + 65 steps.
+int cta_peak_units(Dims d, int W) {
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return 0;
+    const int NU = d.ny + d.nz - 1, NUc = (NU + 29) / 30, NVc = (d.nz + W - 1) / W;
+    const int S = d.nx + 65;
+    const long long kmax = 60LL * (NUc - 1) + 2LL * W * (NVc - 1);
+    std::vector<int> delta((size_t)(kmax + S + 1), 0);
+    for (int U = 0; U < NUc; ++U) {
+        const int umin = 30 * U, umax = std::min(30 * U + 29, NU - 1);
+        for (int V = 0; V < NVc; ++V) {
+            const int vmin = W * V, vmax = std::min(W * V + W - 1, d.nz - 1);
+            if (umax - vmin < 0 || umin - vmax > d.ny - 1) continue;
+            const long long k = 60LL * U + 2LL * W * V;
+            ++delta[(size_t)k];
+            --delta[(size_t)(k + S)];
+        }
+    }
+    int run = 0, peak = 0;
+    for (int v : delta) peak = std::max(peak, run += v);
+    return peak;
+}
+
+// Default warps per unit (m2s_autotune_sweeps measures instead), one CTA per
+// SM.  A lone warp on its sub-partition steps faster (FP64 unit-step 0.58 us
+// with 4 warps, 0.76 us with 8 when no other unit feeds it), so 4-warp units
+// win while the wavefront keeps the SMs short of work, and 8-warp units,
+// which finish twice the points per SM and step, win once it has more ready
+// units than SMs.  Measured FP64 sweeps on a GB300 (4 vs 8 warps): 256^3
+// 1.57 vs 1.59 ms (peak of 197 busy 4-warp units), 320^3 2.18 vs 2.09 ms
+// (285), 512^3 5.96 vs 4.33 ms, 1024^3 39.5 vs 25.0 ms; so FP64 levels take
+// 4-warp units while their peak stays within 1.5 x the SMs.  FP32 levels
+// take 8-warp units (256^3: 1.11 vs 1.30 ms).
 int cta_default_warps(int dtype_is_f64, Dims d) {
-    (void)d;
-    return dtype_is_f64 ? 4 : 8;
+    if (!dtype_is_f64) return 8;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return 8;
+    return 2 * cta_peak_units(d, 4) <= 3 * sms ? 4 : 8;
 }
 
 // Ghost units: warp 0 of unit (U, V) reads the plane sums G of the top plane

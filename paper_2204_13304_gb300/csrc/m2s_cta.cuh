@@ -72,6 +72,11 @@ __device__ __forceinline__ typename Tagged<T>::W mb_load(const u64* mb, i64 p) {
     return w;
 }
 
+// Ask L2 for the line holding p (no register is written, nothing waits).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // A replayed row keeps its mailbox word in the ring registers of Q and b
 // (a row is either computed or replayed, never both).
 __device__ __forceinline__ void tw_to_regs(Tagged<float>::W w, float* q, float* b) {
