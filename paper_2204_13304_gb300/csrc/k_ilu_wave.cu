@@ -173,6 +173,32 @@ __device__ __forceinline__ void ilu_warp(const IluArgs& a, int t, int w, CtaShar
         const bool needp = rv1 && !halo && (unsigned)(x1 + 1) < (unsigned)nx;
         double pn[3] = {0.0, 0.0, 0.0}, xmb = 0.0;
         bool okj[3] = {true, true, true}, okh = true;
+        // Everything that needs only earlier steps is issued before the wait
+        // and overlaps it: the row below at x + 1 (what the lane below
+        // computed last step), the window shifts, and the ten terms of the
+        // sum over values already held (the two older columns of the plane
+        // below, the row below, x - 1).  After the wait only the plane
+        // below's newest column (three FMAs) remains.  Record offsets
+        // k = (dz+1) 9 + (dy+1) 3 + (dx+1) in the sweep's space.
+        const double bn = __shfl_up_sync(FULL, xm1, 1);
+        B0 = B1;
+        B1 = B2;
+        B2 = bn;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            P[j][0] = P[j][1];
+            P[j][1] = P[j][2];
+        }
+        double t0 = fma(-wt[0], P[0][0], inv);
+        t0 = fma(-wt[1], P[0][1], t0);
+        t0 = fma(-wt[3], P[1][0], t0);
+        t0 = fma(-wt[4], P[1][1], t0);
+        double t1 = -wt[6] * P[2][0];
+        t1 = fma(-wt[7], P[2][1], t1);
+        t1 = fma(-wt[9], B0, t1);
+        t1 = fma(-wt[10], B1, t1);
+        t1 = fma(-wt[11], B2, t1);
+        t1 = fma(-wt[12], xm1, t1);
         const TW* re[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -221,34 +247,14 @@ __device__ __forceinline__ void ilu_warp(const IluArgs& a, int t, int w, CtaShar
                 }
             }
         }
-        // the row below at x + 1: what the lane below computed last step
-        const double bn = __shfl_up_sync(FULL, xm1, 1);
-        B0 = B1;
-        B1 = B2;
-        B2 = bn;
+        // the plane below's newest column, then in - sum of the 13 weighted
+        // lower neighbours, times the point's scale
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            P[j][0] = P[j][1];
-            P[j][1] = P[j][2];
-            P[j][2] = pn[j];
-        }
-        // in - sum of the 13 weighted lower neighbours, in two chains (the
-        // FP64 instructions a step issues, not the chains' depth, set its
-        // time); record offsets k = (dz+1) 9 + (dy+1) 3 + (dx+1) in the
-        // sweep's space
-        double t0 = fma(-wt[0], P[0][0], inv);
-        t0 = fma(-wt[1], P[0][1], t0);
+        for (int j = 0; j < 3; ++j) P[j][2] = pn[j];
         t0 = fma(-wt[2], P[0][2], t0);
-        t0 = fma(-wt[3], P[1][0], t0);
-        t0 = fma(-wt[4], P[1][1], t0);
         t0 = fma(-wt[5], P[1][2], t0);
-        double t1 = -wt[6] * P[2][0];
-        t1 = fma(-wt[7], P[2][1], t1);
         t1 = fma(-wt[8], P[2][2], t1);
-        t1 = fma(-wt[9], B0, t1);
-        t1 = fma(-wt[10], B1, t1);
-        t1 = fma(-wt[11], B2, t1);
-        const double acc = fma(-wt[12], xm1, t0 + t1) * wt[13];
+        const double acc = (t0 + t1) * wt[13];
         const double X = comp ? acc : (in1 && halo ? xmb : 0.0);
         // the slot's inputs are used: refill it for step s + kD (from L2,
         // where the record and input of step s + kL2 are asked for now)
