@@ -553,6 +553,19 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
         bool okx = true, okz = true, okr = true;
         if (in && halo) okx = Tagged<double>::unpack(regs_to_tw(m0, m1), tag, &X);
         if (comp && zmb) okz = Tagged<double>::unpack(regs_to_tw(m0, m1), tag, &zc);
+        // The x - 1 and y - 1 neighbours (the own group and the group below,
+        // both from the previous step) need no wait: their ten FMAs are
+        // issued before it and overlap it, and only the five of the z - 1
+        // neighbour follow the wait.
+        const int gy = g >= 1 && g < 6 ? gb - 5 : 0;
+        double acc = DI && a.rev ? 0.0 : rh;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const double vx = __shfl_sync(FULL, xprev, gb + j);
+            const double vy = __shfl_sync(FULL, xprev, gy + j);
+            acc = fma(-cf[j], vx, acc);
+            acc = fma(-cf[5 + j], vy, acc);
+        }
         const TW* re = ring_in ? &sh.ring[w - 1][(s - 1) & (RING - 1)][lane] : nullptr;
         const unsigned rtag = (unsigned)(s - 1 + BIAS);
         if (ring_in && s >= 1) okr = Tagged<double>::unpack(*(volatile const TW*)re, rtag, &zc);
@@ -573,19 +586,12 @@ __device__ __forceinline__ void block_warp(const BlockCtaArgs& a, int t, int w, 
                 }
             }
         }
-        // neighbour 5-vectors: x - 1 (own group, previous step), y - 1 (the
-        // group below, previous step), z - 1 (warp below / unit underneath)
-        // (one chain: the sweep is bound by the number of FP64 instructions
-        // it issues, so no extra partial sums)
-        const int gy = g >= 1 && g < 6 ? gb - 5 : 0;
-        double acc = DI && a.rev ? 0.0 : rh;
+        // the z - 1 neighbour (warp below / unit underneath), continuing the
+        // one chain (the sweep is bound by the FP64 instructions it issues,
+        // so no extra partial sums)
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
-            const double vx = __shfl_sync(FULL, xprev, gb + j);
-            const double vy = __shfl_sync(FULL, xprev, gy + j);
             const double vz = __shfl_sync(FULL, zc, gb + j);
-            acc = fma(-cf[j], vx, acc);
-            acc = fma(-cf[5 + j], vy, acc);
             acc = fma(-cf[10 + j], vz, acc);
         }
         if constexpr (DI) {

@@ -169,6 +169,11 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
         bool okx = true, okz = true, okr = true;
         if (in && halo) okx = Tagged<T>::unpack(regs_to_tw(q, bv), tag, &X1);
         if (comp && zmb) okz = Tagged<T>::unpack(regs_to_tw(m0, m1), tag, &zv);
+        // the x - 1 and y - 1 terms of N need only the previous step: issued
+        // before the wait, they overlap it (same order of operations)
+        const T hu = __shfl_up_sync(FULL, xm1, 1);  // row y - 1 at this x
+        T N = c0 * xm1;
+        N = fma(c1, hu, N);
         const TW* re = ring_in ? &sh.ring[w - 1][(s - 1) & (RING - 1)][lane] : nullptr;
         const unsigned rtag = (unsigned)(s - 1 + BIAS);
         if (ring_in && s >= 1) okr = Tagged<T>::unpack(*(volatile const TW*)re, rtag, &zv);
@@ -190,10 +195,7 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
                 }
             }
         }
-        const T hu = __shfl_up_sync(FULL, xm1, 1);  // row y - 1 at this x
         if (comp) {
-            T N = c0 * xm1;
-            N = fma(c1, hu, N);
             N = fma(c2, zv, N);
             X1 = (q + N) * dd;
             const i64 p = L + dir * xx;
