@@ -79,7 +79,8 @@ EXPORTS = (
     "m2s_symgs", "m2s_gs_sweep", "m2s_mg_restrict", "m2s_mg_prolong", "m2s_mg_vcycle",
     "m2s_pcg_solve", "m2s_ssor_sweep", "m2s_adjoint_solve", "m2s_kappa_grad",
     "m2s_set_spin_limit", "m2s_debug_stall_unit", "m2s_symgs_noalloc", "m2s_status_string",
-    "m2s_sweep_timing", "m2s_sweep_timing_read", "m2s_set_sweep_warps", "m2s_set_graphs",
+    "m2s_sweep_timing", "m2s_sweep_timing_read", "m2s_set_sweep_warps", "m2s_sweep_warps",
+    "m2s_set_graphs",
     "m2s_autotune_sweeps", "m2s_line_penta", "m2s_line_penta_work_bytes", "m2s_line_btri",
     "m2s_line_btri_work_bytes", "m2s_ilu0_setup", "m2s_ilu0_apply",
     "m2s_ilu0_factors", "m2s_debug_bounds_read",
@@ -123,6 +124,7 @@ def load():
         "m2s_status_string": ([i], ctypes.c_char_p),
         "m2s_sweep_timing": ([vp, i], i),
         "m2s_set_sweep_warps": ([vp, i, i], i),
+        "m2s_sweep_warps": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "m2s_set_graphs": ([vp, i], i),
         "m2s_autotune_sweeps": ([vp, i, vp, ctypes.POINTER(i)], i),
         "m2s_sweep_timing_read": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(d),
@@ -256,6 +258,14 @@ def m2s_set_spin_limit(grid, limit_ns):
 
 def m2s_debug_stall_unit(grid, level, unit):
     return _check(load().m2s_debug_stall_unit(grid, int(level), int(unit)), "m2s_debug_stall_unit")
+
+
+def m2s_sweep_warps(grid, level):
+    """(FP64, FP32) warps per unit of the 27-point sweeps of `level`."""
+    w64, w32 = ctypes.c_int(), ctypes.c_int()
+    _check(load().m2s_sweep_warps(grid, int(level), ctypes.byref(w64), ctypes.byref(w32)),
+           "m2s_sweep_warps")
+    return w64.value, w32.value
 
 
 def m2s_set_sweep_warps(grid, level, warps):

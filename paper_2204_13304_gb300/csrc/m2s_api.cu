@@ -869,6 +869,14 @@ m2s_status m2s_sweep_timing_read(m2s_grid* grid, int level, int* launches, doubl
     return M2S_OK;
 }
 
+m2s_status m2s_sweep_warps(m2s_grid* grid, int level, int* warps_f64, int* warps_f32) {
+    if (!grid || !warps_f64 || !warps_f32 || grid->op != M2S_OP_HPCG27) return M2S_ERR_INVALID_ARG;
+    if (level < 0 || level >= grid->levels) return M2S_ERR_INVALID_ARG;
+    *warps_f64 = grid->units[level].W;
+    *warps_f32 = grid->w32_choice[level];
+    return M2S_OK;
+}
+
 m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps) {
     if (!grid || grid->op != M2S_OP_HPCG27 || !cta_warps_supported(warps)) return M2S_ERR_INVALID_ARG;
     if (level < -1 || level >= grid->levels) return M2S_ERR_INVALID_ARG;

@@ -387,6 +387,42 @@ def test_sweep_unit_shapes_agree_bitwise(m, shape, f32):
         assert err64(out[0], oracle.symgs(H27, b, x0, 2)) <= TOL64
 
 
+def peak_busy_units(nx, ny, nz, W):
+    """The most units of W planes whose runs overlap: unit (U, V) covers rows
+    u = y + z in [30 U, 30 U + 30) and planes [W V, W V + W), computes when
+    one of its rows has 0 <= u - v < ny, and runs nx + 65 steps from step
+    60 U + 2 W V of its schedule key."""
+    NU = ny + nz - 1
+    busy = {}
+    for U in range((NU + 29) // 30):
+        for V in range((nz + W - 1) // W):
+            if any(0 <= u - v < ny for u in range(30 * U, min(30 * U + 30, NU))
+                   for v in range(W * V, min(W * V + W, nz))):
+                k = 60 * U + 2 * W * V
+                for t in range(k, k + nx + 65):
+                    busy[t] = busy.get(t, 0) + 1
+    return max(busy.values(), default=0)
+
+
+def test_default_unit_height_follows_parallelism(m):
+    """FP64 levels take 4-warp units while the wavefront of 4-warp units
+    keeps at most 1.5 x the SMs busy, 8-warp units above; FP32 levels take
+    8; the query returns what m2s_set_sweep_warps set."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for shape in [(32, 32, 32), (40, 11, 3), (128, 128, 128), (256, 256, 256), (320, 320, 320)]:
+        g = make_grid(m, shape, levels=1)
+        w64, w32 = m.m2s_sweep_warps(g.handle, 0)
+        nz, ny, nx = shape
+        want = 4 if 2 * peak_busy_units(nx, ny, nz, 4) <= 3 * sms else 8
+        assert (w64, w32) == (want, 8), (shape, w64, w32, want)
+        if sms == 152 and shape[0] in (256, 320):
+            assert w64 == (4 if shape[0] == 256 else 8)
+        m.m2s_set_sweep_warps(g.handle, -1, 8 if w64 == 4 else 4)
+        assert m.m2s_sweep_warps(g.handle, 0) == ((8, 8) if w64 == 4 else (4, 4))
+        g.close()
+
+
 def test_mg_pcg_with_four_warp_units(m):
     import torch
     shape = (64, 64, 64)
