@@ -97,7 +97,7 @@ inline i64 mbg_values(const Dims& d, int W) {
 // compile-time direction makes the FP32 sweep 8 % faster (1.24 -> 1.15 ms)
 // and the FP64 sweep 2 % slower (1.69 -> 1.72 ms), so FP32 launches use
 // RD = 0 / 1 and FP64 launches RD = -1.
-template <typename T, int W, int D, int RD>
+template <typename T, int W, int D, int RD, int ROLE>
 __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
                                              CtaShared<T, W>& sh, unsigned tag) {
     typedef typename Tagged<T>::W TW;
@@ -111,9 +111,10 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
     const int tbase = 2 * (org.x - 2) + 2 * (v1 - 1);
     const T inv26 = Lit<T>::inv26();
     const bool halo = lane < 2;
-    const bool ring_in = w > 0;
-    const bool ring_out = w < W - 1;
-    const bool top = w == W - 1;
+    // ROLE: -1 read from w; 0 the bottom warp, 1 a middle one, 2 the top one
+    const bool ring_in = ROLE < 0 ? w > 0 : ROLE != 0;
+    const bool ring_out = ROLE < 0 ? w < W - 1 : ROLE != 2;
+    const bool top = ROLE < 0 ? w == W - 1 : ROLE == 2;
     const bool mb_out = !halo && lane >= 30;
     const int nx = dd.nx;
     const int y1 = u - v1;
@@ -332,6 +333,15 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
     }
 }
 
+// FP64 warps run a copy of the step compiled for their role (bottom warp:
+// mailbox in, ring out; middle: ring in and out; top: ring in, mailbox out),
+// which drops the role tests from the step: isolated 4-warp unit 584 -> 539
+// ns per step, 256^3 sweep 1.56 -> 1.52 ms, 512^3 with 8-warp units 4.29 ->
+// 4.21 ms.  FP32 keeps one copy: three copies of its eight-step unrolled
+// loop took its 256^3 sweep from 1.07 to 2.04 ms.
+template <typename T, int W>
+constexpr bool kRoles = sizeof(T) == 8;
+
 template <typename T, int K, int W, int D, int RD>
 __global__ void __launch_bounds__(W * 32, 1) gs27_cta_kernel(CtaArgs<T> a) {
     static_assert(K == 2, "one halo plane and one computed plane per warp");
@@ -354,7 +364,18 @@ __global__ void __launch_bounds__(W * 32, 1) gs27_cta_kernel(CtaArgs<T> a) {
         int ab = 0;
         if (threadIdx.x == 0) ab = ld_relaxed_gpu(&a.status->abort) || t == a.stall_unit;
         ab = __syncthreads_or(ab);
-        if (!ab) compute_warp<T, W, D, RD>(a, t, warp, sh, s_tag);
+        if (!ab) {
+            if constexpr (kRoles<T, W>) {
+                if (warp == 0)
+                    compute_warp<T, W, D, RD, 0>(a, t, warp, sh, s_tag);
+                else if (warp == W - 1)
+                    compute_warp<T, W, D, RD, 2>(a, t, warp, sh, s_tag);
+                else
+                    compute_warp<T, W, D, RD, 1>(a, t, warp, sh, s_tag);
+            } else {
+                compute_warp<T, W, D, RD, -1>(a, t, warp, sh, s_tag);
+            }
+        }
         __syncthreads();
     }
     // exit protocol: the last CTA out resets the ticket and advances the tag
