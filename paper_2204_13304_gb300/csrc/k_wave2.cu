@@ -333,14 +333,14 @@ __device__ __forceinline__ void compute_warp(const CtaArgs<T>& a, int t, int w,
     }
 }
 
-// FP64 warps run a copy of the step compiled for their role (bottom warp:
+// Warps run a copy of the step compiled for their role (bottom warp:
 // mailbox in, ring out; middle: ring in and out; top: ring in, mailbox out),
-// which drops the role tests from the step: isolated 4-warp unit 584 -> 539
-// ns per step, 256^3 sweep 1.56 -> 1.52 ms, 512^3 with 8-warp units 4.29 ->
-// 4.21 ms.  FP32 keeps one copy: three copies of its eight-step unrolled
-// loop took its 256^3 sweep from 1.07 to 2.04 ms.
+// which drops the role tests from the step: FP64 isolated 4-warp unit 584 ->
+// 539 ns per step, 256^3 sweep 1.56 -> 1.52 ms, 512^3 with 8-warp units
+// 4.29 -> 4.21 ms; FP32 (at prefetch depth 4) 256^3 sweep 1.03 -> 1.00 ms,
+// 128^3 0.42 -> 0.38 ms.
 template <typename T, int W>
-constexpr bool kRoles = sizeof(T) == 8;
+constexpr bool kRoles = true;
 
 template <typename T, int K, int W, int D, int RD>
 __global__ void __launch_bounds__(W * 32, 1) gs27_cta_kernel(CtaArgs<T> a) {
@@ -398,15 +398,16 @@ __global__ void __launch_bounds__(W * 32, 1) gs27_cta_kernel(CtaArgs<T> a) {
 // Shapes of the CTA wavefront per element type: K register slots per lane
 // (one halo plane + K-1 computed planes) and the depth D of the input
 // prefetch ring in steps, which is also the unrolling of the step loop.  The
-// number W of compute warps per CTA is chosen at run time (4 or 8), and so is
-// D for FP32.  Measured on a GB300: FP64 runs fastest with D = 2 at every
-// level size (a shorter unrolled loop, 1.79 vs 1.93 ms at 256^3); FP32 with
-// D = 8 on levels above 128^3 (1.25 vs 1.75 ms at 256^3: the loads of a
-// faster step need the longer lead) and D = 4 below (0.48 vs 0.56 ms at
-// 128^3: the shorter loop stays in the instruction cache).
+// number W of compute warps per CTA is chosen at run time (4 or 8); D2 is
+// the depth of levels above 128^3 points.  Measured on a GB300: FP64 runs
+// fastest with D = 2 at every level size (a shorter unrolled loop, 1.79 vs
+// 1.93 ms at 256^3).  FP32, whose warps run role-compiled copies of the
+// step, with D = 4 at every size (256^3: 1.00 ms against 1.54 ms with
+// D = 6, whose three copies no longer fit the instruction cache; without
+// the copies D = 8 had measured 1.03 ms and D = 4 1.75 ms there).
 template <typename T> struct CtaShape;
 template <> struct CtaShape<double> { static constexpr int K = 2, D = 2, D2 = 2; };
-template <> struct CtaShape<float> { static constexpr int K = 2, D = 4, D2 = 8; };
+template <> struct CtaShape<float> { static constexpr int K = 2, D = 4, D2 = 4; };
 
 // Prefetch depth of a level: CtaShape::D, or CtaShape::D2 for FP32 levels of
 // more than 128^3 points.
