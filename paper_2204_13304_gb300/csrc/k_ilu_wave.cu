@@ -65,7 +65,7 @@ struct IluArgs {
     int stall_unit;  // test hook: this unit neither computes nor publishes (-1: none)
 };
 
-template <int W>
+template <int W, int ROLE>
 __device__ __forceinline__ void ilu_warp(const IluArgs& a, int t, int w, CtaShared<double, W>& sh,
                                          unsigned tag) {
     typedef Tagged<double>::W TW;
@@ -77,8 +77,9 @@ __device__ __forceinline__ void ilu_warp(const IluArgs& a, int t, int w, CtaShar
     const int u = un.x - 2 + lane;
     const int tbase = 2 * (un.x - 2) + 2 * (v1 - 1);
     const bool halo = lane < 2;
-    const bool ring_in = w > 0;
-    const bool ring_out = w < W - 1;
+    // ROLE (compile time): 0 the bottom warp, 1 a middle one, 2 the top one
+    const bool ring_in = ROLE != 0;
+    const bool ring_out = ROLE != 2;
     const bool mb_out = !halo && lane >= 30;
     const int nx = dd.nx;
     const int y1 = u - v1;
@@ -95,7 +96,7 @@ __device__ __forceinline__ void ilu_warp(const IluArgs& a, int t, int w, CtaShar
     u64* const mbt = a.mbt + a.mboff[2 * un.z + 1] * 2;
     u64* const mbox_p = mbox + (mrow + rx - L1) * 2;  // tagged words of point p at [2p], [2p+1]
     // the top warp publishes its rows for warp 0 of the unit above
-    const bool t_out = w == W - 1 && !halo && rv1 && v1 + 1 < dd.nz;
+    const bool t_out = ROLE == 2 && !halo && rv1 && v1 + 1 < dd.nz;
     u64* const tout = mbt + (t_out ? ((i64)((v1 + 1) / W) * NU + u) * nx + rx : 0) * 2;
     // warp 0 reads rows u - 2 + j (j = 0, 1, 2) of plane v1 - 1 there
     bool pj[3];
@@ -337,7 +338,15 @@ __global__ void __launch_bounds__(W * 32, 1) ilu_cta_kernel(IluArgs a) {
         if (threadIdx.x == 0) ab = ld_relaxed_gpu(&a.status->abort) || t == a.stall_unit;
         const int any = __syncthreads_or(mine);
         ab = __syncthreads_or(ab);
-        if (any && !ab) ilu_warp<W>(a, t, warp, sh, s_tag);
+        // each warp runs a copy of the step compiled for its role
+        if (any && !ab) {
+            if (warp == 0)
+                ilu_warp<W, 0>(a, t, warp, sh, s_tag);
+            else if (warp == W - 1)
+                ilu_warp<W, 2>(a, t, warp, sh, s_tag);
+            else
+                ilu_warp<W, 1>(a, t, warp, sh, s_tag);
+        }
         __syncthreads();
     }
     // exit protocol: the last CTA out resets the ticket and advances the tag

@@ -76,7 +76,7 @@ struct Cta7Shared {
     volatile int prog[W];
 };
 
-template <typename T, int W, int D, int RD>
+template <typename T, int W, int D, int RD, int ROLE>
 __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
                                             Cta7Shared<T, W>& sh, unsigned tag) {
     typedef typename Tagged<T>::W TW;
@@ -88,10 +88,13 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
     const int z = un.y + w;
     const bool halo = lane == 0;
     const bool rv = y >= 0 && y < dm.ny && z < dm.nz;
-    const bool ring_in = w > 0;
-    const bool ring_out = w < W - 1;
-    const bool mb_out = !halo && (lane == 31 || w == W - 1);
-    const bool zmb = w == 0 && z >= 1;  // plane below from the unit underneath
+    // ROLE: -1 read from w; 0 the bottom warp, 1 a middle one, 2 the top one
+    const bool bottom = ROLE < 0 ? w == 0 : ROLE == 0;
+    const bool topw = ROLE < 0 ? w == W - 1 : ROLE == 2;
+    const bool ring_in = !bottom;
+    const bool ring_out = !topw;
+    const bool mb_out = !halo && (lane == 31 || topw);
+    const bool zmb = bottom && z >= 1;  // plane below from the unit underneath
     const int nx = dm.nx;
     // direction: RD = 0 forward, 1 backward (compile time), -1 read at run time
     const bool rev = RD < 0 ? a.rev != 0 : RD == 1;
@@ -253,6 +256,15 @@ __device__ __forceinline__ void sweep7_warp(const Cta7Args<T>& a, int t, int w,
     }
 }
 
+// FP32 warps run a copy of the step compiled for their role, which drops
+// the role tests from the step (256^3 FP32 sweep 0.65 -> 0.62 ms with the
+// loop unrolled four deep; eight deep, the three copies took 1.04 ms).  FP64
+// keeps one copy: with three, the 256^3 sweep was unchanged (0.92 ms) but
+// the batched solve of 64 problems of 32^3-128^3 went 1.80 -> 2.21 s (its
+// finest-level sweep 1.30 -> 1.66 ms).
+template <typename T>
+constexpr bool kRoles7 = sizeof(T) == 4;
+
 template <typename T, int W, int D, int RD>
 __global__ void __launch_bounds__(W * 32, 1) gs7_cta_kernel(Cta7Args<T> a) {
     __shared__ int s_ticket;
@@ -274,7 +286,18 @@ __global__ void __launch_bounds__(W * 32, 1) gs7_cta_kernel(Cta7Args<T> a) {
         int ab = 0;
         if (threadIdx.x == 0) ab = ld_relaxed_gpu(&a.status->abort) || t == a.stall_unit;
         ab = __syncthreads_or(ab);
-        if (!ab) sweep7_warp<T, W, D, RD>(a, t, warp, sh, s_tag);
+        if (!ab) {
+            if constexpr (kRoles7<T>) {
+                if (warp == 0)
+                    sweep7_warp<T, W, D, RD, 0>(a, t, warp, sh, s_tag);
+                else if (warp == W - 1)
+                    sweep7_warp<T, W, D, RD, 2>(a, t, warp, sh, s_tag);
+                else
+                    sweep7_warp<T, W, D, RD, 1>(a, t, warp, sh, s_tag);
+            } else {
+                sweep7_warp<T, W, D, RD, -1>(a, t, warp, sh, s_tag);
+            }
+        }
         __syncthreads();
     }
     // exit protocol: the last CTA out resets the ticket and advances the tag
@@ -297,9 +320,11 @@ template <typename T> struct Cta7Shape;
 // launches (0 and 1 compile the direction in; -1 reads it at run time).
 // Measured on a GB300 (variable-kappa 256^3 MG-PCG): compiled-in directions
 // take the 256^3 sweep from 0.98 to 0.97 ms (FP64) and 0.72 to 0.71 ms
-// (FP32), the solves from 2.54 to 2.50 s and 1.99 to 1.95 s.
+// (FP32), the solves from 2.54 to 2.50 s and 1.99 to 1.95 s.  D is the
+// prefetch depth in steps and the unrolling of the step loop: 4 for both,
+// so that the role copies of the FP32 step fit the instruction cache.
 template <> struct Cta7Shape<double> { static constexpr int W = 8, D = 4, RD0 = 0, RD1 = 1; };
-template <> struct Cta7Shape<float> { static constexpr int W = 8, D = 8, RD0 = 0, RD1 = 1; };
+template <> struct Cta7Shape<float> { static constexpr int W = 8, D = 4, RD0 = 0, RD1 = 1; };
 
 template <typename T>
 size_t cta7_smem_bytes() {
