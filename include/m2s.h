@@ -383,9 +383,10 @@ m2s_status m2s_set_sweep_warps(m2s_grid* grid, int level, int warps);
  * m2s_set_sweep_warps or m2s_autotune_sweeps set last, else the default
  * chosen with the schedule.  The default is 8 for FP32; for FP64 it is 4
  * while the wavefront of 4-warp units keeps at most 1.5 times the device's
- * SM count of units busy at once (the most units whose runs of nx + 65
- * steps, from step 60 U + 8 V of unit (U, V), overlap), else 8: a lone warp
- * per sub-partition steps faster, two finish twice the points per SM.
+ * SM count of units busy at once (the most units, over all problems of the
+ * level, whose runs of nx + 65 steps, from step 60 U + 8 V of unit (U, V),
+ * overlap), else 8: a lone warp per sub-partition steps faster, two finish
+ * twice the points per SM.
  * Errors: M2S_ERR_INVALID_ARG (NULL grid or output, not a 27-point grid,
  * level out of range). */
 m2s_status m2s_sweep_warps(m2s_grid* grid, int level, int* warps_f64, int* warps_f32);

@@ -441,24 +441,28 @@ int cta_occupancy() {
 
 bool cta_warps_supported(int warps) { return warps == 4 || warps == 8; }
 
-// The most units of W planes that the wavefront keeps busy at once on one
-// problem: unit (U, V) has rows u in [30 U, 30 U + 30) and planes v in
+// The most units of W planes that the wavefront keeps busy at once on a
+// level's problems (their units share one schedule, all starting at key 0):
+// unit (U, V) of a problem has rows u in [30 U, 30 U + 30) and planes v in
 // [W V, W V + W), computes when some row y = u - v lies in [0, ny), starts at
 // the step 60 U + 2 W V of its schedule key and runs nx + 65 steps.
-int cta_peak_units(Dims d, int W) {
-    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return 0;
-    const int NU = d.ny + d.nz - 1, NUc = (NU + 29) / 30, NVc = (d.nz + W - 1) / W;
-    const int S = d.nx + 65;
-    const long long kmax = 60LL * (NUc - 1) + 2LL * W * (NVc - 1);
-    std::vector<int> delta((size_t)(kmax + S + 1), 0);
-    for (int U = 0; U < NUc; ++U) {
-        const int umin = 30 * U, umax = std::min(30 * U + 29, NU - 1);
-        for (int V = 0; V < NVc; ++V) {
-            const int vmin = W * V, vmax = std::min(W * V + W - 1, d.nz - 1);
-            if (umax - vmin < 0 || umin - vmax > d.ny - 1) continue;
-            const long long k = 60LL * U + 2LL * W * V;
-            ++delta[(size_t)k];
-            --delta[(size_t)(k + S)];
+int cta_peak_units(const std::vector<Dims>& dims, int W) {
+    std::vector<int> delta;
+    for (const Dims& d : dims) {
+        if (d.nx < 1 || d.ny < 1 || d.nz < 1) continue;
+        const int NU = d.ny + d.nz - 1, NUc = (NU + 29) / 30, NVc = (d.nz + W - 1) / W;
+        const int S = d.nx + 65;
+        const long long kmax = 60LL * (NUc - 1) + 2LL * W * (NVc - 1);
+        if (delta.size() < (size_t)(kmax + S + 1)) delta.resize((size_t)(kmax + S + 1), 0);
+        for (int U = 0; U < NUc; ++U) {
+            const int umin = 30 * U, umax = std::min(30 * U + 29, NU - 1);
+            for (int V = 0; V < NVc; ++V) {
+                const int vmin = W * V, vmax = std::min(W * V + W - 1, d.nz - 1);
+                if (umax - vmin < 0 || umin - vmax > d.ny - 1) continue;
+                const long long k = 60LL * U + 2LL * W * V;
+                ++delta[(size_t)k];
+                --delta[(size_t)(k + S)];
+            }
         }
     }
     int run = 0, peak = 0;
@@ -476,13 +480,13 @@ int cta_peak_units(Dims d, int W) {
 // (285), 512^3 5.96 vs 4.33 ms, 1024^3 39.5 vs 25.0 ms; so FP64 levels take
 // 4-warp units while their peak stays within 1.5 x the SMs.  FP32 levels
 // take 8-warp units (256^3: 1.11 vs 1.30 ms).
-int cta_default_warps(int dtype_is_f64, Dims d) {
+int cta_default_warps(int dtype_is_f64, const std::vector<Dims>& dims) {
     if (!dtype_is_f64) return 8;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
         return 8;
-    return 2 * cta_peak_units(d, 4) <= 3 * sms ? 4 : 8;
+    return 2 * cta_peak_units(dims, 4) <= 3 * sms ? 4 : 8;
 }
 
 // Ghost units: warp 0 of unit (U, V) reads the plane sums G of the top plane

@@ -790,8 +790,9 @@ m2s_status m2s_grid_create(const m2s_grid_desc* descs, int n_problems, void* str
     g->units32.assign(L, WaveUnits{});
     for (int l = 0; l < L; ++l) {
         if (op == M2S_OP_HPCG27) {
-            if ((e = build_level_units27(g, l, cta_default_warps(1, g->dims[0][l]),
-                                         cta_default_warps(0, g->dims[0][l]))) != cudaSuccess)
+            const std::vector<Dims> dl = level_dims(g, l);
+            if ((e = build_level_units27(g, l, cta_default_warps(1, dl), cta_default_warps(0, dl))) !=
+                cudaSuccess)
                 return fail(e);
         } else {
             if ((e = build_cta7_units<double>(level_dims(g, l), &g->units[l])) != cudaSuccess)

@@ -192,7 +192,7 @@ constexpr int kWaveSlots = 5;  // register slots per lane of the sweep kernels
 template <typename T>
 cudaError_t build_cta_units(const std::vector<Dims>& dims, int warps, WaveUnits* out);
 bool cta_warps_supported(int warps);
-int cta_default_warps(int dtype_is_f64, Dims d);
+int cta_default_warps(int dtype_is_f64, const std::vector<Dims>& dims);
 // b.x partials of the largest schedule of these problems
 int cta_rz_partials_max(const std::vector<Dims>& dims);
 // Qin and Qout hold Q/26; b is b/26 when Qout is written, b when the b.x

@@ -421,6 +421,15 @@ def test_default_unit_height_follows_parallelism(m):
         m.m2s_set_sweep_warps(g.handle, -1, 8 if w64 == 4 else 4)
         assert m.m2s_sweep_warps(g.handle, 0) == ((8, 8) if w64 == 4 else (4, 4))
         g.close()
+    # a batch: the problems' units share one schedule, so their busy units add
+    n = 96
+    g = m.Grid([dict(nx=n, ny=n, nz=n, op=0, mg_levels=1)] * 6)
+    one = peak_busy_units(n, n, n, 4)
+    want = 4 if 2 * 6 * one <= 3 * sms else 8
+    assert m.m2s_sweep_warps(g.handle, 0) == (want, 8)
+    if sms == 152:
+        assert want == 8 and 2 * one <= 3 * sms  # one 96^3 problem alone takes 4
+    g.close()
 
 
 def test_mg_pcg_with_four_warp_units(m):
