@@ -245,6 +245,36 @@ def oracle_iterations(n):
         return None, "no stored oracle history for this size"
 
 
+def oracle_samples(n):
+    """Sample indices and values of the oracle's FP64 MG-PCG solution to 1e-10
+    on the n^3 problem (tests/golden/make_hpcg_pcg_samples.py wrote them from
+    the oracle alone), or None when no file is stored for this size."""
+    path = os.path.join(ROOT, "tests", "golden", "hpcg_pcg_samples_%d_rtol.txt" % n)
+    idx, val = [], []
+    try:
+        with open(path) as f:
+            for ln in f:
+                if ln.startswith("#") or ln.startswith("h ") or not ln.strip():
+                    continue
+                p_, v_ = ln.split()
+                idx.append(int(p_))
+                val.append(float(v_))
+    except OSError:
+        return None
+    return idx, val
+
+
+def err_vs_oracle_samples(torch, x, samples):
+    """max_i |x_i - o_i| / max(|o_i|, 1e-3 max |o|) over the stored samples."""
+    if samples is None:
+        return None
+    idx = torch.tensor(samples[0], dtype=torch.int64, device=x.device)
+    g = x.reshape(-1).index_select(0, idx).double().cpu()
+    o = torch.tensor(samples[1], dtype=torch.float64)
+    den = torch.clamp(o.abs(), min=1e-3 * float(o.abs().max()))
+    return float(((g - o).abs() / den).max())
+
+
 def profile_value(kernel_tag, key, sources=None):
     """A machine-read figure (`- key: value` line) of the committed ncu summary
     profiles/<kernel_tag>.md, or None when the summary is missing or the
@@ -908,6 +938,10 @@ def main():
     t32 = e0.elapsed_time(e1) / 1e3 / args.steps
     err32 = float((x - x64).abs().max() / x64.abs().max())
     err64_ones = float((x64 - 1.0).abs().max())
+    # both solutions per entry against the oracle's at its stored samples
+    osamp = oracle_samples(n)
+    eo64 = err_vs_oracle_samples(torch, x64, osamp)
+    eo32 = err_vs_oracle_samples(torch, x, osamp)
 
     # per-kernel timings (CUDA events on the launching stream)
     def time_op(fn, reps=5):
@@ -1059,8 +1093,10 @@ def main():
         "iters_fp64": res64.iters, "rel_resid_fp64": res64.rel_resid,
         "fp64_50_iterations_s": t50,
         "max_err_vs_ones_fp64": err64_ones,
+        "err_vs_oracle_samples_fp64": eo64,
         "fp32_precond": {"value": t32, "unit": "s", "iters": res32.iters,
                          "rel_resid": res32.rel_resid, "rel_err_vs_fp64_solution": err32,
+                         "err_vs_oracle_samples": eo32,
                          "speedup_vs_fp64": t64 / t32},
         "kernels": kern, "sweep_share_of_solve": sweep_share,
         "sweep_ms_per_launch_by_level": [v[1] / max(1, v[0]) for v in sweep_lv],
