@@ -15,7 +15,9 @@
 //    in v, one computed plane per warp, and 32 lanes in u: lanes 0-1 replay
 //    the two rows of the unit to the left, warp 0 also replays the plane
 //    below from the unit underneath.  Units take tickets in topological
-//    order, sorted by the step at which they can start.
+//    order, sorted by the step at which they can start; one CTA runs per
+//    SM, and each warp runs a copy of the step compiled for its role
+//    (bottom, middle or top warp of the unit).
 //  * Values crossing units travel through a mailbox of tagged words (value
 //    and launch tag in one 64-bit relaxed store): a reader that sees the
 //    current tag has the value, so neither side fences.  Warps of a CTA
@@ -91,8 +93,10 @@ inline i64 mbg_values(const Dims& d, int W) {
 // the warp below from its shared-memory ring).  Rows that other units read
 // (lanes 30-31, and the top warp's plane) are also written to the mailbox
 // with the launch tag.  The step is written for the fewest instructions:
-// incremental indices, one warp vote per step for all tag checks.  RD is
-// the direction: 0 forward, 1 backward, -1 read from the launch arguments.
+// one warp vote per step for all tag checks, and the work that needs only
+// the previous step issued ahead of the wait.  RD is the direction: 0
+// forward, 1 backward, -1 read from the launch arguments; ROLE the warp's
+// place in the unit (-1: read from w).
 // Measured on a GB300 (256^3 sweeps inside the MG-PCG solve): a
 // compile-time direction makes the FP32 sweep 8 % faster (1.24 -> 1.15 ms)
 // and the FP64 sweep 2 % slower (1.69 -> 1.72 ms), so FP32 launches use
